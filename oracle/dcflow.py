@@ -1,0 +1,227 @@
+"""Brute-force FP64 DC N-1 evaluation of split topologies (test oracle).
+
+For every candidate topology the oracle builds the post-split bus/branch graph,
+solves the DC loadflow from scratch, and re-solves the whole grid once per
+outage with that branch removed.  No PTDF, LODF or low-rank update is used:
+these are the plain definitions that the fast path must reproduce.
+
+Definitions followed:
+  * DC flows f_l = b_l (theta_from - theta_to) with B theta = p, slack angle 0
+    (Sec. "Importer": linearised DC representation).
+  * Two-node operation of a split station (Sec. "Switching actions"): the assets
+    on busbar B move to a new node; busbar A keeps the rest.
+  * f_e^max = max over outages of |f_e^(o)| (Sec. "Fitness function heuristics").
+  * lambda_o = sum_e Pi(f_e^max - fbar_e), lambda_c = sum_e 1(f_e^max > fbar_e),
+    lambda_c0 = sum_e 1(|f_e^n0| > fbar_e) (same section).
+  * lambda_f1 = -(lambda_o + 200 lambda_c0 + 50 lambda_c) (Sec. "High-level
+    Genetic Algorithm loop").
+  * Workload fitness = -(lambda_o + max loading), max loading over N-0 and N-1.
+  * lambda_s = number of split stations; lambda_r read as the number of moved
+    assets min(|A|, |B|) per split (Sec. "Fitness function heuristics",
+    "Repertoire design").
+
+Readings where the paper is silent (each also listed in the design notes):
+  * an outage that islands the post-split grid is skipped in the maximum and
+    counted; a topology whose split itself islands the grid is invalid
+    (fitness -inf);
+  * with several timesteps, lambda_o / lambda_c / lambda_c0 sum over timesteps
+    and max loading takes the maximum over timesteps;
+  * cell = min(lambda_s, D_s - 1) * D_m + min(moved, D_m - 1).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.csgraph as csg
+import scipy.sparse.linalg as spla
+
+DENSE_MAX = 400
+
+
+class TopologyError(ValueError):
+    pass
+
+
+def _find(parent, x):
+    while parent[x] != x:
+        parent[x] = parent[parent[x]]
+        x = parent[x]
+    return x
+
+
+def is_connected_uf(n_node, fr, to, skip=-1):
+    """Union-find connectivity over all nodes (an isolated node counts)."""
+    parent = list(range(n_node))
+    comps = n_node
+    for e in range(len(fr)):
+        if e == skip:
+            continue
+        a, b = _find(parent, int(fr[e])), _find(parent, int(to[e]))
+        if a != b:
+            parent[b] = a
+            comps -= 1
+    return comps == 1
+
+
+def _is_connected_cs(n_node, fr, to, keep):
+    g = sp.coo_matrix((np.ones(int(keep.sum())), (fr[keep], to[keep])), shape=(n_node, n_node))
+    nc, _ = csg.connected_components(g, directed=False)
+    return nc == 1
+
+
+def post_split_graph(grid, genome):
+    """Apply the split actions of ``genome`` (action ids, -1 = empty slot).
+
+    Returns (n_node, from', to', p' [T][n_node], slots) where each split slot j
+    adds node n_bus + j holding the assets of busbar B.  ``slots`` lists
+    (station, mask, n_assets) for the descriptors.
+    """
+    fr = grid.from_bus.astype(np.int64).copy()
+    to = grid.to_bus.astype(np.int64).copy()
+    n = grid.n_bus
+    acts = [int(a) for a in genome if int(a) >= 0]
+    seen = set()
+    slots = []
+    for a in acts:
+        if a >= grid.n_action:
+            raise TopologyError(f"unknown action id {a}")
+        s = int(grid.action_station[a])
+        if s in seen:
+            raise TopologyError(f"station {s} split twice")
+        seen.add(s)
+        slots.append((s, int(grid.action_mask[a]), int(grid.asset_offset[s + 1] - grid.asset_offset[s])))
+    n_node = n + len(slots)
+    p = np.zeros((grid.T, n_node))
+    p[:, :n] = grid.p
+    for j, (s, mask, m) in enumerate(slots):
+        bus = int(grid.station_bus[s])
+        node = n + j
+        assets = grid.station_assets(s)
+        for i in range(m):
+            if not (mask >> i) & 1:
+                continue
+            e = int(assets[i])
+            if e < 0:
+                p[:, node] = p[:, bus]
+                p[:, bus] = 0.0
+            elif fr[e] == bus:
+                fr[e] = node
+            elif to[e] == bus:
+                to[e] = node
+            else:
+                raise TopologyError("asset branch not incident to its station")
+    return n_node, fr, to, p, slots
+
+
+def solve_flows(n_node, fr, to, b, p, slack, skip=-1):
+    """DC loadflow: branch flows [T][E] for injections p [T][n_node]; branch
+    ``skip`` is out of service (flow 0).  The slack angle is fixed at 0 and the
+    slack absorbs any imbalance."""
+    E = len(fr)
+    keep = np.ones(E, dtype=bool)
+    if skip >= 0:
+        keep[skip] = False
+    f, t, w = fr[keep], to[keep], b[keep]
+    rows = np.concatenate([f, t, f, t])
+    cols = np.concatenate([f, t, t, f])
+    vals = np.concatenate([w, w, -w, -w])
+    L = sp.coo_matrix((vals, (rows, cols)), shape=(n_node, n_node)).tocsc()
+    idx = np.array([i for i in range(n_node) if i != slack])
+    Lr = L[idx][:, idx]
+    rhs = p[:, idx].T
+    if n_node <= DENSE_MAX:
+        th_r = np.linalg.solve(Lr.toarray(), rhs)
+    else:
+        th_r = spla.splu(Lr.tocsc()).solve(np.ascontiguousarray(rhs))
+    theta = np.zeros((n_node, p.shape[0]))
+    theta[idx] = th_r.reshape(len(idx), -1)
+    flows = b[:, None] * (theta[fr] - theta[to])
+    flows[~keep] = 0.0
+    return flows.T
+
+
+def base_flows(grid):
+    """Flows [T][E] of the unsplit grid."""
+    return solve_flows(grid.n_bus, grid.from_bus.astype(np.int64), grid.to_bus.astype(np.int64),
+                       grid.b, grid.p, grid.slack)
+
+
+def descriptors(grid, genome, d_split, d_moved):
+    """(lambda_s, moved assets, cell) of a genome."""
+    ns = 0
+    nm = 0
+    for a in genome:
+        a = int(a)
+        if a < 0:
+            continue
+        s = int(grid.action_station[a])
+        m = int(grid.asset_offset[s + 1] - grid.asset_offset[s])
+        on_b = bin(int(grid.action_mask[a])).count("1")
+        ns += 1
+        nm += min(on_b, m - on_b)
+    cell = min(ns, d_split - 1) * d_moved + min(nm, d_moved - 1)
+    return ns, nm, cell
+
+
+def evaluate(grid, genome, timesteps=None, outages=None, d_split=8, d_moved=8, want_flows=False):
+    """Evaluate one topology by brute force.
+
+    ``outages`` optionally restricts the outage list (indices into
+    ``grid.outages``) for sampled checks; the default is the full set.
+    Returns a dict with the islanding flags, f' (N-0 flows of monitored
+    branches) [T][E_mon], fmax [T][E_mon], the metrics, fitness and cell.
+    """
+    tsel = np.arange(grid.T) if timesteps is None else np.asarray(timesteps)
+    n_node, fr, to, p, _ = post_split_graph(grid, genome)
+    p = p[tsel]
+    ns, nm, cell = descriptors(grid, genome, d_split, d_moved)
+    mon = grid.monitored.astype(np.int64)
+    lim = grid.limit[mon]
+    res = dict(ns=ns, nm=nm, cell=cell)
+    if not is_connected_uf(n_node, fr, to):
+        res.update(island_base=True, island_any=False, n_islanded=0, fitness=-np.inf,
+                   lambda_f1=-np.inf)
+        return res
+    f_n0 = solve_flows(n_node, fr, to, grid.b, p, grid.slack)
+    fprime = f_n0[:, mon]
+    out_idx = np.arange(grid.outages.size) if outages is None else np.asarray(outages)
+    fmax = np.zeros_like(fprime)
+    n_isl = 0
+    per_outage = {} if want_flows else None
+    for oi in out_idx:
+        c = int(grid.outages[oi])
+        keep = np.ones(len(fr), dtype=bool)
+        keep[c] = False
+        if not _is_connected_cs(n_node, fr, to, keep):
+            n_isl += 1
+            continue
+        F = solve_flows(n_node, fr, to, grid.b, p, grid.slack, skip=c)[:, mon]
+        if want_flows:
+            per_outage[int(oi)] = F
+        fmax = np.maximum(fmax, np.abs(F))
+    over = np.maximum(fmax - lim[None, :], 0.0)
+    lam_o = float(over.sum())
+    lam_c = int((fmax > lim[None, :]).sum())
+    lam_c0 = int((np.abs(fprime) > lim[None, :]).sum())
+    maxload = float(np.max(np.maximum(np.abs(fprime), fmax) / lim[None, :]))
+    res.update(island_base=False, island_any=n_isl > 0, n_islanded=n_isl, fprime=fprime,
+               fmax=fmax, lambda_o=lam_o, lambda_c=lam_c, lambda_c0=lam_c0, maxload=maxload,
+               fitness=-(lam_o + maxload), lambda_f1=-(lam_o + 200.0 * lam_c0 + 50.0 * lam_c))
+    if want_flows:
+        res["per_outage"] = per_outage
+    return res
+
+
+def _eval_star(args):
+    grid, genome, kw = args
+    return evaluate(grid, genome, **kw)
+
+
+def evaluate_many(grid, genomes, processes=1, **kw):
+    """Evaluate several topologies, optionally across host processes (spawn)."""
+    jobs = [(grid, g, kw) for g in genomes]
+    if processes <= 1 or len(jobs) <= 1:
+        return [_eval_star(j) for j in jobs]
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(processes) as pool:
+        return pool.map(_eval_star, jobs, chunksize=1)

@@ -1,0 +1,235 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself:
+hand-derived closed forms (3-bus golden file), Kirchhoff's current and voltage
+laws, bridges found by an independent library (networkx), an independent FP64
+restatement of the PTDF/LODF/bus-split low-rank formulas, and the projection
+invariants of the flow-response matrix."""
+import numpy as np
+import networkx as nx
+import pytest
+
+from oracle import dcflow
+from synth import limits_from_flows, random_topologies
+from tests.gridcases import three_bus, small_grid, action_of
+
+
+def test_three_bus_closed_form():
+    g, d = three_bus()
+    base = d["cases"]["base"]
+    r = dcflow.evaluate(g, [-1], want_flows=True)
+    np.testing.assert_allclose(r["fprime"][0], base["fprime"], atol=1e-14)
+    for c, fl in base["outage_flows"].items():
+        np.testing.assert_allclose(r["per_outage"][int(c)][0], fl, atol=1e-14)
+    np.testing.assert_allclose(r["fmax"][0], base["fmax"], atol=1e-14)
+    assert r["n_islanded"] == base["n_islanded"]
+    assert r["lambda_o"] == pytest.approx(base["lambda_o"], abs=1e-14)
+    assert r["lambda_c"] == base["lambda_c"]
+    assert r["lambda_c0"] == base["lambda_c0"]
+    assert r["maxload"] == pytest.approx(base["maxload"], abs=1e-14)
+    assert r["fitness"] == pytest.approx(base["fitness"], abs=1e-14)
+    assert r["lambda_f1"] == pytest.approx(base["lambda_f1"], abs=1e-14)
+
+
+@pytest.mark.parametrize("case", ["split_branch_only", "split_branch_and_injection"])
+def test_three_bus_splits(case):
+    g, d = three_bus()
+    c = d["cases"][case]
+    a = action_of(g, 0, c["mask"])
+    r = dcflow.evaluate(g, [a])
+    assert not r["island_base"]
+    np.testing.assert_allclose(r["fprime"][0], c["fprime"], atol=1e-14)
+    assert r["n_islanded"] == c["n_islanded"]
+    assert r["island_any"]
+    # every outage islands: nothing enters the N-1 maximum
+    np.testing.assert_array_equal(r["fmax"], 0.0)
+
+
+def _kcl_kvl(n_node, fr, to, b, p, slack, flows, skip=-1):
+    E = len(fr)
+    net = np.zeros((p.shape[0], n_node))
+    for l in range(E):
+        if l == skip:
+            continue
+        net[:, fr[l]] += flows[:, l]
+        net[:, to[l]] -= flows[:, l]
+    others = [i for i in range(n_node) if i != slack]
+    np.testing.assert_allclose(net[:, others], p[:, others], atol=1e-9)
+    np.testing.assert_allclose(net.sum(axis=1), 0.0, atol=1e-9)
+    G = nx.Graph()
+    G.add_nodes_from(range(n_node))
+    for l in range(E):
+        if l != skip:
+            G.add_edge(int(fr[l]), int(to[l]), l=l)
+    for cyc in nx.cycle_basis(G):
+        s = np.zeros(p.shape[0])
+        for i in range(len(cyc)):
+            u, v = cyc[i], cyc[(i + 1) % len(cyc)]
+            l = G[u][v]["l"]
+            sign = 1.0 if (fr[l] == u and to[l] == v) else -1.0
+            s += sign * flows[:, l] / b[l]
+        np.testing.assert_allclose(s, 0.0, atol=1e-9)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_kirchhoff_laws_every_state(seed):
+    """KCL at every node (split busbars included) and KVL around every cycle,
+    in the N-0 state and in every non-islanding outage state."""
+    g = small_grid(seed)
+    topo = random_topologies(g, 4, seed=seed)
+    for gen in topo:
+        n_node, fr, to, p, _ = dcflow.post_split_graph(g, gen)
+        if not dcflow.is_connected_uf(n_node, fr, to):
+            continue
+        f = dcflow.solve_flows(n_node, fr, to, g.b, p, g.slack)
+        _kcl_kvl(n_node, fr, to, g.b, p, g.slack, f)
+        for c in range(len(fr)):
+            if not dcflow.is_connected_uf(n_node, fr, to, skip=c):
+                continue
+            F = dcflow.solve_flows(n_node, fr, to, g.b, p, g.slack, skip=c)
+            assert np.all(F[:, c] == 0.0)
+            _kcl_kvl(n_node, fr, to, g.b, p, g.slack, F, skip=c)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_islanding_matches_networkx_bridges(seed):
+    g = small_grid(seed)
+    g = g.with_limits(np.ones(g.n_branch))
+    topo = random_topologies(g, 6, seed=seed)
+    for gen in topo:
+        n_node, fr, to, p, _ = dcflow.post_split_graph(g, gen)
+        G = nx.Graph()
+        G.add_nodes_from(range(n_node))
+        for l in range(len(fr)):
+            G.add_edge(int(fr[l]), int(to[l]), l=l)
+        r = dcflow.evaluate(g, gen)
+        assert r["island_base"] == (not nx.is_connected(G))
+        if r["island_base"]:
+            continue
+        bridges = {G[u][v]["l"] for u, v in nx.bridges(G)}
+        n_br = sum(1 for c in g.outages if int(c) in bridges)
+        assert r["n_islanded"] == n_br
+
+
+def _ptdf_restatement(g):
+    """Independent dense FP64 statement of PTDF = D A X and N = I - D A X A^T."""
+    n, E = g.n_bus, g.n_branch
+    A = np.zeros((E, n))
+    A[np.arange(E), g.from_bus] = 1.0
+    A[np.arange(E), g.to_bus] = -1.0
+    D = np.diag(g.b)
+    idx = [i for i in range(n) if i != g.slack]
+    Br = (A.T @ D @ A)[np.ix_(idx, idx)]
+    X = np.zeros((n, n))
+    X[np.ix_(idx, idx)] = np.linalg.inv(Br)
+    M = D @ A @ X @ A.T
+    return A, D, X, M
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_flow_response_invariants(seed):
+    g = small_grid(seed)
+    A, D, X, M = _ptdf_restatement(g)
+    N = np.eye(g.n_branch) - M
+    np.testing.assert_allclose(M @ M, M, atol=1e-10)
+    assert np.trace(M) == pytest.approx(g.n_bus - 1, abs=1e-9)
+    ND = N @ D
+    np.testing.assert_allclose(ND, ND.T, atol=1e-9)
+    assert np.linalg.eigvalsh((ND + ND.T) / 2).min() > -1e-9
+    d = np.diag(N)
+    assert d.min() > -1e-12 and d.max() < 1 + 1e-12
+    # the oracle's own solve reproduces the M columns: unit transfer across c
+    for c in range(g.n_branch):
+        p = np.zeros((1, g.n_bus))
+        p[0, g.from_bus[c]] += 1.0
+        p[0, g.to_bus[c]] -= 1.0
+        f = dcflow.solve_flows(g.n_bus, g.from_bus.astype(np.int64), g.to_bus.astype(np.int64),
+                               g.b, p, g.slack)
+        np.testing.assert_allclose(f[0], M[:, c], atol=1e-10)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 5, 6])
+def test_low_rank_split_and_outage_formulas(seed):
+    """Brute force vs the rank-k bus-split update and the LODF outage formula,
+    restated here in dense FP64:  f' = f0 + W psi,  W = N D S,
+    psi = K^-1 (p_M - S^T f0),  K = S^T W,  N' = N - W K^-1 W^T D^-1,
+    F^(c) = f' - N'[:,c] f'_c / N'_cc, and N'_cc = 0 exactly for bridges."""
+    g = small_grid(seed)
+    f0 = dcflow.base_flows(g)
+    g = g.with_limits(limits_from_flows(f0[0], 2))
+    A, D, X, M = _ptdf_restatement(g)
+    N = np.eye(g.n_branch) - M
+    f0m = (D @ A @ X @ g.p.T).T
+    np.testing.assert_allclose(f0m, f0, atol=1e-10)
+    topo = random_topologies(g, 8, seed=seed)
+    for gen in topo:
+        acts = [a for a in gen if a >= 0]
+        k = len(acts)
+        S = np.zeros((g.n_branch, k))
+        pM = np.zeros((g.T, k))
+        for j, a in enumerate(acts):
+            s = g.action_station[a]
+            bus = g.station_bus[s]
+            mask = int(g.action_mask[a])
+            for i, e in enumerate(g.station_assets(s)):
+                if not (mask >> i) & 1:
+                    continue
+                if e < 0:
+                    pM[:, j] = g.p[:, bus]
+                else:
+                    S[e, j] = 1.0 if g.from_bus[e] == bus else -1.0
+        W = N @ D @ S
+        K = S.T @ W
+        r = dcflow.evaluate(g, gen, want_flows=True)
+        if r["island_base"]:
+            assert abs(np.linalg.det(K)) < 1e-8 * max(1.0, np.abs(K).max()) ** k
+            continue
+        psi = np.linalg.solve(K, (pM - f0 @ S).T)
+        fp = f0 + (W @ psi).T
+        np.testing.assert_allclose(r["fprime"], fp, atol=1e-9)
+        Np = N - W @ np.linalg.solve(K, W.T) @ np.diag(1.0 / g.b)
+        for c in range(g.n_branch):
+            if c in r["per_outage"]:
+                F = fp - np.outer(fp[:, c] / Np[c, c], Np[:, c])
+                np.testing.assert_allclose(r["per_outage"][c], F, atol=1e-8)
+            else:
+                assert abs(Np[c, c]) < 1e-9
+
+
+def test_metrics_follow_definitions_on_a_random_grid():
+    g = small_grid(7, T=3)
+    f0 = dcflow.base_flows(g)
+    g = g.with_limits(limits_from_flows(f0[0], 3))
+    gen = random_topologies(g, 1, seed=3)[0]
+    r = dcflow.evaluate(g, gen, want_flows=True)
+    assert not r["island_base"]
+    lim = g.limit
+    fm = np.zeros_like(r["fprime"])
+    for F in r["per_outage"].values():
+        fm = np.maximum(fm, np.abs(F))
+    np.testing.assert_array_equal(fm, r["fmax"])
+    lo = sum(max(fm[t, l] - lim[l], 0.0) for t in range(g.T) for l in range(g.n_branch))
+    assert r["lambda_o"] == pytest.approx(lo, rel=1e-12)
+    ml = max(max(abs(r["fprime"][t, l]), fm[t, l]) / lim[l] for t in range(g.T) for l in range(g.n_branch))
+    assert r["maxload"] == pytest.approx(ml, rel=1e-12)
+    assert r["fitness"] == pytest.approx(-(lo + ml), rel=1e-12)
+
+
+def test_descriptors_and_cell():
+    g, _ = three_bus()
+    a = action_of(g, 0, 2)   # busbar B = {branch 1->2}: 1 moved asset of 3
+    assert dcflow.descriptors(g, [a], 8, 8) == (1, 1, 9)
+    a = action_of(g, 0, 6)   # B = {branch, injection}: min(1, 2) = 1
+    assert dcflow.descriptors(g, [a], 8, 8) == (1, 1, 9)
+    assert dcflow.descriptors(g, [-1], 8, 8) == (0, 0, 0)
+    big = small_grid(2, n_station=4, k_max=3)
+    gen = random_topologies(big, 32, seed=9)
+    for row in gen:
+        ns, nm, cell = dcflow.descriptors(big, row, 2, 3)
+        assert ns == int((row >= 0).sum())
+        assert cell == min(ns, 1) * 3 + min(nm, 2)
+
+
+def test_duplicate_station_rejected():
+    g = small_grid(1)
+    a0 = int(g.action_offset[0])
+    with pytest.raises(dcflow.TopologyError):
+        dcflow.evaluate(g.with_limits(np.ones(g.n_branch)), [a0, a0 + 1, -1])
