@@ -1,0 +1,214 @@
+/*
+ * tto.h -- C ABI of the B300 DC N-1 topology evaluator and MapElites search.
+ *
+ * The library evaluates candidate switching topologies (substation bus splits,
+ * two-node operation) of a transmission grid by DC loadflow with full N-1
+ * contingency analysis (paper Sec. "DC-Optimizer": PTDF-based flows with
+ * low-rank topology updates), reduces each topology to the overload metrics of
+ * Sec. "Fitness function heuristics" and the MapElites descriptors of Sec.
+ * "Repertoire design", and runs the mutation and archive insert of Algorithms
+ * 1 and 3 on the device.
+ *
+ * Conventions for every call:
+ *   - return 0 (TTO_OK) on success, a negative TTO_E_* code otherwise; the
+ *     thread-local message of the last failure is tto_last_error();
+ *   - "host" pointers are read during the call only; "device" pointers are CUDA
+ *     device memory owned by the caller, accessed asynchronously on the given
+ *     stream (a cudaStream_t passed as void*; NULL = legacy default stream);
+ *   - there is no CPU fallback: without a usable CUDA device every call that
+ *     needs one returns TTO_E_CUDA.
+ */
+#ifndef TTO_H
+#define TTO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TTO_OK 0
+#define TTO_E_ARG (-1)          /* invalid argument or inconsistent input */
+#define TTO_E_DISCONNECTED (-2) /* the unsplit grid is not connected */
+#define TTO_E_CUDA (-3)         /* CUDA runtime failure or no device */
+#define TTO_E_NOMEM (-4)        /* host or device allocation failed */
+#define TTO_E_TOPOLOGY (-5)     /* a genome named an unknown action or split a station twice */
+#define TTO_E_TIMEOUT (-6)      /* a bounded device wait gave up */
+
+#define TTO_MAX_K 8        /* split slots per genome */
+#define TTO_MAX_T 32       /* timesteps per evaluation call */
+#define TTO_MAX_ASSETS 16  /* assets per splittable station */
+
+/* Precision of the low-rank term U V^T of the N-1 sweep (flows are FP32 and the
+ * split/outage denominators FP64 in every mode). */
+#define TTO_PREC_FP32 0    /* FP32 FMAs on the CUDA cores */
+#define TTO_PREC_BF16X3 1  /* tensor cores, BF16 hi/lo split (3 products), FP32 accumulate */
+#define TTO_PREC_BF16 2    /* tensor cores, single BF16 product, FP32 accumulate */
+
+#define TTO_FIT_WORKLOAD 0 /* fitness = -(lambda_o + max loading) */
+#define TTO_FIT_F1 1       /* fitness = lambda_f1 = -(lambda_o + 200 lambda_c0 + 50 lambda_c) */
+
+typedef struct tto_grid tto_grid;
+typedef struct tto_archive tto_archive;
+
+/* Grid description (all host pointers, copied by tto_grid_create).
+ * Branch l joins from[l] -> to[l] with susceptance b[l] > 0 (p.u.); flows are
+ * positive in the from->to direction.  p is [n_time][n_bus]; the slack bus
+ * absorbs the imbalance of each timestep.  limit[l] > 0 is the thermal limit.
+ * Stations: station s sits at bus station_bus[s] (not the slack) and owns the
+ * assets asset_branch[asset_offset[s] .. asset_offset[s+1]) -- a branch id
+ * incident to that bus, or -1 for the bus injection.  Actions: action a splits
+ * station action_station[a]; bit i of action_mask[a] puts asset i on busbar B
+ * (bit 0 must be clear; busbar B must hold at least one branch). */
+typedef struct {
+  int32_t n_bus;
+  int32_t n_branch;
+  const int32_t* from;
+  const int32_t* to;
+  const double* b;
+  int32_t slack;
+  int32_t n_time;
+  const double* p;
+  const double* limit;
+  int32_t n_monitored;
+  const int32_t* monitored;
+  int32_t n_outage;
+  const int32_t* outage;
+  int32_t n_station;
+  const int32_t* station_bus;
+  const int32_t* asset_offset;
+  const int32_t* asset_branch;
+  int32_t n_action;
+  const int32_t* action_station;
+  const uint32_t* action_mask;
+  int32_t k_max;   /* genome slots, 0 < k_max <= TTO_MAX_K */
+  int32_t device;  /* CUDA device ordinal */
+} tto_grid_desc;
+
+/* Options of one evaluation call. */
+typedef struct {
+  int32_t precision;     /* TTO_PREC_* */
+  int32_t fitness_kind;  /* TTO_FIT_* */
+  int32_t d_split;       /* archive extent over split stations (cell rows) */
+  int32_t d_moved;       /* archive extent over moved assets (cell columns) */
+} tto_eval_opts;
+
+/* Mutation parameters of Algorithm 1 (split part). */
+typedef struct {
+  double p_add, p_remove, p_change, p_identity;
+  double n_mut_mean;     /* Poisson mean of the number of mutation rounds */
+} tto_mut_params;
+
+/* tto_grid_create -- copy the grid, check it, and run the one-time FP64
+ * precompute: sparse LDL^T factorisation of the reduced susceptance matrix
+ * (slack removed), the flow-response columns N = I - D A X A^T for every outage
+ * and every branch that a split can move, the base flows f0 = D A X p for every
+ * timestep (Sec. "Importer": PTDF of the pre-optimisation topology), and their
+ * upload to the device.  *out owns all device copies.
+ * Errors: TTO_E_ARG (sizes, ids, masks, station at slack, ...),
+ * TTO_E_DISCONNECTED, TTO_E_CUDA, TTO_E_NOMEM. */
+int tto_grid_create(const tto_grid_desc* d, tto_grid** out);
+
+/* Release a grid and its device memory (NULL is accepted). */
+int tto_grid_destroy(tto_grid* g);
+
+/* Sizes of a created grid: n_branch, n_monitored, n_outage, n_time, k_max,
+ * n_action (any pointer may be NULL). */
+int tto_grid_info(const tto_grid* g, int32_t* n_branch, int32_t* n_monitored, int32_t* n_outage,
+                  int32_t* n_time, int32_t* k_max, int32_t* n_action);
+
+/* Copy the FP64 base flows f0 [n_time][n_branch] of the unsplit grid into the
+ * host buffer f0_host (the PTDF flows computed by tto_grid_create). */
+int tto_grid_base_flows(const tto_grid* g, double* f0_host);
+
+/* Replace the thermal limits (host [n_branch], all > 0). */
+int tto_grid_set_limits(tto_grid* g, const double* limit_host);
+
+/* Reserve evaluation workspace for batches of up to max_batch topologies and
+ * n_t timesteps so that later calls allocate nothing (needed before capturing
+ * evaluation calls in a CUDA graph). */
+int tto_grid_reserve(tto_grid* g, int32_t max_batch, int32_t n_t);
+
+/* tto_evaluate_batch -- exact DC N-1 evaluation of B topologies.
+ *   topo      device int32 [B][k_max]: action ids, -1 = empty slot;
+ *   timesteps host int32 [n_t] indices into the grid's timesteps (NULL = all);
+ *   fitness   device float [B]   (-inf when the split itself islands the grid);
+ *   desc      device int32 [B][2] (split stations, moved assets);
+ *   cell      device int32 [B]   archive cell of the descriptors;
+ *   island    device uint8 [B]   bit0: split islands the grid, bit1: some outage islands;
+ *   metrics   device float [B][4] (lambda_o, max loading, lambda_c, lambda_c0) or NULL;
+ *   fmax      device float [B][n_t][n_monitored] N-1 maximum |flow| or NULL.
+ * Per topology: rank-k bus-split update of the base flows (FP64 split matrix
+ * K and outage denominators N'_cc, islanding test N'_cc <= 1e-6), then a fused
+ * sweep over all (monitored branch, outage) pairs that never stores the
+ * post-contingency flows, reduced to the metrics of Sec. "Fitness function
+ * heuristics" (an outage that islands the split grid is skipped and counted).
+ * Asynchronous on stream.  A genome with an unknown action id or a repeated
+ * station is reported by the device; read it with tto_grid_sync_status. */
+int tto_evaluate_batch(tto_grid* g, const int32_t* topo, int32_t B, const int32_t* timesteps,
+                       int32_t n_t, const tto_eval_opts* opts, float* fitness, int32_t* desc,
+                       int32_t* cell, uint8_t* island, float* metrics, float* fmax, void* stream);
+
+/* Per-stage CUDA-event timing of evaluation calls, off by default.
+ * tto_grid_profile(g, 1) clears the record and times the next calls (at most
+ * 256); tto_grid_profile(g, 0) stops.  tto_grid_profile_read synchronises on
+ * the recorded events and returns, summed over the recorded calls, the
+ * milliseconds of the split update, the N-1 sweep and the metric reduction in
+ * ms_stage[0..2], and the number of calls in *n_calls. */
+int tto_grid_profile(tto_grid* g, int32_t enable);
+int tto_grid_profile_read(tto_grid* g, float* ms_stage, int32_t* n_calls);
+
+/* Synchronise the stream and return (then clear) the device status word:
+ * TTO_OK, TTO_E_TOPOLOGY or TTO_E_TIMEOUT. */
+int tto_grid_sync_status(tto_grid* g, void* stream);
+
+/* Archive of d_split x d_moved cells, one elite per cell, device resident.
+ * Starts empty. */
+int tto_archive_create(tto_grid* g, int32_t d_split, int32_t d_moved, tto_archive** out);
+int tto_archive_destroy(tto_archive* a);
+
+/* Copy the archive to host buffers: fitness [cells] (-inf = empty cell),
+ * genome [cells][k_max], filled [cells] (0/1).  Synchronous. */
+int tto_archive_export(const tto_archive* a, float* fitness, int32_t* genome, uint8_t* filled);
+/* Overwrite the archive from host buffers of the same layout. */
+int tto_archive_import(tto_archive* a, const float* fitness, const int32_t* genome,
+                       const uint8_t* filled);
+
+/* Scatter-insert B evaluated candidates (device arrays from
+ * tto_evaluate_batch) into the archive: per cell, the candidate with the
+ * highest fitness wins (lowest index on ties) and replaces the elite only if
+ * strictly better; non-finite fitness is skipped.  Equals a sequential
+ * in-order insert with strict '>' (Algorithm 3).  Asynchronous. */
+int tto_archive_insert(tto_archive* a, const int32_t* topo, int32_t B, const float* fitness,
+                       const int32_t* cell, void* stream);
+
+/* Propose B mutated genomes (device int32 [B][k_max]) from parents drawn
+ * uniformly over the filled cells, with Algorithm 1's split mutation driven by
+ * Philox4x32-10 keyed by seed and countered by (word block, candidate,
+ * iteration).  Deterministic given (archive, seed, iteration).  Errors:
+ * TTO_E_ARG if the archive is empty. */
+int tto_mapelites_propose(tto_archive* a, uint64_t seed, uint64_t iteration, int32_t B,
+                          const tto_mut_params* mp, int32_t* topo_out, void* stream);
+
+/* One full MapElites iteration on the device: propose B candidates, evaluate
+ * them exactly (tto_evaluate_batch with opts), insert them.  The candidates
+ * and their fitness stay in library workspace; topo_out / fitness_out
+ * (device, optional) receive copies.  Asynchronous. */
+int tto_mapelites_step(tto_archive* a, uint64_t seed, uint64_t iteration, int32_t B,
+                       const tto_mut_params* mp, const tto_eval_opts* opts, int32_t* topo_out,
+                       float* fitness_out, void* stream);
+
+/* The 4x32-bit Philox words of counter block `block` of candidate `cand` in
+ * `iteration` under `seed`, written to device uint32 [n][4] for blocks
+ * block .. block+n-1 (exposes the generator that drives the mutation). */
+int tto_philox_blocks(uint64_t seed, uint64_t iteration, uint32_t cand, uint32_t block, int32_t n,
+                      uint32_t* out, void* stream);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char* tto_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TTO_H */

@@ -225,3 +225,38 @@ def evaluate_many(grid, genomes, processes=1, **kw):
     import multiprocessing as mp
     with mp.get_context("spawn").Pool(processes) as pool:
         return pool.map(_eval_star, jobs, chunksize=1)
+
+
+def _eval_chunk(args):
+    grid, genome, chunk, kw = args
+    return evaluate(grid, genome, outages=chunk, **kw)
+
+
+def evaluate_parallel_outages(grid, genome, processes=8, **kw):
+    """Brute-force evaluation of one topology with its outage re-solves spread
+    over host processes (spawn); the per-process maxima are combined by max and
+    the metrics recomputed from the combined f^max with the same formulas as
+    :func:`evaluate`."""
+    import multiprocessing as mp
+    O = grid.outages.size
+    chunks = [c for c in np.array_split(np.arange(O), max(1, processes)) if c.size]
+    jobs = [(grid, genome, c, kw) for c in chunks]
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        parts = pool.map(_eval_chunk, jobs, chunksize=1)
+    r = dict(parts[0])
+    if r["island_base"]:
+        return r
+    fmax = parts[0]["fmax"]
+    for q in parts[1:]:
+        fmax = np.maximum(fmax, q["fmax"])
+    n_isl = sum(q["n_islanded"] for q in parts)
+    lim = grid.limit[grid.monitored.astype(np.int64)]
+    fprime = r["fprime"]
+    lam_o = float(np.maximum(fmax - lim[None, :], 0.0).sum())
+    lam_c = int((fmax > lim[None, :]).sum())
+    lam_c0 = int((np.abs(fprime) > lim[None, :]).sum())
+    maxload = float(np.max(np.maximum(np.abs(fprime), fmax) / lim[None, :]))
+    r.update(fmax=fmax, n_islanded=n_isl, island_any=n_isl > 0, lambda_o=lam_o, lambda_c=lam_c,
+             lambda_c0=lam_c0, maxload=maxload, fitness=-(lam_o + maxload),
+             lambda_f1=-(lam_o + 200.0 * lam_c0 + 50.0 * lam_c))
+    return r

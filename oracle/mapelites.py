@@ -12,7 +12,8 @@
   Add (the forced-change rule, applied to split slots because this genome has
   no disconnection slots).
 * Parent selection: uniform over the filled archive cells, in ascending cell
-  order (the paper does not state it).
+  order (the paper does not state it); an empty archive yields the unsplit
+  topology as parent (Algorithm 3 initialises the repertoire with it).
 * Archive insert: Algorithm 3's sorted insert, read as one elite per cell and a
   candidate replacing it only when strictly better, candidates taken in batch
   order.
@@ -149,14 +150,19 @@ def mutate(parent, tab, ws, probs=DEFAULT_PROBS, mean=2.0):
     return np.array(g, dtype=np.int32)
 
 
-def propose(archive, tab, seed, iteration, B, probs=DEFAULT_PROBS, mean=2.0):
-    """B mutated genomes from parents drawn uniformly over filled cells."""
+def propose(archive, tab, seed, iteration, B, k_max, probs=DEFAULT_PROBS, mean=2.0):
+    """B mutated genomes from parents drawn uniformly over filled cells (the
+    parent word is drawn even when the archive is empty)."""
     filled = sorted(archive.elites)
     out = []
     for cand in range(B):
         ws = WordStream(seed, iteration, cand)
-        cell = filled[uniform_index(ws.next(), len(filled))]
-        out.append(mutate(archive.elites[cell][1], tab, ws, probs, mean))
+        w = ws.next()
+        if filled:
+            parent = archive.elites[filled[uniform_index(w, len(filled))]][1]
+        else:  # empty archive: mutate the pre-optimisation (unsplit) topology
+            parent = np.full(k_max, -1, dtype=np.int32)
+        out.append(mutate(parent, tab, ws, probs, mean))
     return np.stack(out)
 
 

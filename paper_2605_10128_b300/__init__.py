@@ -1,0 +1,160 @@
+"""B300-native DC N-1 topology evaluation and MapElites search.
+
+Thin Python layer over the C ABI of ``libtto.so`` (``include/tto.h``).  Torch is
+used only for device memory and streams; all computation runs in the library's
+CUDA kernels.  There is no CPU fallback: without the built library or a CUDA
+device every call raises.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _lib
+from ._lib import (  # noqa: F401
+    TTOError, PREC_FP32, PREC_BF16X3, PREC_BF16, FIT_WORKLOAD, FIT_F1,
+)
+
+DEFAULT_MUTATION = (0.2, 0.2, 0.5, 0.1, 2.0)  # p_add, p_remove, p_change, p_identity, N_mutmean
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise TTOError(_lib.TTO_E_CUDA, "no CUDA device")
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+class Grid:
+    """A grid resident on the device, created from a grid description (any
+    object with the fields of ``synth.SynthGrid``)."""
+
+    def __init__(self, desc, device: int = 0):
+        _torch()
+        self.device = device
+        self._h = _lib.tto_grid_create(desc, device)
+        info = _lib.tto_grid_info(self._h)
+        self.n_branch = info["n_branch"]
+        self.n_monitored = info["n_monitored"]
+        self.n_outage = info["n_outage"]
+        self.n_time = info["n_time"]
+        self.k_max = info["k_max"]
+        self.n_action = info["n_action"]
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None:
+            _lib.tto_grid_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def base_flows(self) -> np.ndarray:
+        return _lib.tto_grid_base_flows(self._h, self.n_time, self.n_branch)
+
+    def set_limits(self, limit):
+        _lib.tto_grid_set_limits(self._h, limit)
+
+    def reserve(self, max_batch: int, n_t: int | None = None):
+        _lib.tto_grid_reserve(self._h, max_batch, self.n_time if n_t is None else n_t)
+
+    def evaluate(self, topo, timesteps=None, precision=PREC_FP32, fitness_kind=FIT_WORKLOAD,
+                 d_split=8, d_moved=8, metrics=False, fmax=False, stream=None, out=None):
+        """Exact N-1 evaluation of ``topo`` (CUDA int32 tensor [B][k_max]).
+        Returns a dict of CUDA tensors: fitness, desc, cell, island and, when
+        asked, metrics [B][4] and fmax [B][n_t][n_monitored]."""
+        torch = _torch()
+        B = int(topo.shape[0])
+        if topo.dtype != torch.int32 or not topo.is_cuda or topo.shape[1] != self.k_max:
+            raise TTOError(_lib.TTO_E_ARG, "topo must be a CUDA int32 tensor [B][k_max]")
+        topo = topo.contiguous()
+        n_t = self.n_time if timesteps is None else len(timesteps)
+        dev = topo.device
+        if out is None:
+            out = dict(fitness=torch.empty(B, dtype=torch.float32, device=dev),
+                       desc=torch.empty(B, 2, dtype=torch.int32, device=dev),
+                       cell=torch.empty(B, dtype=torch.int32, device=dev),
+                       island=torch.empty(B, dtype=torch.uint8, device=dev))
+            if metrics:
+                out["metrics"] = torch.empty(B, 4, dtype=torch.float32, device=dev)
+            if fmax:
+                out["fmax"] = torch.empty(B, n_t, self.n_monitored, dtype=torch.float32, device=dev)
+        o = _lib.EvalOpts(precision, fitness_kind, d_split, d_moved)
+        _lib.tto_evaluate_batch(self._h, topo, B, timesteps, o, out["fitness"], out.get("desc"),
+                                out.get("cell"), out.get("island"), out.get("metrics"),
+                                out.get("fmax"), _stream(stream))
+        out["_topo"] = topo
+        return out
+
+    def sync_status(self, stream=None):
+        _lib.tto_grid_sync_status(self._h, _stream(stream))
+
+    def profile(self, enable=True):
+        """Start (clearing the record) or stop per-stage event timing."""
+        _lib.tto_grid_profile(self._h, enable)
+
+    def profile_read(self):
+        """([split update ms, sweep ms, reduction ms] summed, number of calls)."""
+        return _lib.tto_grid_profile_read(self._h)
+
+
+class Archive:
+    """Device-resident MapElites archive (one elite per cell)."""
+
+    def __init__(self, grid: Grid, d_split: int, d_moved: int):
+        self.grid = grid
+        self.d_split = d_split
+        self.d_moved = d_moved
+        self.cells = d_split * d_moved
+        self._h = _lib.tto_archive_create(grid.handle, d_split, d_moved)
+
+    def close(self):
+        if self._h is not None:
+            _lib.tto_archive_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def export(self):
+        return _lib.tto_archive_export(self._h, self.cells, self.grid.k_max)
+
+    def load(self, fitness, genome, filled):
+        _lib.tto_archive_import(self._h, fitness, genome, filled)
+
+    def insert(self, topo, fitness, cell, stream=None):
+        _lib.tto_archive_insert(self._h, topo, int(topo.shape[0]), fitness, cell, _stream(stream))
+
+    def propose(self, seed, iteration, B, mutation=DEFAULT_MUTATION, stream=None):
+        torch = _torch()
+        out = torch.empty(B, self.grid.k_max, dtype=torch.int32, device=f"cuda:{self.grid.device}")
+        _lib.tto_mapelites_propose(self._h, seed, iteration, B, mutation, out, _stream(stream))
+        return out
+
+    def step(self, seed, iteration, B, mutation=DEFAULT_MUTATION, precision=PREC_FP32,
+             fitness_kind=FIT_WORKLOAD, topo_out=None, fitness_out=None, stream=None):
+        o = _lib.EvalOpts(precision, fitness_kind, self.d_split, self.d_moved)
+        _lib.tto_mapelites_step(self._h, seed, iteration, B, mutation, o, topo_out, fitness_out,
+                                _stream(stream))
+
+
+def philox_blocks(seed, iteration, cand, block, n, stream=None):
+    torch = _torch()
+    out = torch.empty(n, 4, dtype=torch.int32, device="cuda")
+    _lib.tto_philox_blocks(seed, iteration, cand, block, n, out, _stream(stream))
+    return out

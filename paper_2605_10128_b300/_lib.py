@@ -1,0 +1,278 @@
+"""ctypes binding of libtto.so: one Python function per C entry point, same
+names, argument marshalling only (every step of the computation runs in the
+library's CUDA kernels).  Device buffers are torch CUDA tensors; their
+addresses are passed as plain pointers together with the current stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtto.so")
+
+TTO_OK = 0
+TTO_E_ARG = -1
+TTO_E_DISCONNECTED = -2
+TTO_E_CUDA = -3
+TTO_E_NOMEM = -4
+TTO_E_TOPOLOGY = -5
+TTO_E_TIMEOUT = -6
+PREC_FP32, PREC_BF16X3, PREC_BF16 = 0, 1, 2
+FIT_WORKLOAD, FIT_F1 = 0, 1
+
+_i32p = C.POINTER(C.c_int32)
+_u32p = C.POINTER(C.c_uint32)
+_f64p = C.POINTER(C.c_double)
+_vp = C.c_void_p
+
+
+class TTOError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"tto error {code}: {msg}")
+        self.code = code
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("n_bus", C.c_int32), ("n_branch", C.c_int32), ("from_", _i32p), ("to", _i32p),
+                ("b", _f64p), ("slack", C.c_int32), ("n_time", C.c_int32), ("p", _f64p),
+                ("limit", _f64p), ("n_monitored", C.c_int32), ("monitored", _i32p),
+                ("n_outage", C.c_int32), ("outage", _i32p), ("n_station", C.c_int32),
+                ("station_bus", _i32p), ("asset_offset", _i32p), ("asset_branch", _i32p),
+                ("n_action", C.c_int32), ("action_station", _i32p), ("action_mask", _u32p),
+                ("k_max", C.c_int32), ("device", C.c_int32)]
+
+
+class EvalOpts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("fitness_kind", C.c_int32), ("d_split", C.c_int32),
+                ("d_moved", C.c_int32)]
+
+
+class MutParams(C.Structure):
+    _fields_ = [("p_add", C.c_double), ("p_remove", C.c_double), ("p_change", C.c_double),
+                ("p_identity", C.c_double), ("n_mut_mean", C.c_double)]
+
+
+_lib = None
+
+_SIGS = {
+    "tto_grid_create": ([C.POINTER(GridDesc), C.POINTER(_vp)], C.c_int),
+    "tto_grid_destroy": ([_vp], C.c_int),
+    "tto_grid_info": ([_vp, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p], C.c_int),
+    "tto_grid_base_flows": ([_vp, _f64p], C.c_int),
+    "tto_grid_set_limits": ([_vp, _f64p], C.c_int),
+    "tto_grid_reserve": ([_vp, C.c_int32, C.c_int32], C.c_int),
+    "tto_evaluate_batch": ([_vp, _vp, C.c_int32, _i32p, C.c_int32, C.POINTER(EvalOpts), _vp, _vp,
+                            _vp, _vp, _vp, _vp, _vp], C.c_int),
+    "tto_grid_sync_status": ([_vp, _vp], C.c_int),
+    "tto_grid_profile": ([_vp, C.c_int32], C.c_int),
+    "tto_grid_profile_read": ([_vp, C.POINTER(C.c_float), _i32p], C.c_int),
+    "tto_archive_create": ([_vp, C.c_int32, C.c_int32, C.POINTER(_vp)], C.c_int),
+    "tto_archive_destroy": ([_vp], C.c_int),
+    "tto_archive_export": ([_vp, _vp, _vp, _vp], C.c_int),
+    "tto_archive_import": ([_vp, _vp, _vp, _vp], C.c_int),
+    "tto_archive_insert": ([_vp, _vp, C.c_int32, _vp, _vp, _vp], C.c_int),
+    "tto_mapelites_propose": ([_vp, C.c_uint64, C.c_uint64, C.c_int32, C.POINTER(MutParams), _vp,
+                               _vp], C.c_int),
+    "tto_mapelites_step": ([_vp, C.c_uint64, C.c_uint64, C.c_int32, C.POINTER(MutParams),
+                            C.POINTER(EvalOpts), _vp, _vp, _vp], C.c_int),
+    "tto_philox_blocks": ([C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_int32, _vp, _vp],
+                          C.c_int),
+    "tto_last_error": ([], C.c_char_p),
+}
+
+
+def lib():
+    """The loaded library; raises if it has not been built (there is no
+    fallback implementation)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -m paper_2605_10128_b300.build`")
+        h = C.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(h, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = h
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def check(rc):
+    if rc != TTO_OK:
+        raise TTOError(rc, lib().tto_last_error().decode())
+    return rc
+
+
+def _ptr(arr, ctype):
+    return arr.ctypes.data_as(C.POINTER(ctype))
+
+
+def tto_grid_create(grid, device=0):
+    """Create a library grid from an object with the fields of a grid
+    description (see synth.SynthGrid); returns (handle, keepalive)."""
+    keep = dict(
+        fr=np.ascontiguousarray(grid.from_bus, dtype=np.int32),
+        to=np.ascontiguousarray(grid.to_bus, dtype=np.int32),
+        b=np.ascontiguousarray(grid.b, dtype=np.float64),
+        p=np.ascontiguousarray(grid.p, dtype=np.float64),
+        lim=np.ascontiguousarray(grid.limit if grid.limit is not None else np.ones(len(grid.b)),
+                                 dtype=np.float64),
+        mon=np.ascontiguousarray(grid.monitored, dtype=np.int32),
+        out=np.ascontiguousarray(grid.outages, dtype=np.int32),
+        sb=np.ascontiguousarray(grid.station_bus, dtype=np.int32),
+        ao=np.ascontiguousarray(grid.asset_offset, dtype=np.int32),
+        ab=np.ascontiguousarray(grid.asset_branch, dtype=np.int32),
+        ast=np.ascontiguousarray(grid.action_station, dtype=np.int32),
+        am=np.ascontiguousarray(grid.action_mask, dtype=np.uint32),
+    )
+    d = GridDesc()
+    d.n_bus = int(grid.n_bus)
+    d.n_branch = int(keep["fr"].size)
+    d.from_ = _ptr(keep["fr"], C.c_int32)
+    d.to = _ptr(keep["to"], C.c_int32)
+    d.b = _ptr(keep["b"], C.c_double)
+    d.slack = int(grid.slack)
+    d.n_time = int(keep["p"].shape[0])
+    d.p = _ptr(keep["p"], C.c_double)
+    d.limit = _ptr(keep["lim"], C.c_double)
+    d.n_monitored = int(keep["mon"].size)
+    d.monitored = _ptr(keep["mon"], C.c_int32)
+    d.n_outage = int(keep["out"].size)
+    d.outage = _ptr(keep["out"], C.c_int32)
+    d.n_station = int(keep["sb"].size)
+    d.station_bus = _ptr(keep["sb"], C.c_int32)
+    d.asset_offset = _ptr(keep["ao"], C.c_int32)
+    d.asset_branch = _ptr(keep["ab"], C.c_int32)
+    d.n_action = int(keep["ast"].size)
+    d.action_station = _ptr(keep["ast"], C.c_int32)
+    d.action_mask = _ptr(keep["am"], C.c_uint32)
+    d.k_max = int(grid.k_max)
+    d.device = int(device)
+    h = _vp()
+    check(lib().tto_grid_create(C.byref(d), C.byref(h)))
+    return h
+
+
+def tto_grid_destroy(h):
+    return check(lib().tto_grid_destroy(h))
+
+
+def tto_grid_info(h):
+    v = [C.c_int32() for _ in range(6)]
+    check(lib().tto_grid_info(h, *[C.byref(x) for x in v]))
+    keys = ["n_branch", "n_monitored", "n_outage", "n_time", "k_max", "n_action"]
+    return {k: x.value for k, x in zip(keys, v)}
+
+
+def tto_grid_base_flows(h, n_time, n_branch):
+    f0 = np.zeros((n_time, n_branch), dtype=np.float64)
+    check(lib().tto_grid_base_flows(h, _ptr(f0, C.c_double)))
+    return f0
+
+
+def tto_grid_set_limits(h, limit):
+    lim = np.ascontiguousarray(limit, dtype=np.float64)
+    return check(lib().tto_grid_set_limits(h, _ptr(lim, C.c_double)))
+
+
+def tto_grid_reserve(h, max_batch, n_t):
+    return check(lib().tto_grid_reserve(h, int(max_batch), int(n_t)))
+
+
+def _dp(t):
+    return None if t is None else _vp(t.data_ptr())
+
+
+def tto_evaluate_batch(h, topo, B, timesteps, opts, fitness, desc, cell, island, metrics, fmax,
+                       stream):
+    ts = None
+    n_t = 0
+    if timesteps is not None:
+        ts_arr = np.ascontiguousarray(timesteps, dtype=np.int32)
+        ts = _ptr(ts_arr, C.c_int32)
+        n_t = int(ts_arr.size)
+    return check(lib().tto_evaluate_batch(h, _dp(topo), int(B), ts, n_t, C.byref(opts),
+                                          _dp(fitness), _dp(desc), _dp(cell), _dp(island),
+                                          _dp(metrics), _dp(fmax), _vp(stream)))
+
+
+def tto_grid_sync_status(h, stream):
+    return check(lib().tto_grid_sync_status(h, _vp(stream)))
+
+
+def tto_grid_profile(h, enable):
+    return check(lib().tto_grid_profile(h, int(enable)))
+
+
+def tto_grid_profile_read(h):
+    ms = (C.c_float * 3)()
+    n = C.c_int32()
+    check(lib().tto_grid_profile_read(h, ms, C.byref(n)))
+    return [ms[0], ms[1], ms[2]], n.value
+
+
+def tto_archive_create(grid_h, d_split, d_moved):
+    a = _vp()
+    check(lib().tto_archive_create(grid_h, int(d_split), int(d_moved), C.byref(a)))
+    return a
+
+
+def tto_archive_destroy(a):
+    return check(lib().tto_archive_destroy(a))
+
+
+def tto_archive_export(a, cells, k_max):
+    fit = np.zeros(cells, dtype=np.float32)
+    gen = np.zeros((cells, k_max), dtype=np.int32)
+    filled = np.zeros(cells, dtype=np.uint8)
+    check(lib().tto_archive_export(a, fit.ctypes.data, gen.ctypes.data, filled.ctypes.data))
+    return fit, gen, filled
+
+
+def tto_archive_import(a, fit, gen, filled):
+    fit = np.ascontiguousarray(fit, dtype=np.float32)
+    gen = np.ascontiguousarray(gen, dtype=np.int32)
+    filled = np.ascontiguousarray(filled, dtype=np.uint8)
+    return check(lib().tto_archive_import(a, fit.ctypes.data, gen.ctypes.data, filled.ctypes.data))
+
+
+def tto_archive_insert(a, topo, B, fitness, cell, stream):
+    return check(lib().tto_archive_insert(a, _dp(topo), int(B), _dp(fitness), _dp(cell),
+                                          _vp(stream)))
+
+
+def _mut(mp):
+    m = MutParams()
+    m.p_add, m.p_remove, m.p_change, m.p_identity = mp[0], mp[1], mp[2], mp[3]
+    m.n_mut_mean = mp[4]
+    return m
+
+
+def tto_mapelites_propose(a, seed, iteration, B, mut, topo_out, stream):
+    m = _mut(mut)
+    return check(lib().tto_mapelites_propose(a, int(seed), int(iteration), int(B), C.byref(m),
+                                             _dp(topo_out), _vp(stream)))
+
+
+def tto_mapelites_step(a, seed, iteration, B, mut, opts, topo_out, fitness_out, stream):
+    m = _mut(mut)
+    return check(lib().tto_mapelites_step(a, int(seed), int(iteration), int(B), C.byref(m),
+                                          C.byref(opts), _dp(topo_out), _dp(fitness_out),
+                                          _vp(stream)))
+
+
+def tto_philox_blocks(seed, iteration, cand, block, n, out, stream):
+    return check(lib().tto_philox_blocks(int(seed), int(iteration), int(cand), int(block), int(n),
+                                         _dp(out), _vp(stream)))
+
+
+def tto_last_error():
+    return lib().tto_last_error().decode()

@@ -1,0 +1,499 @@
+// Exact DC N-1 evaluation of a batch of split topologies.
+//
+// Three kernels per call, all on the caller's stream:
+//  1. split_update_kernel (one CTA per topology): decodes the genome into the
+//     moved branch ends S (E x k, +-1) and moved injections, forms the split
+//     matrix K = S^T N D S in FP64, factorises it (a pivot at or below
+//     1e-6 * the moved susceptance marks a split that islands the grid), and
+//     writes per topology
+//        f'[t] = f0[t] + W psi[t],  psi[t] = K^-1 (p_M[t] - S^T f0[t]),  W = N D S,
+//        U = W K^-1 (monitored rows),  V_c = W_c / b_c (outage rows),
+//        g_c[t] = f'_c[t] / N'_cc  with  N'_cc = N_cc - U_c . V_c  in FP64
+//     and g = NaN for an outage that islands the split grid (N'_cc <= 1e-6).
+//     This is the bus split written as a phase shift on the moved branch ends
+//     plus KCL at the new busbar: post-split flow responses are
+//     N' = N - U V^T, the low-rank topology update of Sec. "DC-Optimizer".
+//  2. the N-1 sweep (sweep_*.cu): for every (monitored l, outage c, t)
+//        F = f'_l[t] - (N_lc - U_l . V_c) g_c[t],   fmax_l[t] = max_c |F|
+//     (the LODF outage formula on the split grid), reduced on the fly to the
+//     overload metrics; F is never stored.  fmaxf ignores a NaN operand, so
+//     islanding outages drop out of the maximum for free.
+//  3. fitness_kernel: fixed-order reduction of the per-row-tile partial
+//     metrics into lambda_o, lambda_c, max loading and the fitness, plus the
+//     descriptors and archive cell.
+#include <math.h>
+#include <stdio.h>
+
+#include "sweep.cuh"
+#include "tto_internal.h"
+
+namespace tto {
+
+// ---------------------------------------------------------------- split update
+__global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x;
+  __shared__ int s_k, s_island, s_ns, s_nm;
+  __shared__ int s_slot[TTO_MAX_K + 1];
+  __shared__ int s_e[kMaxMoved];
+  __shared__ double s_sign[kMaxMoved];
+  __shared__ double s_coef[kMaxMoved];
+  __shared__ const double* s_col[kMaxMoved];
+  __shared__ int s_injbus[TTO_MAX_K];
+  __shared__ double s_K[TTO_MAX_K][TTO_MAX_K];
+  __shared__ double s_Ki[TTO_MAX_K][TTO_MAX_K];
+  __shared__ double s_rhs[TTO_MAX_T][TTO_MAX_K];
+  __shared__ double s_psi[TTO_MAX_T][TTO_MAX_K];
+  __shared__ double s_sb[TTO_MAX_K];
+  __shared__ int s_cnt_c0, s_cnt_isl;
+
+  if (tid == 0) {
+    int k = 0, ne = 0, bad = 0, ns = 0, nm = 0;
+    int stations[TTO_MAX_K];
+    s_slot[0] = 0;
+    for (int j = 0; j < a.k_max; ++j) {
+      int act = a.topo[(size_t)b * a.k_max + j];
+      if (act < 0) continue;
+      if (act >= a.A) {
+        bad = 1;
+        break;
+      }
+      int st = a.act_st[act];
+      for (int q = 0; q < k; ++q)
+        if (stations[q] == st) bad = 1;
+      if (bad) break;
+      stations[k] = st;
+      uint32_t mask = a.act_mask[act];
+      int bus = a.station_bus[st];
+      int a0 = a.asset_off[st], m = a.asset_off[st + 1] - a0;
+      int onb = __popc(mask);
+      ++ns;
+      nm += min(onb, m - onb);
+      s_injbus[k] = -1;
+      for (int i = 0; i < m; ++i) {
+        if (!((mask >> i) & 1u)) continue;
+        int e = a.asset_br[a0 + i];
+        if (e < 0) {
+          s_injbus[k] = bus;
+          continue;
+        }
+        double sg = (a.from[e] == bus) ? 1.0 : -1.0;
+        s_e[ne] = e;
+        s_sign[ne] = sg;
+        s_coef[ne] = sg * a.b[e];
+        s_col[ne] = a.Nsw + (size_t)a.swcol[e] * a.E;
+        ++ne;
+      }
+      ++k;
+      s_slot[k] = ne;
+    }
+    s_k = bad ? 0 : k;
+    s_ns = ns;
+    s_nm = nm;
+    s_island = bad;
+    s_cnt_c0 = 0;
+    s_cnt_isl = 0;
+    if (bad) atomicExch(a.status, TTO_E_TOPOLOGY);
+  }
+  __syncthreads();
+  const int k = s_k;
+  const int nt = a.n_t;
+  // K = S^T W, rhs = p_M - S^T f0 (sequential sums: deterministic)
+  if (tid < k * k) {
+    int i = tid / k, j = tid % k;
+    double acc = 0.0;
+    for (int q = s_slot[i]; q < s_slot[i + 1]; ++q) {
+      double w = 0.0;
+      for (int r = s_slot[j]; r < s_slot[j + 1]; ++r) w += s_coef[r] * s_col[r][s_e[q]];
+      acc += s_sign[q] * w;
+    }
+    s_K[i][j] = acc;
+  }
+  if (tid < k * nt) {
+    int j = tid / nt, t = tid % nt;
+    int tt = a.tsel[t];
+    double st = 0.0;
+    for (int q = s_slot[j]; q < s_slot[j + 1]; ++q) st += s_sign[q] * a.f0[(size_t)tt * a.E + s_e[q]];
+    double pm = s_injbus[j] >= 0 ? a.p[(size_t)tt * a.n_bus + s_injbus[j]] : 0.0;
+    s_rhs[t][j] = pm - st;
+  }
+  if (tid < k) {
+    double sb = 0.0;
+    for (int q = s_slot[tid]; q < s_slot[tid + 1]; ++q) sb += a.b[s_e[q]];
+    s_sb[tid] = sb;
+  }
+  __syncthreads();
+  if (tid == 0 && k > 0) {
+    // LDL^T of the SPD split matrix; a vanishing pivot means the split islands
+    double L[TTO_MAX_K][TTO_MAX_K], D[TTO_MAX_K];
+    int isl = 0;
+    for (int j = 0; j < k; ++j) {
+      double d = s_K[j][j];
+      for (int q = 0; q < j; ++q) d -= L[j][q] * L[j][q] * D[q];
+      D[j] = d;
+      if (!(d > kIslandTol * s_sb[j])) {
+        isl = 1;
+        break;
+      }
+      for (int i = j + 1; i < k; ++i) {
+        double v = s_K[i][j];
+        for (int q = 0; q < j; ++q) v -= L[i][q] * L[j][q] * D[q];
+        L[i][j] = v / d;
+      }
+      L[j][j] = 1.0;
+    }
+    s_island = isl;
+    if (!isl) {
+      for (int c = 0; c < k; ++c) {
+        double x[TTO_MAX_K];
+        for (int i = 0; i < k; ++i) {
+          double v = (i == c) ? 1.0 : 0.0;
+          for (int q = 0; q < i; ++q) v -= L[i][q] * x[q];
+          x[i] = v;
+        }
+        for (int i = 0; i < k; ++i) x[i] /= D[i];
+        for (int i = k - 1; i >= 0; --i) {
+          double v = x[i];
+          for (int q = i + 1; q < k; ++q) v -= L[q][i] * x[q];
+          x[i] = v;
+        }
+        for (int i = 0; i < k; ++i) s_Ki[i][c] = x[i];
+      }
+    }
+  }
+  __syncthreads();
+  const bool dead = s_island != 0;
+  if (!dead && tid < k * nt) {
+    int j = tid / nt, t = tid % nt;
+    double v = 0.0;
+    for (int q = 0; q < k; ++q) v += s_Ki[j][q] * s_rhs[t][q];
+    s_psi[t][j] = v;
+  }
+  __syncthreads();
+
+  const int KP = a.KP, TT = a.TT;
+  const float qnan = __int_as_float(0x7fc00000);
+  int c0cnt = 0;
+  // monitored rows: f', U
+  for (int l = tid; l < a.E_mon_pad; l += blockDim.x) {
+    const int lr = min(l, a.E_mon - 1);
+    const int e = a.mon[lr];
+    float* Urow = a.U + ((size_t)b * a.E_mon_pad + l) * KP;
+    if (dead) {
+      for (int j = 0; j < KP; ++j) Urow[j] = 0.f;
+      for (int t = 0; t < TT; ++t) a.fp[((size_t)b * TT + t) * a.E_mon_pad + l] = 0.f;
+      continue;
+    }
+    double W[TTO_MAX_K];
+    for (int j = 0; j < k; ++j) {
+      double w = 0.0;
+      for (int q = s_slot[j]; q < s_slot[j + 1]; ++q) w += s_coef[q] * s_col[q][e];
+      W[j] = w;
+    }
+    for (int jj = 0; jj < KP; ++jj) {
+      double u = 0.0;
+      if (jj < k)
+        for (int j = 0; j < k; ++j) u += W[j] * s_Ki[j][jj];
+      Urow[jj] = (float)u;
+    }
+    const float lim = a.lim[lr];
+    for (int t = 0; t < TT; ++t) {
+      float fv = 0.f;
+      if (t < nt) {
+        double f = a.f0[(size_t)a.tsel[t] * a.E + e];
+        for (int j = 0; j < k; ++j) f += W[j] * s_psi[t][j];
+        fv = (float)f;
+        if (l < a.E_mon && fabsf(fv) > lim) ++c0cnt;
+      }
+      a.fp[((size_t)b * TT + t) * a.E_mon_pad + l] = fv;
+    }
+  }
+  // outage rows: V, g, islanding of each outage
+  int islcnt = 0;
+  for (int c = tid; c < a.O_pad; c += blockDim.x) {
+    const int cr = min(c, a.O - 1);
+    const int e = a.out[cr];
+    float* Vrow = a.V + ((size_t)b * a.O_pad + c) * KP;
+    float* grow = a.gg + ((size_t)b * a.O_pad + c) * TT;
+    if (dead) {
+      for (int j = 0; j < KP; ++j) Vrow[j] = 0.f;
+      for (int t = 0; t < TT; ++t) grow[t] = t < nt ? qnan : 0.f;
+      continue;
+    }
+    double W[TTO_MAX_K];
+    for (int j = 0; j < k; ++j) {
+      double w = 0.0;
+      for (int q = s_slot[j]; q < s_slot[j + 1]; ++q) w += s_coef[q] * s_col[q][e];
+      W[j] = w;
+    }
+    const double be = a.b[e];
+    double npcc = a.Ncc[cr];
+    for (int jj = 0; jj < k; ++jj) {
+      double u = 0.0;
+      for (int j = 0; j < k; ++j) u += W[j] * s_Ki[j][jj];
+      npcc -= u * (W[jj] / be);
+    }
+    for (int jj = 0; jj < KP; ++jj) Vrow[jj] = jj < k ? (float)(W[jj] / be) : 0.f;
+    const bool isl = !(npcc > kIslandTol);
+    if (isl && c < a.O) ++islcnt;
+    for (int t = 0; t < TT; ++t) {
+      float gv = 0.f;
+      if (t < nt) {
+        if (isl) {
+          gv = qnan;
+        } else {
+          double f = a.f0[(size_t)a.tsel[t] * a.E + e];
+          for (int j = 0; j < k; ++j) f += W[j] * s_psi[t][j];
+          gv = (float)(f / npcc);
+        }
+      }
+      grow[t] = gv;
+    }
+  }
+  if (c0cnt) atomicAdd(&s_cnt_c0, c0cnt);
+  if (islcnt) atomicAdd(&s_cnt_isl, islcnt);
+  __syncthreads();
+  if (tid == 0) {
+    TopoInfo inf;
+    inf.island_base = s_island;
+    inf.n_islanded = dead ? 0 : s_cnt_isl;
+    inf.ns = s_ns;
+    inf.nm = s_nm;
+    inf.lambda_c0 = dead ? 0.f : (float)s_cnt_c0;
+    inf.pad0 = inf.pad1 = inf.pad2 = 0.f;
+    a.info[b] = inf;
+  }
+}
+
+// ---------------------------------------------------------------- fitness
+__global__ void fitness_kernel(EvalArgs a) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= a.B) return;
+  const TopoInfo inf = a.info[b];
+  double lo = 0.0;
+  float lc = 0.f, ml = 0.f;
+  const float* pp = a.part + (size_t)b * a.n_rowtiles * 4;
+  for (int r = 0; r < a.n_rowtiles; ++r) {
+    lo += (double)pp[r * 4 + 0];
+    lc += pp[r * 4 + 1];
+    ml = fmaxf(ml, pp[r * 4 + 2]);
+  }
+  float fit;
+  if (inf.island_base) {
+    fit = -INFINITY;
+  } else if (a.fitness_kind == TTO_FIT_F1) {
+    fit = (float)(-(lo + 200.0 * inf.lambda_c0 + 50.0 * lc));
+  } else {
+    fit = (float)(-(lo + (double)ml));
+  }
+  a.fitness[b] = fit;
+  const int cs = min(inf.ns, a.d_split - 1), cm = min(inf.nm, a.d_moved - 1);
+  if (a.desc) {
+    a.desc[2 * b] = inf.ns;
+    a.desc[2 * b + 1] = inf.nm;
+  }
+  if (a.cell) a.cell[b] = cs * a.d_moved + cm;
+  if (a.island) a.island[b] = (uint8_t)((inf.island_base ? 1 : 0) | (inf.n_islanded > 0 ? 2 : 0));
+  if (a.metrics) {
+    float* m = a.metrics + (size_t)b * 4;
+    m[0] = inf.island_base ? 0.f : (float)lo;
+    m[1] = inf.island_base ? 0.f : ml;
+    m[2] = inf.island_base ? 0.f : lc;
+    m[3] = inf.lambda_c0;
+  }
+}
+
+// ---------------------------------------------------------------- workspace
+void free_workspace(tto_grid* g) {
+  Workspace& w = g->ws;
+  void* ptrs[] = {w.U, w.V, w.Ub, w.Vb, w.fp, w.gg, w.info, w.part, w.fit, w.cell, w.desc, w.island, w.topo};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  w = Workspace();
+}
+
+int ensure_workspace(tto_grid* g, int B, int T) {
+  Workspace& w = g->ws;
+  if (B <= w.cap_B && T <= w.cap_T) return TTO_OK;
+  int nB = B > w.cap_B ? B : w.cap_B;
+  int nT = T > w.cap_T ? T : w.cap_T;
+  free_workspace(g);
+  const size_t Ep = g->E_mon_pad, Op = g->O_pad;
+  TTO_CUDA_TRY(cudaMalloc(&w.U, (size_t)nB * Ep * 8 * sizeof(float)));
+  TTO_CUDA_TRY(cudaMalloc(&w.V, (size_t)nB * Op * 8 * sizeof(float)));
+  TTO_CUDA_TRY(cudaMalloc(&w.Ub, (size_t)nB * Ep * 16 * sizeof(uint16_t)));
+  TTO_CUDA_TRY(cudaMalloc(&w.Vb, (size_t)nB * Op * 16 * sizeof(uint16_t)));
+  TTO_CUDA_TRY(cudaMalloc(&w.fp, (size_t)nB * nT * Ep * sizeof(float)));
+  TTO_CUDA_TRY(cudaMalloc(&w.gg, (size_t)nB * Op * nT * sizeof(float)));
+  TTO_CUDA_TRY(cudaMalloc(&w.info, (size_t)nB * sizeof(TopoInfo)));
+  TTO_CUDA_TRY(cudaMalloc(&w.part, (size_t)nB * g->n_rowtiles * 4 * sizeof(float)));
+  TTO_CUDA_TRY(cudaMalloc(&w.fit, (size_t)nB * sizeof(float)));
+  TTO_CUDA_TRY(cudaMalloc(&w.cell, (size_t)nB * sizeof(int32_t)));
+  TTO_CUDA_TRY(cudaMalloc(&w.desc, (size_t)nB * 2 * sizeof(int32_t)));
+  TTO_CUDA_TRY(cudaMalloc(&w.island, (size_t)nB * sizeof(uint8_t)));
+  TTO_CUDA_TRY(cudaMalloc(&w.topo, (size_t)nB * g->k_max * sizeof(int32_t)));
+  w.cap_B = nB;
+  w.cap_T = nT;
+  return TTO_OK;
+}
+
+int padded_T(int n_t) {
+  const int opts[] = {1, 2, 4, 8, 16, 24, 32};
+  for (int v : opts)
+    if (n_t <= v) return v;
+  return -1;
+}
+
+static int padded_K(int k) { return k <= 2 ? 2 : (k <= 4 ? 4 : 8); }
+
+int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, int n_t,
+                  const tto_eval_opts* o, float* fitness, int32_t* desc, int32_t* cell,
+                  uint8_t* island, float* metrics, float* fmax, cudaStream_t s) {
+  if (!g || !o || !topo || !fitness) return set_error(TTO_E_ARG, "null argument");
+  if (B < 0) return set_error(TTO_E_ARG, "negative batch");
+  if (o->d_split < 1 || o->d_moved < 1) return set_error(TTO_E_ARG, "archive extents must be >= 1");
+  if (o->precision < TTO_PREC_FP32 || o->precision > TTO_PREC_BF16) return set_error(TTO_E_ARG, "unknown precision");
+  if (o->fitness_kind != TTO_FIT_WORKLOAD && o->fitness_kind != TTO_FIT_F1) return set_error(TTO_E_ARG, "unknown fitness kind");
+  if (n_t < 0 || n_t > TTO_MAX_T || (tsel == nullptr && g->T > TTO_MAX_T))
+    return set_error(TTO_E_ARG, "n_t must be in [1, %d]", TTO_MAX_T);
+  EvalArgs a;
+  memset(&a, 0, sizeof(a));
+  if (tsel == nullptr) {
+    n_t = g->T;
+    for (int t = 0; t < n_t; ++t) a.tsel[t] = t;
+  } else {
+    if (n_t < 1) return set_error(TTO_E_ARG, "n_t must be >= 1");
+    for (int t = 0; t < n_t; ++t) {
+      if (tsel[t] < 0 || tsel[t] >= g->T) return set_error(TTO_E_ARG, "timestep %d out of range", tsel[t]);
+      a.tsel[t] = tsel[t];
+    }
+  }
+  if (B == 0) return TTO_OK;
+  const int TT = padded_T(n_t);
+  TTO_CUDA_TRY(cudaSetDevice(g->device));
+  int rc = ensure_workspace(g, B, TT);
+  if (rc) return rc;
+  Workspace& w = g->ws;
+  a.Nmo = g->d_Nmo;
+  a.Nsw = g->d_Nsw;
+  a.swcol = g->d_swcol;
+  a.f0 = g->d_f0;
+  a.p = g->d_p;
+  a.b = g->d_b;
+  a.lim = g->d_lim;
+  a.mon = g->d_mon;
+  a.out = g->d_out;
+  a.Ncc = g->d_Ncc;
+  a.station_bus = g->d_station_bus;
+  a.asset_off = g->d_asset_off;
+  a.asset_br = g->d_asset_br;
+  a.act_st = g->d_act_st;
+  a.act_mask = g->d_act_mask;
+  a.status = g->d_status;
+  a.E = g->E;
+  a.n_bus = g->n_bus;
+  a.E_mon = g->E_mon;
+  a.O = g->O;
+  a.E_mon_pad = g->E_mon_pad;
+  a.O_pad = g->O_pad;
+  a.A = g->A;
+  a.k_max = g->k_max;
+  a.n_t = n_t;
+  a.TT = TT;
+  a.KP = padded_K(g->k_max);
+  a.d_split = o->d_split;
+  a.d_moved = o->d_moved;
+  a.topo = topo;
+  a.B = B;
+  a.U = w.U;
+  a.V = w.V;
+  a.Ub = w.Ub;
+  a.Vb = w.Vb;
+  a.fp = w.fp;
+  a.gg = w.gg;
+  a.info = w.info;
+  a.part = w.part;
+  a.fitness = fitness;
+  a.desc = desc;
+  a.cell = cell;
+  a.island = island;
+  a.metrics = metrics;
+  a.fmax = fmax;
+  a.fitness_kind = o->fitness_kind;
+  a.n_rowtiles = g->n_rowtiles;
+  a.precision = o->precision;
+  a.from = g->d_from;
+  cudaEvent_t* ev = nullptr;
+  if (g->prof_on && g->prof_n < kProfileCalls) ev = &g->prof_ev[4 * g->prof_n++];
+  if (ev) TTO_CUDA_TRY(cudaEventRecord(ev[0], s));
+  split_update_kernel<<<B, 256, 0, s>>>(a);
+  TTO_CUDA_TRY(cudaGetLastError());
+  if (ev) TTO_CUDA_TRY(cudaEventRecord(ev[1], s));
+  rc = launch_sweep(a, s);
+  if (rc) return rc;
+  if (ev) TTO_CUDA_TRY(cudaEventRecord(ev[2], s));
+  fitness_kernel<<<(B + 127) / 128, 128, 0, s>>>(a);
+  TTO_CUDA_TRY(cudaGetLastError());
+  if (ev) TTO_CUDA_TRY(cudaEventRecord(ev[3], s));
+  return TTO_OK;
+}
+
+}  // namespace tto
+
+extern "C" {
+
+int tto_grid_reserve(tto_grid* g, int32_t max_batch, int32_t n_t) {
+  if (!g || max_batch < 1 || n_t < 1 || n_t > TTO_MAX_T) return tto::set_error(TTO_E_ARG, "bad reserve arguments");
+  TTO_CUDA_TRY(cudaSetDevice(g->device));
+  return tto::ensure_workspace(g, max_batch, tto::padded_T(n_t));
+}
+
+int tto_evaluate_batch(tto_grid* g, const int32_t* topo, int32_t B, const int32_t* timesteps,
+                       int32_t n_t, const tto_eval_opts* opts, float* fitness, int32_t* desc,
+                       int32_t* cell, uint8_t* island, float* metrics, float* fmax, void* stream) {
+  return tto::evaluate_impl(g, topo, B, timesteps, n_t, opts, fitness, desc, cell, island, metrics,
+                            fmax, (cudaStream_t)stream);
+}
+
+int tto_grid_profile(tto_grid* g, int32_t enable) {
+  if (!g) return tto::set_error(TTO_E_ARG, "null grid");
+  TTO_CUDA_TRY(cudaSetDevice(g->device));
+  if (enable && g->prof_ev.empty()) {
+    g->prof_ev.resize(4 * tto::kProfileCalls);
+    for (auto& e : g->prof_ev) TTO_CUDA_TRY(cudaEventCreate(&e));
+  }
+  g->prof_on = enable ? 1 : 0;
+  if (enable) g->prof_n = 0;
+  return TTO_OK;
+}
+
+int tto_grid_profile_read(tto_grid* g, float* ms_stage, int32_t* n_calls) {
+  if (!g || !ms_stage) return tto::set_error(TTO_E_ARG, "null argument");
+  TTO_CUDA_TRY(cudaSetDevice(g->device));
+  for (int q = 0; q < 3; ++q) ms_stage[q] = 0.f;
+  for (int c = 0; c < g->prof_n; ++c) {
+    TTO_CUDA_TRY(cudaEventSynchronize(g->prof_ev[4 * c + 3]));
+    for (int q = 0; q < 3; ++q) {
+      float ms = 0.f;
+      TTO_CUDA_TRY(cudaEventElapsedTime(&ms, g->prof_ev[4 * c + q], g->prof_ev[4 * c + q + 1]));
+      ms_stage[q] += ms;
+    }
+  }
+  if (n_calls) *n_calls = g->prof_n;
+  return TTO_OK;
+}
+
+int tto_grid_sync_status(tto_grid* g, void* stream) {
+  if (!g) return tto::set_error(TTO_E_ARG, "null grid");
+  TTO_CUDA_TRY(cudaSetDevice(g->device));
+  TTO_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  int st = 0;
+  TTO_CUDA_TRY(cudaMemcpy(&st, g->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  int zero = 0;
+  TTO_CUDA_TRY(cudaMemcpy(g->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice));
+  if (st == TTO_E_TOPOLOGY) return tto::set_error(TTO_E_TOPOLOGY, "a genome named an unknown action or split a station twice");
+  if (st == TTO_E_TIMEOUT) return tto::set_error(TTO_E_TIMEOUT, "a bounded device wait gave up");
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,60 @@
+// Kernel arguments shared by the evaluation kernels, and the sweep launcher.
+#pragma once
+
+#include <stdint.h>
+
+#include "tto_internal.h"
+
+namespace tto {
+
+struct EvalArgs {
+  // grid (device)
+  const float* Nmo;
+  const double* Nsw;
+  const int* swcol;
+  const double* f0;
+  const double* p;
+  const double* b;
+  const float* lim;
+  const int* mon;
+  const int* out;
+  const double* Ncc;
+  const int* from;
+  const int* station_bus;
+  const int* asset_off;
+  const int* asset_br;
+  const int* act_st;
+  const uint32_t* act_mask;
+  int* status;
+  int E, n_bus, E_mon, O, E_mon_pad, O_pad, A, k_max;
+  int n_t, TT, KP;
+  int tsel[TTO_MAX_T];
+  int d_split, d_moved;
+  int precision;
+  int fitness_kind;
+  int n_rowtiles;
+  // batch
+  const int32_t* topo;
+  int B;
+  // workspace
+  float* U;
+  float* V;
+  uint16_t* Ub;
+  uint16_t* Vb;
+  float* fp;
+  float* gg;
+  TopoInfo* info;
+  float* part;
+  // outputs
+  float* fitness;
+  int32_t* desc;
+  int32_t* cell;
+  uint8_t* island;
+  float* metrics;
+  float* fmax;
+};
+
+// Launch the fused N-1 sweep for the precision in a.precision.
+int launch_sweep(const EvalArgs& a, cudaStream_t s);
+
+}  // namespace tto

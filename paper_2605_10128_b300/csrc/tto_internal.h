@@ -1,0 +1,109 @@
+// Internal state of the DC N-1 topology evaluator (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tto.h"
+
+namespace tto {
+
+constexpr int kRowTile = 128;   // monitored-branch rows per sweep CTA
+constexpr int kColPad = 64;     // outage columns are padded to this multiple
+constexpr int kMaxMoved = TTO_MAX_K * TTO_MAX_ASSETS;
+constexpr int kProfileCalls = 256;  // evaluation calls timed per profiling window
+constexpr double kIslandTol = 1e-6;  // N'_cc (and normalised split pivot) at or below: islanded
+
+int set_error(int code, const char* fmt, ...);
+int cuda_error(cudaError_t e, const char* what);
+
+#define TTO_CUDA_TRY(expr)                                  \
+  do {                                                      \
+    cudaError_t _e = (expr);                                \
+    if (_e != cudaSuccess) return ::tto::cuda_error(_e, #expr); \
+  } while (0)
+
+// Per-topology scalars written by the prep kernel.
+struct TopoInfo {
+  int island_base;   // the split disconnects the grid
+  int n_islanded;    // outages that island the split grid
+  int ns;            // split stations
+  int nm;            // moved assets
+  float lambda_c0;   // N-0 critical branches (summed over timesteps)
+  float pad0, pad1, pad2;
+};
+
+// Evaluation workspace, grown on demand (or once by tto_grid_reserve).
+struct Workspace {
+  int cap_B = 0;
+  int cap_T = 0;
+  float* U = nullptr;        // [B][E_mon_pad][KP]  FP32 low-rank row factors
+  float* V = nullptr;        // [B][O_pad][KP]      FP32 low-rank column factors
+  uint16_t* Ub = nullptr;    // [B][E_mon_pad][16]  BF16 (hi | lo) row factors
+  uint16_t* Vb = nullptr;    // [B][O_pad][16]      BF16 (hi | lo) column factors
+  float* fp = nullptr;       // [B][TT][E_mon_pad]  post-split N-0 flows
+  float* gg = nullptr;       // [B][O_pad][TT]      f'_c / N'_cc (NaN: outage islands)
+  TopoInfo* info = nullptr;  // [B]
+  float* part = nullptr;     // [B][n_rowtiles][4]  per row-tile partial metrics
+  float* fit = nullptr;      // [B] scratch fitness (MapElites step)
+  int32_t* cell = nullptr;   // [B]
+  int32_t* desc = nullptr;   // [B][2]
+  uint8_t* island = nullptr; // [B]
+  int32_t* topo = nullptr;   // [B][k_max] proposed genomes (MapElites step)
+};
+
+}  // namespace tto
+
+struct tto_grid {
+  int device = 0;
+  int n_bus = 0, E = 0, slack = 0, T = 0, E_mon = 0, O = 0, S = 0, A = 0, k_max = 0;
+  int E_mon_pad = 0, O_pad = 0, n_sw = 0, n_rowtiles = 0;
+  std::vector<int> from, to, mon, out, station_bus, asset_off, asset_br, act_st, act_off;
+  std::vector<uint32_t> act_mask;
+  std::vector<double> b, p, limit, f0;
+  // device copies
+  float* d_Nmo = nullptr;      // [E_mon_pad][O_pad] N[mon l][out c], FP32
+  double* d_Nsw = nullptr;     // [n_sw][E] full N columns of movable branches, FP64
+  int* d_swcol = nullptr;      // [E] column of a movable branch in d_Nsw, else -1
+  double* d_f0 = nullptr;      // [T][E] base flows
+  double* d_p = nullptr;       // [T][n_bus]
+  double* d_b = nullptr;       // [E]
+  float* d_lim = nullptr;      // [E_mon] limits of monitored branches
+  int* d_mon = nullptr;        // [E_mon]
+  int* d_out = nullptr;        // [O]
+  double* d_Ncc = nullptr;     // [O] N[c][c]
+  int* d_from = nullptr;       // [E]
+  int* d_station_bus = nullptr;
+  int* d_asset_off = nullptr;
+  int* d_asset_br = nullptr;
+  int* d_act_st = nullptr;
+  int* d_act_off = nullptr;
+  uint32_t* d_act_mask = nullptr;
+  int* d_status = nullptr;
+  tto::Workspace ws;
+  // optional per-stage timing (tto_grid_profile)
+  int prof_on = 0, prof_n = 0;
+  std::vector<cudaEvent_t> prof_ev;  // 4 per recorded call
+};
+
+struct tto_archive {
+  tto_grid* g = nullptr;
+  int d_split = 0, d_moved = 0, cells = 0;
+  float* d_fit = nullptr;         // [cells]
+  int32_t* d_genome = nullptr;    // [cells][k_max]
+  uint8_t* d_filled = nullptr;    // [cells]
+  unsigned long long* d_key = nullptr;  // [cells] batch winner keys
+  int32_t* d_filled_list = nullptr;     // [cells + 1]: count, then filled cells ascending
+};
+
+namespace tto {
+int ensure_workspace(tto_grid* g, int B, int T);
+int padded_T(int n_t);  // timesteps rounded up to a compiled sweep width (-1 if > TTO_MAX_T)
+void free_workspace(tto_grid* g);
+int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, int n_t,
+                  const tto_eval_opts* o, float* fitness, int32_t* desc, int32_t* cell,
+                  uint8_t* island, float* metrics, float* fmax, cudaStream_t s);
+}  // namespace tto

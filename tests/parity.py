@@ -1,0 +1,64 @@
+"""Comparison of library outputs with the FP64 oracle.
+
+Tolerance: post-contingency loadings within TOL of each branch's thermal limit
+(|fmax_gpu - fmax_oracle| <= TOL * limit), TOL = 1e-4 for the FP32 sweep and
+1e-3 when the low-rank term runs in BF16 on the tensor cores.  Islanding flags,
+descriptors and cells must match bit for bit.  Critical-branch counts may differ
+only where the oracle's loading sits within the tolerance band of the limit.
+"""
+import os
+
+import numpy as np
+
+from oracle import dcflow
+
+TOL_FP32 = 1e-4
+TOL_BF16 = 1e-3
+
+
+def n_procs():
+    return max(1, min(16, os.cpu_count() or 1))
+
+
+def oracle_eval(grid, topo, idx, timesteps=None, d_split=8, d_moved=8):
+    return dcflow.evaluate_many(grid, [topo[i] for i in idx], processes=min(n_procs(), len(idx)),
+                                timesteps=timesteps, d_split=d_split, d_moved=d_moved)
+
+
+def compare(grid, out, idx, refs, tol=TOL_FP32, fitness_kind=0):
+    """Assert parity for sampled batch indices; returns the largest loading
+    error in units of the thermal limit."""
+    lim = grid.limit[grid.monitored.astype(np.int64)]
+    worst = 0.0
+    for i, r in zip(idx, refs):
+        isl = int(out["island"][i])
+        assert (isl & 1) == (1 if r["island_base"] else 0), f"base islanding differs at {i}"
+        assert int(out["cell"][i]) == r["cell"], f"cell differs at {i}"
+        assert tuple(int(x) for x in out["desc"][i]) == (r["ns"], r["nm"])
+        if r["island_base"]:
+            assert out["fitness"][i] == -np.inf
+            continue
+        assert ((isl >> 1) & 1) == (1 if r["island_any"] else 0), f"outage islanding differs at {i}"
+        fm = out["fmax"][i].astype(np.float64)
+        err = np.abs(fm - r["fmax"]) / lim[None, :]
+        worst = max(worst, float(err.max()))
+        assert err.max() <= tol, f"topology {i}: fmax error {err.max():.3e} of limit"
+        lam_o = r["lambda_o"]
+        n = r["fmax"].size
+        m = out["metrics"][i]
+        band = tol * lim[None, :] * np.ones_like(r["fmax"])
+        assert abs(m[0] - lam_o) <= (band.sum() + 1e-5 * abs(lam_o) + 1e-6), (i, m[0], lam_o)
+        assert abs(m[1] - r["maxload"]) <= tol + 1e-6 * r["maxload"], (i, m[1], r["maxload"])
+        near = int((np.abs(r["fmax"] - lim[None, :]) <= band).sum())
+        assert abs(int(m[2]) - r["lambda_c"]) <= near, (i, m[2], r["lambda_c"], near)
+        near0 = int((np.abs(np.abs(r["fprime"]) - lim[None, :]) <= band).sum())
+        assert abs(int(m[3]) - r["lambda_c0"]) <= near0, (i, m[3], r["lambda_c0"])
+        if fitness_kind == 0:
+            ref = r["fitness"]
+            bound = band.sum() + tol + 1e-5 * abs(ref) + 1e-6
+        else:
+            ref = r["lambda_f1"]
+            bound = band.sum() + 50.0 * near + 200.0 * near0 + 1e-5 * abs(ref) + 1e-6
+        assert abs(float(out["fitness"][i]) - ref) <= bound, (i, out["fitness"][i], ref)
+        del n
+    return worst
