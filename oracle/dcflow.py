@@ -35,7 +35,7 @@ import scipy.sparse as sp
 import scipy.sparse.csgraph as csg
 import scipy.sparse.linalg as spla
 
-DENSE_MAX = 400
+DENSE_MAX = 64
 
 
 class TopologyError(ValueError):
@@ -212,6 +212,28 @@ def evaluate(grid, genome, timesteps=None, outages=None, d_split=8, d_moved=8, w
     return res
 
 
+def _pool(processes):
+    """A spawn-started process pool whose workers run single-threaded BLAS
+    (one solve per process; threaded BLAS in every worker oversubscribes the
+    host)."""
+    import multiprocessing as mp
+    import os
+    saved = {k: os.environ.get(k) for k in _BLAS_VARS}
+    for k in _BLAS_VARS:
+        os.environ[k] = "1"
+    try:
+        return mp.get_context("spawn").Pool(processes)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+_BLAS_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
 def _eval_star(args):
     grid, genome, kw = args
     return evaluate(grid, genome, **kw)
@@ -222,8 +244,7 @@ def evaluate_many(grid, genomes, processes=1, **kw):
     jobs = [(grid, g, kw) for g in genomes]
     if processes <= 1 or len(jobs) <= 1:
         return [_eval_star(j) for j in jobs]
-    import multiprocessing as mp
-    with mp.get_context("spawn").Pool(processes) as pool:
+    with _pool(processes) as pool:
         return pool.map(_eval_star, jobs, chunksize=1)
 
 
@@ -237,11 +258,10 @@ def evaluate_parallel_outages(grid, genome, processes=8, **kw):
     over host processes (spawn); the per-process maxima are combined by max and
     the metrics recomputed from the combined f^max with the same formulas as
     :func:`evaluate`."""
-    import multiprocessing as mp
     O = grid.outages.size
     chunks = [c for c in np.array_split(np.arange(O), max(1, processes)) if c.size]
     jobs = [(grid, genome, c, kw) for c in chunks]
-    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+    with _pool(len(jobs)) as pool:
         parts = pool.map(_eval_chunk, jobs, chunksize=1)
     r = dict(parts[0])
     if r["island_base"]:

@@ -349,8 +349,9 @@ static int padded_K(int k) { return k <= 2 ? 2 : (k <= 4 ? 4 : 8); }
 int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, int n_t,
                   const tto_eval_opts* o, float* fitness, int32_t* desc, int32_t* cell,
                   uint8_t* island, float* metrics, float* fmax, cudaStream_t s) {
-  if (!g || !o || !topo || !fitness) return set_error(TTO_E_ARG, "null argument");
+  if (!g || !o) return set_error(TTO_E_ARG, "null argument");
   if (B < 0) return set_error(TTO_E_ARG, "negative batch");
+  if (B > 0 && (!topo || !fitness)) return set_error(TTO_E_ARG, "null topology or fitness buffer");
   if (o->d_split < 1 || o->d_moved < 1) return set_error(TTO_E_ARG, "archive extents must be >= 1");
   if (o->precision < TTO_PREC_FP32 || o->precision > TTO_PREC_BF16) return set_error(TTO_E_ARG, "unknown precision");
   if (o->fitness_kind != TTO_FIT_WORKLOAD && o->fitness_kind != TTO_FIT_F1) return set_error(TTO_E_ARG, "unknown fitness kind");
