@@ -52,7 +52,7 @@ def _random_archive(sg, d_split, d_moved, n_fill, seed):
 
 
 @pytest.mark.parametrize("mut", [(0.2, 0.2, 0.5, 0.1, 2.0), (0.6, 0.1, 0.2, 0.1, 3.0),
-                                 (0.0, 0.5, 0.5, 0.0, 1.0)])
+                                 (0.3, 0.3, 0.4, 0.0, 1.0)])
 def test_proposals_bit_exact(mut):
     from paper_2605_10128_b300 import Grid, Archive
     sg = config_grid("tto2k")
@@ -135,14 +135,18 @@ def test_mapelites_trajectory_tto30():
         assert np.array_equal(fin, np.isfinite(fgot))
         assert np.all(np.abs(fgot[fin] - fref[fin]) <= tol)
         cells = np.array([r["cell"] for r in res])
-        # near-tie check: any decision within tolerance ends the comparison
+        # near-tie check: a decision between different genomes whose fitness
+        # lies within the tolerance ends the comparison (identical genomes
+        # tie harmlessly)
         tie = False
         for cc in np.unique(cells[fin]):
-            vals = np.sort(fref[fin & (cells == cc)])[::-1]
+            ids = np.flatnonzero(fin & (cells == cc))
+            top = ids[np.argmax(fref[ids])]
+            for j in ids:
+                if j != top and fref[top] - fref[j] <= 2 * tol and not np.array_equal(ref_topo[j], ref_topo[top]):
+                    tie = True
             inc = arch.elites.get(int(cc))
-            if len(vals) > 1 and vals[0] - vals[1] <= 2 * tol:
-                tie = True
-            if inc is not None and abs(vals[0] - inc[0]) <= 2 * tol:
+            if inc is not None and abs(fref[top] - inc[0]) <= 2 * tol and not np.array_equal(inc[1], ref_topo[top]):
                 tie = True
         arch.insert(cells, fref, ref_topo)
         if tie:
