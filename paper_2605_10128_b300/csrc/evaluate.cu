@@ -24,10 +24,68 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <cuda_bf16.h>
+
 #include "sweep.cuh"
 #include "tto_internal.h"
 
 namespace tto {
+
+// ------------------------------------------------------- factor layouts
+// FP32 sweep: U [B][E_mon_pad][KP], V [B][O_pad][KP], g [B][O_pad][TT].
+// Tensor-core sweep (mma m16n8k16, bf16 in, fp32 accumulate), fragment order:
+//   A = [U_hi | U_lo] (16 x 16 per 16-row tile): Ua [B][E_mon_pad/16][lane][4 x bf16x2]
+//   B columns (8 outages per tile): Vb [B][O_pad/8][lane][2] = (V_hi pair, V_lo pair)
+//   g [B][O_pad/8][q][TT][2]: the two outage columns 2q, 2q+1 a lane owns.
+__device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
+  const uint32_t a = __bfloat16_as_ushort(__float2bfloat16_rn(lo_elem));
+  const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn(hi_elem));
+  return a | (b << 16);
+}
+
+__device__ __forceinline__ void split_bf16(float x, float& hi, float& lo) {
+  hi = __bfloat162float(__float2bfloat16_rn(x));
+  lo = x - hi;
+}
+
+__device__ void store_row_factors(const EvalArgs& a, int b, int l, const float* u) {
+  if (a.precision == TTO_PREC_FP32) {
+    float* Urow = a.U + ((size_t)b * a.E_mon_pad + l) * a.KP;
+    for (int j = 0; j < a.KP; ++j) Urow[j] = u[j];
+    return;
+  }
+  float hi[TTO_MAX_K], lo[TTO_MAX_K];
+  for (int j = 0; j < TTO_MAX_K; ++j) split_bf16(u[j], hi[j], lo[j]);
+  const int mt = l >> 4, r = l & 15, g = r & 7, half = r >> 3;
+  uint32_t* base = reinterpret_cast<uint32_t*>(a.U) + ((size_t)b * (a.E_mon_pad >> 4) + mt) * 128;
+  for (int q = 0; q < 4; ++q) {
+    uint32_t* w = base + (g * 4 + q) * 4;
+    w[half] = pack_bf16(hi[2 * q], hi[2 * q + 1]);
+    w[2 + half] = pack_bf16(lo[2 * q], lo[2 * q + 1]);
+  }
+}
+
+__device__ void store_col_factors(const EvalArgs& a, int b, int c, const float* v, const float* gv) {
+  const int TT = a.TT;
+  if (a.precision == TTO_PREC_FP32) {
+    float* Vrow = a.V + ((size_t)b * a.O_pad + c) * a.KP;
+    for (int j = 0; j < a.KP; ++j) Vrow[j] = v[j];
+    float* grow = a.gg + ((size_t)b * a.O_pad + c) * TT;
+    for (int t = 0; t < TT; ++t) grow[t] = gv[t];
+    return;
+  }
+  float hi[TTO_MAX_K], lo[TTO_MAX_K];
+  for (int j = 0; j < TTO_MAX_K; ++j) split_bf16(v[j], hi[j], lo[j]);
+  const int ntl = c >> 3, cc = c & 7;
+  const size_t tile = (size_t)b * (a.O_pad >> 3) + ntl;
+  uint32_t* vb = reinterpret_cast<uint32_t*>(a.V) + tile * 64;
+  for (int q = 0; q < 4; ++q) {
+    vb[(cc * 4 + q) * 2 + 0] = pack_bf16(hi[2 * q], hi[2 * q + 1]);
+    vb[(cc * 4 + q) * 2 + 1] = pack_bf16(lo[2 * q], lo[2 * q + 1]);
+  }
+  float* gq = a.gg + (tile * 4 + (cc >> 1)) * TT * 2 + (cc & 1);
+  for (int t = 0; t < TT; ++t) gq[2 * t] = gv[t];
+}
 
 // ---------------------------------------------------------------- split update
 __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
@@ -171,16 +229,17 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
   }
   __syncthreads();
 
-  const int KP = a.KP, TT = a.TT;
+  const int TT = a.TT;
   const float qnan = __int_as_float(0x7fc00000);
   int c0cnt = 0;
   // monitored rows: f', U
   for (int l = tid; l < a.E_mon_pad; l += blockDim.x) {
     const int lr = min(l, a.E_mon - 1);
     const int e = a.mon[lr];
-    float* Urow = a.U + ((size_t)b * a.E_mon_pad + l) * KP;
+    float u[TTO_MAX_K];
     if (dead) {
-      for (int j = 0; j < KP; ++j) Urow[j] = 0.f;
+      for (int j = 0; j < TTO_MAX_K; ++j) u[j] = 0.f;
+      store_row_factors(a, b, l, u);
       for (int t = 0; t < TT; ++t) a.fp[((size_t)b * TT + t) * a.E_mon_pad + l] = 0.f;
       continue;
     }
@@ -190,12 +249,13 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
       for (int q = s_slot[j]; q < s_slot[j + 1]; ++q) w += s_coef[q] * s_col[q][e];
       W[j] = w;
     }
-    for (int jj = 0; jj < KP; ++jj) {
-      double u = 0.0;
+    for (int jj = 0; jj < TTO_MAX_K; ++jj) {
+      double uu = 0.0;
       if (jj < k)
-        for (int j = 0; j < k; ++j) u += W[j] * s_Ki[j][jj];
-      Urow[jj] = (float)u;
+        for (int j = 0; j < k; ++j) uu += W[j] * s_Ki[j][jj];
+      u[jj] = (float)uu;
     }
+    store_row_factors(a, b, l, u);
     const float lim = a.lim[lr];
     for (int t = 0; t < TT; ++t) {
       float fv = 0.f;
@@ -213,11 +273,11 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
   for (int c = tid; c < a.O_pad; c += blockDim.x) {
     const int cr = min(c, a.O - 1);
     const int e = a.out[cr];
-    float* Vrow = a.V + ((size_t)b * a.O_pad + c) * KP;
-    float* grow = a.gg + ((size_t)b * a.O_pad + c) * TT;
+    float v[TTO_MAX_K], gv[TTO_MAX_T];
     if (dead) {
-      for (int j = 0; j < KP; ++j) Vrow[j] = 0.f;
-      for (int t = 0; t < TT; ++t) grow[t] = t < nt ? qnan : 0.f;
+      for (int j = 0; j < TTO_MAX_K; ++j) v[j] = 0.f;
+      for (int t = 0; t < TT; ++t) gv[t] = t < nt ? qnan : 0.f;
+      store_col_factors(a, b, c, v, gv);
       continue;
     }
     double W[TTO_MAX_K];
@@ -229,26 +289,27 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
     const double be = a.b[e];
     double npcc = a.Ncc[cr];
     for (int jj = 0; jj < k; ++jj) {
-      double u = 0.0;
-      for (int j = 0; j < k; ++j) u += W[j] * s_Ki[j][jj];
-      npcc -= u * (W[jj] / be);
+      double uu = 0.0;
+      for (int j = 0; j < k; ++j) uu += W[j] * s_Ki[j][jj];
+      npcc -= uu * (W[jj] / be);
     }
-    for (int jj = 0; jj < KP; ++jj) Vrow[jj] = jj < k ? (float)(W[jj] / be) : 0.f;
+    for (int jj = 0; jj < TTO_MAX_K; ++jj) v[jj] = jj < k ? (float)(W[jj] / be) : 0.f;
     const bool isl = !(npcc > kIslandTol);
     if (isl && c < a.O) ++islcnt;
     for (int t = 0; t < TT; ++t) {
-      float gv = 0.f;
+      float g = 0.f;
       if (t < nt) {
         if (isl) {
-          gv = qnan;
+          g = qnan;
         } else {
           double f = a.f0[(size_t)a.tsel[t] * a.E + e];
           for (int j = 0; j < k; ++j) f += W[j] * s_psi[t][j];
-          gv = (float)(f / npcc);
+          g = (float)(f / npcc);
         }
       }
-      grow[t] = gv;
+      gv[t] = g;
     }
+    store_col_factors(a, b, c, v, gv);
   }
   if (c0cnt) atomicAdd(&s_cnt_c0, c0cnt);
   if (islcnt) atomicAdd(&s_cnt_isl, islcnt);
@@ -272,8 +333,8 @@ __global__ void fitness_kernel(EvalArgs a) {
   const TopoInfo inf = a.info[b];
   double lo = 0.0;
   float lc = 0.f, ml = 0.f;
-  const float* pp = a.part + (size_t)b * a.n_rowtiles * 4;
-  for (int r = 0; r < a.n_rowtiles; ++r) {
+  const float* pp = a.part + (size_t)b * a.n_parts * 4;
+  for (int r = 0; r < a.n_parts; ++r) {
     lo += (double)pp[r * 4 + 0];
     lc += pp[r * 4 + 1];
     ml = fmaxf(ml, pp[r * 4 + 2]);
@@ -306,7 +367,7 @@ __global__ void fitness_kernel(EvalArgs a) {
 // ---------------------------------------------------------------- workspace
 void free_workspace(tto_grid* g) {
   Workspace& w = g->ws;
-  void* ptrs[] = {w.U, w.V, w.Ub, w.Vb, w.fp, w.gg, w.info, w.part, w.fit, w.cell, w.desc, w.island, w.topo};
+  void* ptrs[] = {w.U, w.V, w.fp, w.gg, w.info, w.part, w.fit, w.cell, w.desc, w.island, w.topo};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   w = Workspace();
@@ -321,12 +382,10 @@ int ensure_workspace(tto_grid* g, int B, int T) {
   const size_t Ep = g->E_mon_pad, Op = g->O_pad;
   TTO_CUDA_TRY(cudaMalloc(&w.U, (size_t)nB * Ep * 8 * sizeof(float)));
   TTO_CUDA_TRY(cudaMalloc(&w.V, (size_t)nB * Op * 8 * sizeof(float)));
-  TTO_CUDA_TRY(cudaMalloc(&w.Ub, (size_t)nB * Ep * 16 * sizeof(uint16_t)));
-  TTO_CUDA_TRY(cudaMalloc(&w.Vb, (size_t)nB * Op * 16 * sizeof(uint16_t)));
   TTO_CUDA_TRY(cudaMalloc(&w.fp, (size_t)nB * nT * Ep * sizeof(float)));
   TTO_CUDA_TRY(cudaMalloc(&w.gg, (size_t)nB * Op * nT * sizeof(float)));
   TTO_CUDA_TRY(cudaMalloc(&w.info, (size_t)nB * sizeof(TopoInfo)));
-  TTO_CUDA_TRY(cudaMalloc(&w.part, (size_t)nB * g->n_rowtiles * 4 * sizeof(float)));
+  TTO_CUDA_TRY(cudaMalloc(&w.part, (size_t)nB * max_parts(g) * 4 * sizeof(float)));
   TTO_CUDA_TRY(cudaMalloc(&w.fit, (size_t)nB * sizeof(float)));
   TTO_CUDA_TRY(cudaMalloc(&w.cell, (size_t)nB * sizeof(int32_t)));
   TTO_CUDA_TRY(cudaMalloc(&w.desc, (size_t)nB * 2 * sizeof(int32_t)));
@@ -408,8 +467,6 @@ int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, 
   a.B = B;
   a.U = w.U;
   a.V = w.V;
-  a.Ub = w.Ub;
-  a.Vb = w.Vb;
   a.fp = w.fp;
   a.gg = w.gg;
   a.info = w.info;
@@ -422,6 +479,7 @@ int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, 
   a.fmax = fmax;
   a.fitness_kind = o->fitness_kind;
   a.n_rowtiles = g->n_rowtiles;
+  a.n_parts = g->n_rowtiles;
   a.precision = o->precision;
   a.from = g->d_from;
   cudaEvent_t* ev = nullptr;
@@ -430,6 +488,11 @@ int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, 
   split_update_kernel<<<B, 256, 0, s>>>(a);
   TTO_CUDA_TRY(cudaGetLastError());
   if (ev) TTO_CUDA_TRY(cudaEventRecord(ev[1], s));
+  if (a.precision != TTO_PREC_FP32) {
+    rc = ensure_fragment_N(g, s);
+    if (rc) return rc;
+    a.Nf = g->d_Nf;
+  }
   rc = launch_sweep(a, s);
   if (rc) return rc;
   if (ev) TTO_CUDA_TRY(cudaEventRecord(ev[2], s));

@@ -10,6 +10,7 @@ namespace tto {
 struct EvalArgs {
   // grid (device)
   const float* Nmo;
+  const float4* Nf;  // -N in mma C-fragment order (tensor-core sweep)
   const double* Nsw;
   const int* swcol;
   const double* f0;
@@ -33,14 +34,13 @@ struct EvalArgs {
   int precision;
   int fitness_kind;
   int n_rowtiles;
+  int n_parts;  // partial-metric records per topology (set by the sweep launcher)
   // batch
   const int32_t* topo;
   int B;
   // workspace
   float* U;
   float* V;
-  uint16_t* Ub;
-  uint16_t* Vb;
   float* fp;
   float* gg;
   TopoInfo* info;
@@ -54,7 +54,13 @@ struct EvalArgs {
   float* fmax;
 };
 
-// Launch the fused N-1 sweep for the precision in a.precision.
-int launch_sweep(const EvalArgs& a, cudaStream_t s);
+// Launch the fused N-1 sweep for the precision in a.precision; sets a.n_parts.
+int launch_sweep(EvalArgs& a, cudaStream_t s);
+int launch_sweep_fp32(const EvalArgs& a, cudaStream_t s);
+int launch_sweep_tc(EvalArgs& a, cudaStream_t s);
+// Partial-metric records per topology the workspace must hold.
+size_t max_parts(const tto_grid* g);
+// Build the fragment-ordered copy of -N used by the tensor-core sweep (once).
+int ensure_fragment_N(tto_grid* g, cudaStream_t s);
 
 }  // namespace tto

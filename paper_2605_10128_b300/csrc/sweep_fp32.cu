@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kRowTile) sweep_fp32_kernel(EvalArgs a) {
       cnt += sred[w][tid][1];
       ml = fmaxf(ml, sred[w][tid][2]);
     }
-    float* pp = a.part + ((size_t)(b0 + tid) * a.n_rowtiles + tile) * 4;
+    float* pp = a.part + ((size_t)(b0 + tid) * a.n_parts + tile) * 4;
     pp[0] = over;
     pp[1] = cnt;
     pp[2] = ml;
@@ -167,9 +167,12 @@ int launch_sweep_fp32(const EvalArgs& a, cudaStream_t s) {
   return set_error(TTO_E_ARG, "unsupported padded rank %d", a.KP);
 }
 
-int launch_sweep(const EvalArgs& a, cudaStream_t s) {
-  if (a.precision == TTO_PREC_FP32) return launch_sweep_fp32(a, s);
-  return set_error(TTO_E_ARG, "precision mode %d is not available in this build", a.precision);
+int launch_sweep(EvalArgs& a, cudaStream_t s) {
+  if (a.precision == TTO_PREC_FP32) {
+    a.n_parts = a.n_rowtiles;
+    return launch_sweep_fp32(a, s);
+  }
+  return launch_sweep_tc(a, s);
 }
 
 }  // namespace tto

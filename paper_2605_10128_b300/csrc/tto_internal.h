@@ -40,14 +40,12 @@ struct TopoInfo {
 struct Workspace {
   int cap_B = 0;
   int cap_T = 0;
-  float* U = nullptr;        // [B][E_mon_pad][KP]  FP32 low-rank row factors
-  float* V = nullptr;        // [B][O_pad][KP]      FP32 low-rank column factors
-  uint16_t* Ub = nullptr;    // [B][E_mon_pad][16]  BF16 (hi | lo) row factors
-  uint16_t* Vb = nullptr;    // [B][O_pad][16]      BF16 (hi | lo) column factors
+  float* U = nullptr;        // [B][E_mon_pad][8] FP32 row factors, or bf16 A fragments
+  float* V = nullptr;        // [B][O_pad][8] FP32 column factors, or bf16 B fragments
   float* fp = nullptr;       // [B][TT][E_mon_pad]  post-split N-0 flows
   float* gg = nullptr;       // [B][O_pad][TT]      f'_c / N'_cc (NaN: outage islands)
   TopoInfo* info = nullptr;  // [B]
-  float* part = nullptr;     // [B][n_rowtiles][4]  per row-tile partial metrics
+  float* part = nullptr;     // [B][parts][4]        per row-band partial metrics
   float* fit = nullptr;      // [B] scratch fitness (MapElites step)
   int32_t* cell = nullptr;   // [B]
   int32_t* desc = nullptr;   // [B][2]
@@ -66,6 +64,7 @@ struct tto_grid {
   std::vector<double> b, p, limit, f0;
   // device copies
   float* d_Nmo = nullptr;      // [E_mon_pad][O_pad] N[mon l][out c], FP32
+  float4* d_Nf = nullptr;      // -N in mma C-fragment order, built on first tensor-core use
   double* d_Nsw = nullptr;     // [n_sw][E] full N columns of movable branches, FP64
   int* d_swcol = nullptr;      // [E] column of a movable branch in d_Nsw, else -1
   double* d_f0 = nullptr;      // [T][E] base flows

@@ -55,16 +55,30 @@ def test_three_bus_golden_through_library():
     assert list(out["cell"]) == [0, 9, 9]
 
 
+PRECISIONS = [("fp32", 0, parity.TOL_FP32), ("bf16x3", 1, parity.TOL_BF16)]
+
+
+def check_all_precisions(label, sg, g, topo, idx, refs, plain_bf16=True, **kw):
+    """Every precision mode against the same oracle results; the plain-BF16
+    mode is held to the structural checks and its loading error reported."""
+    for name, prec, tol in PRECISIONS:
+        out = run(g, topo, precision=prec, **kw)
+        worst = parity.compare(sg, out, idx, refs, tol=tol)
+        print(f"{label} {name} worst loading error {worst:.2e} of limit")
+    if plain_bf16:
+        out = run(g, topo, precision=2, **kw)
+        worst = parity.compare(sg, out, idx, refs, tol=np.inf)
+        print(f"{label} bf16 (single product) worst loading error {worst:.2e} of limit")
+
+
 def test_tto30_every_topology():
     sg = with_limits(config_grid("tto30"), CONFIGS["tto30"]["n_tight"])
     topo = random_topologies(sg, 256, seed=11)
     topo[0] = -1  # the unsplit topology
     g = lib_grid(sg)
-    out = run(g, topo)
     idx = list(range(256))
     refs = parity.oracle_eval(sg, topo, idx)
-    worst = parity.compare(sg, out, idx, refs)
-    print(f"tto30 worst loading error {worst:.2e} of limit")
+    check_all_precisions("tto30", sg, g, topo, idx, refs)
     assert sum(r["island_base"] for r in refs) > 0  # the batch exercises split islanding
     assert sum(r["island_any"] for r in refs) > 0
 
@@ -82,10 +96,23 @@ def test_ragged_tiles_subsets_and_timesteps(seed):
     topo = random_topologies(sg, 37, seed=seed)
     g = lib_grid(sg)
     for ts in [None, [2, 0]]:
-        out = run(g, topo, timesteps=ts)
         idx = list(range(37))
         refs = parity.oracle_eval(sg, topo, idx, timesteps=ts)
-        parity.compare(sg, out, idx, refs)
+        check_all_precisions(f"ragged{seed} t={ts}", sg, g, topo, idx, refs, timesteps=ts)
+
+
+@pytest.mark.parametrize("T", [24, 9])
+def test_long_horizons(T):
+    """Timestep counts that the tensor-core sweep splits into passes (24 = 3 x 8)
+    or pads (9 -> 16)."""
+    sg = make_grid(120, 180, 10, assets=(4, 8), T=T, b_dist=("loguniform", 2.0, 200.0),
+                   noise=0.1, seed=T, k_max=4, name="long")
+    sg = with_limits(sg, 3)
+    topo = random_topologies(sg, 20, seed=T)
+    g = lib_grid(sg)
+    idx = list(range(20))
+    refs = parity.oracle_eval(sg, topo, idx)
+    check_all_precisions(f"T={T}", sg, g, topo, idx, refs)
 
 
 def test_fitness_f1_option():
@@ -103,11 +130,9 @@ def test_tto2k_sampled_against_oracle():
     sg = with_limits(config_grid("tto2k"), CONFIGS["tto2k"]["n_tight"])
     topo = random_topologies(sg, 512, seed=21)
     g = lib_grid(sg)
-    out = run(g, topo)
     idx = [0, 1, 2, 3]
     refs = parity.oracle_eval(sg, topo, idx)
-    worst = parity.compare(sg, out, idx, refs)
-    print(f"tto2k worst loading error {worst:.2e} of limit")
+    check_all_precisions("tto2k", sg, g, topo, idx, refs)
 
 
 @pytest.mark.slow
@@ -119,7 +144,6 @@ def test_tto10k_full_batch_sampled_against_oracle():
     sg = with_limits(config_grid("tto10k"), c["n_tight"])
     topo = random_topologies(sg, c["batch"], seed=1)
     g = lib_grid(sg)
-    out = run(g, topo, d_split=20, d_moved=20)
     picks = []
     want_isl = True
     for i in range(64):
@@ -135,8 +159,8 @@ def test_tto10k_full_batch_sampled_against_oracle():
     idx = [p[0] for p in picks]
     refs = [dcflow.evaluate_parallel_outages(sg, topo[i], processes=parity.n_procs(), d_split=20,
                                              d_moved=20) for i in idx]
-    worst = parity.compare(sg, out, idx, refs)
-    print(f"tto10k worst loading error {worst:.2e} of limit")
+    check_all_precisions("tto10k", sg, g, topo, idx, refs, d_split=20, d_moved=20)
+    out = run(g, topo, d_split=20, d_moved=20, precision=1)
     # every cell of the batch matches the oracle's descriptor mapping
     for i in range(0, c["batch"], 97):
         ns, nm, cell = dcflow.descriptors(sg, topo[i], 20, 20)
@@ -158,14 +182,15 @@ def test_invalid_genomes_reported():
     g.sync_status()  # cleared
 
 
-def test_deterministic_and_order_independent():
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_deterministic_and_order_independent(prec):
     sg = with_limits(config_grid("tto30", seed=4), 5)
     topo = random_topologies(sg, 200, seed=8)
     g = lib_grid(sg)
-    a = run(g, topo)
-    b = run(g, topo)
+    a = run(g, topo, precision=prec)
+    b = run(g, topo, precision=prec)
     perm = np.random.default_rng(0).permutation(200)
-    c = run(g, topo[perm])
+    c = run(g, topo[perm], precision=prec)
     for k in ["fitness", "desc", "cell", "island", "metrics", "fmax"]:
         np.testing.assert_array_equal(a[k], b[k])
         np.testing.assert_array_equal(a[k][perm], c[k])
