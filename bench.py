@@ -195,7 +195,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="tto10k")
     ap.add_argument("--batch", type=int, default=0)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "bf16"])
+    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3", "bf16x3", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-outages", type=int, default=120)
     args = ap.parse_args()
@@ -209,12 +209,12 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_2605_10128_b300 import Archive, PREC_BF16, PREC_BF16X3, PREC_FP32
+    from paper_2605_10128_b300 import Archive, PREC_BF16, PREC_BF16X3, PREC_FP32, PREC_TF32X3
 
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
-    prec = {"fp32": PREC_FP32, "bf16x3": PREC_BF16X3, "bf16": PREC_BF16}[args.precision]
+    prec = {"fp32": PREC_FP32, "tf32x3": PREC_TF32X3, "bf16x3": PREC_BF16X3, "bf16": PREC_BF16}[args.precision]
     c = CONFIGS[args.config]
     B = args.batch or c["batch"]
     ds, dm = c["archive"]

@@ -33,14 +33,27 @@ namespace tto {
 
 // ------------------------------------------------------- factor layouts
 // FP32 sweep: U [B][E_mon_pad][KP], V [B][O_pad][KP], g [B][O_pad][TT].
-// Tensor-core sweep (mma m16n8k16, bf16 in, fp32 accumulate), fragment order:
-//   A = [U_hi | U_lo] (16 x 16 per 16-row tile): Ua [B][E_mon_pad/16][lane][4 x bf16x2]
-//   B columns (8 outages per tile): Vb [B][O_pad/8][lane][2] = (V_hi pair, V_lo pair)
+// Tensor-core sweep, mma fragment order (lane = 4 g + q):
+//   bf16 (m16n8k16): A = [U_hi | U_lo] per 16-row tile, Ua [B][E_mon_pad/16][lane][4 x bf16x2];
+//     B per 8-outage tile, Vb [B][O_pad/8][lane][2] = (V_hi pair, V_lo pair).
+//   tf32 (m16n8k8): Ua [B][E_mon_pad/16][lane][8] = (U_hi a0..a3, U_lo a0..a3);
+//     Vb [B][O_pad/8][lane][4] = (V_hi b0 b1, V_lo b0 b1).
 //   g [B][O_pad/8][q][TT][2]: the two outage columns 2q, 2q+1 a lane owns.
 __device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
   const uint32_t a = __bfloat16_as_ushort(__float2bfloat16_rn(lo_elem));
   const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn(hi_elem));
   return a | (b << 16);
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
 }
 
 __device__ __forceinline__ void split_bf16(float x, float& hi, float& lo) {
@@ -54,9 +67,22 @@ __device__ void store_row_factors(const EvalArgs& a, int b, int l, const float* 
     for (int j = 0; j < a.KP; ++j) Urow[j] = u[j];
     return;
   }
+  const int mt = l >> 4, r = l & 15, g = r & 7, half = r >> 3;
+  if (a.precision == TTO_PREC_TF32X3) {
+    uint32_t hi[TTO_MAX_K], lo[TTO_MAX_K];
+    for (int j = 0; j < TTO_MAX_K; ++j) split_tf32(u[j], hi[j], lo[j]);
+    uint32_t* base = reinterpret_cast<uint32_t*>(a.U) + ((size_t)b * (a.E_mon_pad >> 4) + mt) * 256;
+    for (int q = 0; q < 4; ++q) {
+      uint32_t* w = base + (g * 4 + q) * 8;
+      w[half] = hi[q];
+      w[2 + half] = hi[q + 4];
+      w[4 + half] = lo[q];
+      w[6 + half] = lo[q + 4];
+    }
+    return;
+  }
   float hi[TTO_MAX_K], lo[TTO_MAX_K];
   for (int j = 0; j < TTO_MAX_K; ++j) split_bf16(u[j], hi[j], lo[j]);
-  const int mt = l >> 4, r = l & 15, g = r & 7, half = r >> 3;
   uint32_t* base = reinterpret_cast<uint32_t*>(a.U) + ((size_t)b * (a.E_mon_pad >> 4) + mt) * 128;
   for (int q = 0; q < 4; ++q) {
     uint32_t* w = base + (g * 4 + q) * 4;
@@ -74,14 +100,27 @@ __device__ void store_col_factors(const EvalArgs& a, int b, int c, const float* 
     for (int t = 0; t < TT; ++t) grow[t] = gv[t];
     return;
   }
-  float hi[TTO_MAX_K], lo[TTO_MAX_K];
-  for (int j = 0; j < TTO_MAX_K; ++j) split_bf16(v[j], hi[j], lo[j]);
   const int ntl = c >> 3, cc = c & 7;
   const size_t tile = (size_t)b * (a.O_pad >> 3) + ntl;
-  uint32_t* vb = reinterpret_cast<uint32_t*>(a.V) + tile * 64;
-  for (int q = 0; q < 4; ++q) {
-    vb[(cc * 4 + q) * 2 + 0] = pack_bf16(hi[2 * q], hi[2 * q + 1]);
-    vb[(cc * 4 + q) * 2 + 1] = pack_bf16(lo[2 * q], lo[2 * q + 1]);
+  if (a.precision == TTO_PREC_TF32X3) {
+    uint32_t hi[TTO_MAX_K], lo[TTO_MAX_K];
+    for (int j = 0; j < TTO_MAX_K; ++j) split_tf32(v[j], hi[j], lo[j]);
+    uint32_t* vb = reinterpret_cast<uint32_t*>(a.V) + tile * 128;
+    for (int q = 0; q < 4; ++q) {
+      uint32_t* w = vb + (cc * 4 + q) * 4;
+      w[0] = hi[q];
+      w[1] = hi[q + 4];
+      w[2] = lo[q];
+      w[3] = lo[q + 4];
+    }
+  } else {
+    float hi[TTO_MAX_K], lo[TTO_MAX_K];
+    for (int j = 0; j < TTO_MAX_K; ++j) split_bf16(v[j], hi[j], lo[j]);
+    uint32_t* vb = reinterpret_cast<uint32_t*>(a.V) + tile * 64;
+    for (int q = 0; q < 4; ++q) {
+      vb[(cc * 4 + q) * 2 + 0] = pack_bf16(hi[2 * q], hi[2 * q + 1]);
+      vb[(cc * 4 + q) * 2 + 1] = pack_bf16(lo[2 * q], lo[2 * q + 1]);
+    }
   }
   float* gq = a.gg + (tile * 4 + (cc >> 1)) * TT * 2 + (cc & 1);
   for (int t = 0; t < TT; ++t) gq[2 * t] = gv[t];
@@ -380,8 +419,8 @@ int ensure_workspace(tto_grid* g, int B, int T) {
   int nT = T > w.cap_T ? T : w.cap_T;
   free_workspace(g);
   const size_t Ep = g->E_mon_pad, Op = g->O_pad;
-  TTO_CUDA_TRY(cudaMalloc(&w.U, (size_t)nB * Ep * 8 * sizeof(float)));
-  TTO_CUDA_TRY(cudaMalloc(&w.V, (size_t)nB * Op * 8 * sizeof(float)));
+  TTO_CUDA_TRY(cudaMalloc(&w.U, (size_t)nB * Ep * 16 * sizeof(float)));
+  TTO_CUDA_TRY(cudaMalloc(&w.V, (size_t)nB * Op * 16 * sizeof(float)));
   TTO_CUDA_TRY(cudaMalloc(&w.fp, (size_t)nB * nT * Ep * sizeof(float)));
   TTO_CUDA_TRY(cudaMalloc(&w.gg, (size_t)nB * Op * nT * sizeof(float)));
   TTO_CUDA_TRY(cudaMalloc(&w.info, (size_t)nB * sizeof(TopoInfo)));
@@ -412,7 +451,7 @@ int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, 
   if (B < 0) return set_error(TTO_E_ARG, "negative batch");
   if (B > 0 && (!topo || !fitness)) return set_error(TTO_E_ARG, "null topology or fitness buffer");
   if (o->d_split < 1 || o->d_moved < 1) return set_error(TTO_E_ARG, "archive extents must be >= 1");
-  if (o->precision < TTO_PREC_FP32 || o->precision > TTO_PREC_BF16) return set_error(TTO_E_ARG, "unknown precision");
+  if (o->precision < TTO_PREC_FP32 || o->precision > TTO_PREC_TF32X3) return set_error(TTO_E_ARG, "unknown precision");
   if (o->fitness_kind != TTO_FIT_WORKLOAD && o->fitness_kind != TTO_FIT_F1) return set_error(TTO_E_ARG, "unknown fitness kind");
   if (n_t < 0 || n_t > TTO_MAX_T || (tsel == nullptr && g->T > TTO_MAX_T))
     return set_error(TTO_E_ARG, "n_t must be in [1, %d]", TTO_MAX_T);

@@ -4,11 +4,12 @@
 //     N'_lc = N_lc - U_l . V_c        (rank k <= 8)
 // and the post-contingency flow of every timestep is
 //     F_lc[t] = f'_l[t] - N'_lc g_c[t],     fmax_l[t] = max_c |F_lc[t]|.
-// One mma.sync m16n8k16 (bf16 in, fp32 accumulate) per 16 x 8 tile forms
-// D = [U_hi | U_lo] [V_hi ; V_hi] + C with the accumulator C preloaded with
-// -N (stored once per grid in C-fragment order), and a second mma adds
-// U_hi V_lo, so D = U V^T - N = -N' to about 2^-16 relative accuracy of the
-// low-rank term (TTO_PREC_BF16X3; TTO_PREC_BF16 keeps only U_hi V_hi).  The
+// Per 16 x 8 tile, mma.sync accumulates the split products of U and V onto an
+// accumulator preloaded with -N (stored once per grid in C-fragment order), so
+// D = U V^T - N = -N'.  Modes: TF32X3 = three m16n8k8 tf32 products
+// U_hi V_hi + U_lo V_hi + U_hi V_lo (about 2^-22 relative error of the low-rank
+// term); BF16X3 = two m16n8k16 bf16 products [U_hi|U_lo][V_hi;V_hi] and
+// [U_hi|U_lo][V_lo;0] (about 2^-16); BF16 = U_hi V_hi only.  The
 // accumulator registers hold each lane's four (l, c) entries, and the epilogue
 // runs on them directly: F = fma(D, g_c[t], f'_l[t]) and a max of |F| per row
 // and timestep, two FP32 instructions per (l, c, t).  Islanding outages carry
@@ -30,11 +31,36 @@ constexpr int kTCWarps = 8;           // topologies per CTA
 constexpr int kSwB = 16, kSwG = 16;   // launch-order tile: row bands x topology groups
 constexpr int kMaxTChunk = 8;         // timesteps per sweep pass
 
-__device__ __forceinline__ void mma_bf16(float4& d, const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+__device__ __forceinline__ void mma_bf16(float4& d, const uint32_t* a, uint32_t b0, uint32_t b1) {
   asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
       "{%0,%1,%2,%3};"
       : "+f"(d.x), "+f"(d.y), "+f"(d.z), "+f"(d.w)
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void mma_tf32(float4& d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d.x), "+f"(d.y), "+f"(d.z), "+f"(d.w)
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Low-rank modes of the tensor-core sweep.
+enum { kModeBF16x3 = 0, kModeBF16 = 1, kModeTF32x3 = 2 };
+
+template <int BW>
+__device__ __forceinline__ void load_b(uint32_t (&vb)[BW], const uint32_t* p) {
+  if constexpr (BW == 2) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+    vb[0] = v.x;
+    vb[1] = v.y;
+  } else {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+    vb[0] = v.x;
+    vb[1] = v.y;
+    vb[2] = v.z;
+    vb[3] = v.w;
+  }
 }
 
 template <int TC>
@@ -55,7 +81,7 @@ __device__ __forceinline__ void load_g(float (&gv)[2 * TC], const float* p) {
   }
 }
 
-template <int TC, int MW, bool SPLIT>
+template <int TC, int MW, int MODE>
 __global__ void __launch_bounds__(kTCWarps * 32, 2)
     sweep_tc_kernel(EvalArgs a, int t0, int tci, int n_tchunks, int n_bands, int n_groups) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
@@ -71,16 +97,22 @@ __global__ void __launch_bounds__(kTCWarps * 32, 2)
   const int mt0 = band * MW;
   const size_t Ep = a.E_mon_pad;
 
-  uint32_t A[MW][4];
+  constexpr bool TF = MODE == kModeTF32x3;
+  constexpr int AW = TF ? 8 : 4;  // A-fragment words per lane
+  constexpr int BW = TF ? 4 : 2;  // B-fragment words per lane
+  uint32_t A[MW][AW];
   float f[MW][2][TC], m[MW][2][TC];
   const uint4* Ua = reinterpret_cast<const uint4*>(a.U);
 #pragma unroll
   for (int i = 0; i < MW; ++i) {
-    const uint4 u = __ldg(Ua + ((size_t)b * n_mt + mt0 + i) * 32 + lane);
-    A[i][0] = u.x;
-    A[i][1] = u.y;
-    A[i][2] = u.z;
-    A[i][3] = u.w;
+#pragma unroll
+    for (int w = 0; w < AW / 4; ++w) {
+      const uint4 u = __ldg(Ua + (((size_t)b * n_mt + mt0 + i) * 32 + lane) * (AW / 4) + w);
+      A[i][4 * w + 0] = u.x;
+      A[i][4 * w + 1] = u.y;
+      A[i][4 * w + 2] = u.z;
+      A[i][4 * w + 3] = u.w;
+    }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int row = (mt0 + i) * 16 + g + 8 * h;
@@ -92,37 +124,47 @@ __global__ void __launch_bounds__(kTCWarps * 32, 2)
     }
   }
   const float4* Nf = a.Nf + (size_t)mt0 * n_nt * 32 + lane;
-  const uint2* Vb = reinterpret_cast<const uint2*>(a.V) + (size_t)b * n_nt * 32 + lane;
+  const uint32_t* Vb = reinterpret_cast<const uint32_t*>(a.V) + ((size_t)b * n_nt * 32 + lane) * BW;
   const float* gq = a.gg + ((size_t)b * n_nt * 4 + q) * TT * 2 + t0 * 2;
   const size_t gstride = (size_t)4 * TT * 2;
 
   float4 nf_n[MW];
-  uint2 vb_n;
+  uint32_t vb_n[BW];
   float gv_n[2 * TC];
 #pragma unroll
   for (int i = 0; i < MW; ++i) nf_n[i] = __ldg(Nf + (size_t)i * n_nt * 32);
-  vb_n = __ldg(Vb);
+  load_b<BW>(vb_n, Vb);
   load_g<TC>(gv_n, gq);
 
   for (int nt = 0; nt < n_nt; ++nt) {
     float4 nf[MW];
 #pragma unroll
     for (int i = 0; i < MW; ++i) nf[i] = nf_n[i];
-    const uint2 vb = vb_n;
+    uint32_t vb[BW];
+#pragma unroll
+    for (int j = 0; j < BW; ++j) vb[j] = vb_n[j];
     float gv[2 * TC];
 #pragma unroll
     for (int j = 0; j < 2 * TC; ++j) gv[j] = gv_n[j];
     if (nt + 1 < n_nt) {
 #pragma unroll
       for (int i = 0; i < MW; ++i) nf_n[i] = __ldg(Nf + ((size_t)i * n_nt + nt + 1) * 32);
-      vb_n = __ldg(Vb + (size_t)(nt + 1) * 32);
+      load_b<BW>(vb_n, Vb + (size_t)(nt + 1) * 32 * BW);
       load_g<TC>(gv_n, gq + (nt + 1) * gstride);
     }
 #pragma unroll
     for (int i = 0; i < MW; ++i) {
       float4 d = nf[i];
-      mma_bf16(d, A[i], vb.x, SPLIT ? vb.x : 0u);
-      if (SPLIT) mma_bf16(d, A[i], vb.y, 0u);
+      if (MODE == kModeTF32x3) {
+        mma_tf32(d, &A[i][0], vb[0], vb[1]);  // U_hi V_hi
+        mma_tf32(d, &A[i][4], vb[0], vb[1]);  // U_lo V_hi
+        mma_tf32(d, &A[i][0], vb[2], vb[3]);  // U_hi V_lo
+      } else if (MODE == kModeBF16x3) {
+        mma_bf16(d, &A[i][0], vb[0], vb[0]);  // [U_hi | U_lo] [V_hi ; V_hi]
+        mma_bf16(d, &A[i][0], vb[1], 0u);     // [U_hi | U_lo] [V_lo ; 0]
+      } else {
+        mma_bf16(d, &A[i][0], vb[0], 0u);     // U_hi V_hi
+      }
 #pragma unroll
       for (int t = 0; t < TC; ++t) {
         const float g0 = gv[2 * t], g1 = gv[2 * t + 1];
@@ -210,25 +252,25 @@ size_t max_parts(const tto_grid* g) {
   return fp32 > tc ? fp32 : tc;
 }
 
-template <int TC, int MW, bool SPLIT>
+template <int TC, int MW, int MODE>
 static int launch_tc(EvalArgs& a, int t0, int tci, int n_tchunks, cudaStream_t s) {
   const int n_bands = a.E_mon_pad / (16 * MW);
   const int n_groups = (a.B + kTCWarps - 1) / kTCWarps;
   const int tiles_b = (n_bands + kSwB - 1) / kSwB, tiles_g = (n_groups + kSwG - 1) / kSwG;
   const size_t blocks = (size_t)tiles_b * tiles_g * kSwB * kSwG;
   if (blocks > 0x7fffffffu) return set_error(TTO_E_ARG, "batch too large for one sweep launch");
-  sweep_tc_kernel<TC, MW, SPLIT><<<(unsigned)blocks, kTCWarps * 32, 0, s>>>(a, t0, tci, n_tchunks, n_bands, n_groups);
+  sweep_tc_kernel<TC, MW, MODE><<<(unsigned)blocks, kTCWarps * 32, 0, s>>>(a, t0, tci, n_tchunks, n_bands, n_groups);
   TTO_CUDA_TRY(cudaGetLastError());
   return TTO_OK;
 }
 
-template <bool SPLIT>
+template <int MODE>
 static int launch_tc_chunk(EvalArgs& a, int tc, int t0, int tci, int n_tchunks, cudaStream_t s) {
   switch (tc) {
-    case 1: return launch_tc<1, 2, SPLIT>(a, t0, tci, n_tchunks, s);
-    case 2: return launch_tc<2, 2, SPLIT>(a, t0, tci, n_tchunks, s);
-    case 4: return launch_tc<4, 2, SPLIT>(a, t0, tci, n_tchunks, s);
-    case 8: return launch_tc<8, 1, SPLIT>(a, t0, tci, n_tchunks, s);
+    case 1: return launch_tc<1, 2, MODE>(a, t0, tci, n_tchunks, s);
+    case 2: return launch_tc<2, 2, MODE>(a, t0, tci, n_tchunks, s);
+    case 4: return launch_tc<4, 2, MODE>(a, t0, tci, n_tchunks, s);
+    case 8: return launch_tc<8, 1, MODE>(a, t0, tci, n_tchunks, s);
   }
   return set_error(TTO_E_ARG, "unsupported timestep chunk %d", tc);
 }
@@ -240,8 +282,13 @@ int launch_sweep_tc(EvalArgs& a, cudaStream_t s) {
   const int mw = tc <= 4 ? 2 : 1;
   a.n_parts = (a.E_mon_pad / (16 * mw)) * n_tchunks;
   for (int ci = 0; ci < n_tchunks; ++ci) {
-    const int rc = a.precision == TTO_PREC_BF16 ? launch_tc_chunk<false>(a, tc, ci * tc, ci, n_tchunks, s)
-                                                : launch_tc_chunk<true>(a, tc, ci * tc, ci, n_tchunks, s);
+    int rc;
+    if (a.precision == TTO_PREC_TF32X3)
+      rc = launch_tc_chunk<kModeTF32x3>(a, tc, ci * tc, ci, n_tchunks, s);
+    else if (a.precision == TTO_PREC_BF16)
+      rc = launch_tc_chunk<kModeBF16>(a, tc, ci * tc, ci, n_tchunks, s);
+    else
+      rc = launch_tc_chunk<kModeBF16x3>(a, tc, ci * tc, ci, n_tchunks, s);
     if (rc) return rc;
   }
   return TTO_OK;
