@@ -38,7 +38,8 @@ namespace tto {
 //     B per 8-outage tile, Vb [B][O_pad/8][lane][2] = (V_hi pair, V_lo pair).
 //   tf32 (m16n8k8): Ua [B][E_mon_pad/16][lane][8] = (U_hi a0..a3, U_lo a0..a3);
 //     Vb [B][O_pad/8][lane][4] = (V_hi b0 b1, V_lo b0 b1).
-//   g [B][O_pad/8][q][TT][2]: the two outage columns 2q, 2q+1 a lane owns.
+//   g [B][n_tch][O_pad/8][q][TC][2]: per chunk of TC timesteps, the two outage
+//     columns 2q, 2q+1 a lane owns.
 __device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
   const uint32_t a = __bfloat16_as_ushort(__float2bfloat16_rn(lo_elem));
   const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn(hi_elem));
@@ -122,8 +123,12 @@ __device__ void store_col_factors(const EvalArgs& a, int b, int c, const float* 
       vb[(cc * 4 + q) * 2 + 1] = pack_bf16(lo[2 * q], lo[2 * q + 1]);
     }
   }
-  float* gq = a.gg + (tile * 4 + (cc >> 1)) * TT * 2 + (cc & 1);
-  for (int t = 0; t < TT; ++t) gq[2 * t] = gv[t];
+  const int TC = a.TC, n_nt = a.O_pad >> 3;
+  for (int t = 0; t < TT; ++t) {
+    const int ci = t / TC, tt = t - ci * TC;
+    const size_t slab = ((size_t)b * a.n_tch + ci) * n_nt + ntl;
+    a.gg[((slab * 4 + (cc >> 1)) * TC + tt) * 2 + (cc & 1)] = gv[t];
+  }
 }
 
 // ---------------------------------------------------------------- split update
@@ -499,6 +504,8 @@ int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, 
   a.k_max = g->k_max;
   a.n_t = n_t;
   a.TT = TT;
+  a.TC = TT <= 4 ? TT : 8;
+  a.n_tch = (TT + a.TC - 1) / a.TC;
   a.KP = padded_K(g->k_max);
   a.d_split = o->d_split;
   a.d_moved = o->d_moved;

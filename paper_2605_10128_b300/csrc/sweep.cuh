@@ -29,6 +29,7 @@ struct EvalArgs {
   int* status;
   int E, n_bus, E_mon, O, E_mon_pad, O_pad, A, k_max;
   int n_t, TT, KP;
+  int TC, n_tch;  // tensor-core sweep: timesteps per pass and number of passes
   int tsel[TTO_MAX_T];
   int d_split, d_moved;
   int precision;

@@ -9,18 +9,24 @@
 // D = U V^T - N = -N'.  Modes: TF32X3 = three m16n8k8 tf32 products
 // U_hi V_hi + U_lo V_hi + U_hi V_lo (about 2^-22 relative error of the low-rank
 // term); BF16X3 = two m16n8k16 bf16 products [U_hi|U_lo][V_hi;V_hi] and
-// [U_hi|U_lo][V_lo;0] (about 2^-16); BF16 = U_hi V_hi only.  The
-// accumulator registers hold each lane's four (l, c) entries, and the epilogue
-// runs on them directly: F = fma(D, g_c[t], f'_l[t]) and a max of |F| per row
-// and timestep, two FP32 instructions per (l, c, t).  Islanding outages carry
-// g = NaN, which fmaxf ignores.
+// [U_hi|U_lo][V_lo;0] (about 2^-16); BF16 = U_hi V_hi only.  The accumulator
+// registers hold each lane's four (l, c) entries, and the epilogue runs on them
+// directly: F = fma(D, g_c[t], f'_l[t]) and a max of |F| per row and timestep,
+// two FP32 instructions per (l, c, t).  Islanding outages carry g = NaN, which
+// fmaxf ignores.
 //
 // CTA = 8 warps = 8 topologies on one band of 16*MW monitored rows; each warp
 // walks every outage column of its topology, so the running maxima stay in
-// registers and every warp reduces its own rows at the end (no atomics).  The
-// 8 warps of a CTA read the same -N tiles (L1 hits after the first), and the
-// launch order is tiled (16 row bands x 16 topology groups) so that the -N
-// band and the column factors of the co-resident CTAs stay in L2.
+// registers and every warp reduces its own rows at the end (no atomics).
+// Operands stream through a two-slot shared-memory ring filled by TMA bulk
+// copies (cp.async.bulk, completion counted on an mbarrier): per stage of 8
+// outage tiles, the -N slab of the band (read once, used by all 8 warps) and
+// each warp's column factors V and g.  One lane of warp 0 issues the copies of
+// stage s+2 once every warp has released stage s (a second mbarrier).  Every
+// wait is bounded; a wait that gives up sets the status word to TTO_E_TIMEOUT,
+// drains the copies already issued, and ends the kernel.  The launch order is
+// tiled (16 row bands x 16 topology groups) so that the -N band and the
+// column factors of co-resident CTAs stay in L2.
 #include <cuda_bf16.h>
 
 #include "sweep.cuh"
@@ -30,6 +36,11 @@ namespace tto {
 constexpr int kTCWarps = 8;           // topologies per CTA
 constexpr int kSwB = 16, kSwG = 16;   // launch-order tile: row bands x topology groups
 constexpr int kMaxTChunk = 8;         // timesteps per sweep pass
+constexpr int kSN = 8;                // outage tiles (8 columns each) per pipeline stage
+constexpr int kSlots = 2;             // pipeline depth
+constexpr long long kWaitCycles = 1ll << 31;  // give up after ~1 s at 2 GHz
+
+enum { kModeBF16x3 = 0, kModeBF16 = 1, kModeTF32x3 = 2 };
 
 __device__ __forceinline__ void mma_bf16(float4& d, const uint32_t* a, uint32_t b0, uint32_t b1) {
   asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -45,61 +56,123 @@ __device__ __forceinline__ void mma_tf32(float4& d, const uint32_t* a, uint32_t 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// Low-rank modes of the tensor-core sweep.
-enum { kModeBF16x3 = 0, kModeBF16 = 1, kModeTF32x3 = 2 };
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
 
-template <int BW>
-__device__ __forceinline__ void load_b(uint32_t (&vb)[BW], const uint32_t* p) {
-  if constexpr (BW == 2) {
-    const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
-    vb[0] = v.x;
-    vb[1] = v.y;
-  } else {
-    const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
-    vb[0] = v.x;
-    vb[1] = v.y;
-    vb[2] = v.z;
-    vb[3] = v.w;
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity to complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_test(bar, parity)) return true;
+  const long long t0 = clock64();
+  for (;;) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_test(bar, parity)) return true;
+    if (clock64() - t0 > kWaitCycles) return false;
   }
 }
 
-template <int TC>
-__device__ __forceinline__ void load_g(float (&gv)[2 * TC], const float* p) {
-  if constexpr (TC == 1) {
-    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
-    gv[0] = v.x;
-    gv[1] = v.y;
-  } else {
-#pragma unroll
-    for (int i = 0; i < TC / 2; ++i) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(p) + i);
-      gv[4 * i + 0] = v.x;
-      gv[4 * i + 1] = v.y;
-      gv[4 * i + 2] = v.z;
-      gv[4 * i + 3] = v.w;
-    }
-  }
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
 }
+
+template <int MODE>
+struct TCMode {
+  static constexpr int AW = MODE == kModeTF32x3 ? 8 : 4;  // A-fragment words per lane
+  static constexpr int BW = MODE == kModeTF32x3 ? 4 : 2;  // B-fragment words per lane
+};
+
+// Shared-memory layout of one pipeline slot.
+template <int MW, int MODE, int TC>
+struct Slot {
+  static constexpr uint32_t kNf = MW * kSN * 32 * 16;                     // -N fragments of the band
+  static constexpr uint32_t kVb = kSN * 32 * TCMode<MODE>::BW * 4;        // per warp
+  static constexpr uint32_t kG = kSN * 4 * TC * 2 * 4;                    // per warp
+  static constexpr uint32_t kWarp = kVb + kG;
+  static constexpr uint32_t kBytes = kNf + kTCWarps * kWarp;
+};
 
 template <int TC, int MW, int MODE>
 __global__ void __launch_bounds__(kTCWarps * 32, 2)
-    sweep_tc_kernel(EvalArgs a, int t0, int tci, int n_tchunks, int n_bands, int n_groups) {
+    sweep_tc_kernel(EvalArgs a, int tci, int n_bands, int n_groups) {
+  using S = Slot<MW, MODE, TC>;
+  constexpr int AW = TCMode<MODE>::AW, BW = TCMode<MODE>::BW;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[kSlots], empty[kSlots];
+
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
   const int tiles_b = (n_bands + kSwB - 1) / kSwB;
   const int tile = blockIdx.x / (kSwB * kSwG), within = blockIdx.x % (kSwB * kSwG);
   const int band = (tile % tiles_b) * kSwB + within % kSwB;
   const int grp = (tile / tiles_b) * kSwG + within / kSwB;
-  if (band >= n_bands || grp >= n_groups) return;
+  if (band >= n_bands || grp >= n_groups) return;  // CTA-uniform
+  const int n_active = min(kTCWarps, a.B - grp * kTCWarps);
   const int b = grp * kTCWarps + warp;
-  if (b >= a.B) return;  // warp-uniform; the kernel has no block barrier
   const int TT = a.TT;
+  const int t0 = tci * TC;
   const int n_mt = a.E_mon_pad >> 4, n_nt = a.O_pad >> 3;
+  const int n_stages = n_nt / kSN;
   const int mt0 = band * MW;
   const size_t Ep = a.E_mon_pad;
+  const bool producer = threadIdx.x == 0;
 
-  constexpr bool TF = MODE == kModeTF32x3;
-  constexpr int AW = TF ? 8 : 4;  // A-fragment words per lane
-  constexpr int BW = TF ? 4 : 2;  // B-fragment words per lane
+  if (producer) {
+    for (int sl = 0; sl < kSlots; ++sl) {
+      mbar_init(&full[sl], 1);
+      mbar_init(&empty[sl], n_active);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  // stage s -> slot s % kSlots
+  auto issue = [&](int s) {
+    const int sl = s % kSlots;
+    unsigned char* base = smem + (size_t)sl * S::kBytes;
+    mbar_expect_tx(&full[sl], S::kNf + n_active * S::kWarp);
+    const int nt0 = s * kSN;
+    for (int i = 0; i < MW; ++i)
+      bulk_copy(base + i * (kSN * 512), a.Nf + ((size_t)(mt0 + i) * n_nt + nt0) * 32, kSN * 512, &full[sl]);
+    for (int w = 0; w < n_active; ++w) {
+      const int bw = grp * kTCWarps + w;
+      unsigned char* wb = base + S::kNf + w * S::kWarp;
+      bulk_copy(wb, reinterpret_cast<const uint32_t*>(a.V) + ((size_t)bw * n_nt + nt0) * 32 * BW, S::kVb,
+                &full[sl]);
+      bulk_copy(wb + S::kVb, a.gg + (((size_t)bw * a.n_tch + tci) * n_nt + nt0) * 4 * TC * 2, S::kG,
+                &full[sl]);
+    }
+  };
+  if (producer)
+    for (int s = 0; s < kSlots && s < n_stages; ++s) issue(s);
+
+  if (warp >= n_active) return;  // past the batch end; not counted by the empty barriers
+
   uint32_t A[MW][AW];
   float f[MW][2][TC], m[MW][2][TC];
   const uint4* Ua = reinterpret_cast<const uint4*>(a.U);
@@ -123,55 +196,97 @@ __global__ void __launch_bounds__(kTCWarps * 32, 2)
       }
     }
   }
-  const float4* Nf = a.Nf + (size_t)mt0 * n_nt * 32 + lane;
-  const uint32_t* Vb = reinterpret_cast<const uint32_t*>(a.V) + ((size_t)b * n_nt * 32 + lane) * BW;
-  const float* gq = a.gg + ((size_t)b * n_nt * 4 + q) * TT * 2 + t0 * 2;
-  const size_t gstride = (size_t)4 * TT * 2;
 
-  float4 nf_n[MW];
-  uint32_t vb_n[BW];
-  float gv_n[2 * TC];
-#pragma unroll
-  for (int i = 0; i < MW; ++i) nf_n[i] = __ldg(Nf + (size_t)i * n_nt * 32);
-  load_b<BW>(vb_n, Vb);
-  load_g<TC>(gv_n, gq);
-
-  for (int nt = 0; nt < n_nt; ++nt) {
-    float4 nf[MW];
-#pragma unroll
-    for (int i = 0; i < MW; ++i) nf[i] = nf_n[i];
-    uint32_t vb[BW];
-#pragma unroll
-    for (int j = 0; j < BW; ++j) vb[j] = vb_n[j];
-    float gv[2 * TC];
-#pragma unroll
-    for (int j = 0; j < 2 * TC; ++j) gv[j] = gv_n[j];
-    if (nt + 1 < n_nt) {
-#pragma unroll
-      for (int i = 0; i < MW; ++i) nf_n[i] = __ldg(Nf + ((size_t)i * n_nt + nt + 1) * 32);
-      load_b<BW>(vb_n, Vb + (size_t)(nt + 1) * 32 * BW);
-      load_g<TC>(gv_n, gq + (nt + 1) * gstride);
+  bool ok = true;
+  int issued = kSlots < n_stages ? kSlots : n_stages;
+  int pending = 0;  // first stage whose copies may still be in flight
+  for (int s = 0; s < n_stages; ++s) {
+    const int sl = s % kSlots;
+    const uint32_t par = (uint32_t)(s / kSlots) & 1u;
+    // every lane observes the stage's completion; the decision is warp-uniform
+    if (!__all_sync(0xffffffffu, mbar_wait(&full[sl], par))) {
+      ok = false;
+      break;
     }
+    pending = s + 1;
+    const unsigned char* base = smem + (size_t)sl * S::kBytes;
+    const float4* nfs = reinterpret_cast<const float4*>(base) + lane;
+    const uint32_t* vbs = reinterpret_cast<const uint32_t*>(base + S::kNf + warp * S::kWarp) + lane * BW;
+    const float* gs = reinterpret_cast<const float*>(base + S::kNf + warp * S::kWarp + S::kVb) + q * TC * 2;
 #pragma unroll
-    for (int i = 0; i < MW; ++i) {
-      float4 d = nf[i];
-      if (MODE == kModeTF32x3) {
-        mma_tf32(d, &A[i][0], vb[0], vb[1]);  // U_hi V_hi
-        mma_tf32(d, &A[i][4], vb[0], vb[1]);  // U_lo V_hi
-        mma_tf32(d, &A[i][0], vb[2], vb[3]);  // U_hi V_lo
-      } else if (MODE == kModeBF16x3) {
-        mma_bf16(d, &A[i][0], vb[0], vb[0]);  // [U_hi | U_lo] [V_hi ; V_hi]
-        mma_bf16(d, &A[i][0], vb[1], 0u);     // [U_hi | U_lo] [V_lo ; 0]
+    for (int j = 0; j < kSN; ++j) {
+      uint32_t vb[BW];
+      if constexpr (BW == 2) {
+        const uint2 v = *reinterpret_cast<const uint2*>(vbs + j * 32 * BW);
+        vb[0] = v.x;
+        vb[1] = v.y;
       } else {
-        mma_bf16(d, &A[i][0], vb[0], 0u);     // U_hi V_hi
+        const uint4 v = *reinterpret_cast<const uint4*>(vbs + j * 32 * BW);
+        vb[0] = v.x;
+        vb[1] = v.y;
+        vb[2] = v.z;
+        vb[3] = v.w;
+      }
+      float gv[2 * TC];
+      if constexpr (TC == 1) {
+        const float2 v = *reinterpret_cast<const float2*>(gs + j * 8 * TC);
+        gv[0] = v.x;
+        gv[1] = v.y;
+      } else {
+#pragma unroll
+        for (int x = 0; x < TC / 2; ++x) {
+          const float4 v = *reinterpret_cast<const float4*>(gs + j * 8 * TC + 4 * x);
+          gv[4 * x + 0] = v.x;
+          gv[4 * x + 1] = v.y;
+          gv[4 * x + 2] = v.z;
+          gv[4 * x + 3] = v.w;
+        }
       }
 #pragma unroll
-      for (int t = 0; t < TC; ++t) {
-        const float g0 = gv[2 * t], g1 = gv[2 * t + 1];
-        m[i][0][t] = fmaxf(fmaxf(m[i][0][t], fabsf(fmaf(d.x, g0, f[i][0][t]))), fabsf(fmaf(d.y, g1, f[i][0][t])));
-        m[i][1][t] = fmaxf(fmaxf(m[i][1][t], fabsf(fmaf(d.z, g0, f[i][1][t]))), fabsf(fmaf(d.w, g1, f[i][1][t])));
+      for (int i = 0; i < MW; ++i) {
+        float4 d = nfs[(i * kSN + j) * 32];
+        if (MODE == kModeTF32x3) {
+          mma_tf32(d, &A[i][0], vb[0], vb[1]);  // U_hi V_hi
+          mma_tf32(d, &A[i][4], vb[0], vb[1]);  // U_lo V_hi
+          mma_tf32(d, &A[i][0], vb[2], vb[3]);  // U_hi V_lo
+        } else if (MODE == kModeBF16x3) {
+          mma_bf16(d, &A[i][0], vb[0], vb[0]);  // [U_hi | U_lo] [V_hi ; V_hi]
+          mma_bf16(d, &A[i][0], vb[1], 0u);     // [U_hi | U_lo] [V_lo ; 0]
+        } else {
+          mma_bf16(d, &A[i][0], vb[0], 0u);     // U_hi V_hi
+        }
+#pragma unroll
+        for (int t = 0; t < TC; ++t) {
+          const float g0 = gv[2 * t], g1 = gv[2 * t + 1];
+          m[i][0][t] = fmaxf(fmaxf(m[i][0][t], fabsf(fmaf(d.x, g0, f[i][0][t]))), fabsf(fmaf(d.y, g1, f[i][0][t])));
+          m[i][1][t] = fmaxf(fmaxf(m[i][1][t], fabsf(fmaf(d.z, g0, f[i][1][t]))), fabsf(fmaf(d.w, g1, f[i][1][t])));
+        }
       }
     }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[sl]);
+    int refill = 1;
+    if (producer && s + kSlots < n_stages) {
+      refill = mbar_wait(&empty[sl], par) ? 1 : 0;
+      if (refill) {
+        issue(s + kSlots);
+        ++issued;
+      }
+    }
+    if (!__shfl_sync(0xffffffffu, refill, 0)) {  // reconverges warp 0 after the producer step
+      ok = false;
+      break;
+    }
+  }
+
+  if (!ok) {
+    atomicExch(a.status, TTO_E_TIMEOUT);
+    if (producer) {
+      // let the copies already in flight land before the CTA releases its
+      // shared memory
+      for (int s = pending; s < issued; ++s) mbar_wait(&full[s % kSlots], (uint32_t)(s / kSlots) & 1u);
+    }
+    return;
   }
 
   // rows: combine the four lanes that share a row, then per-row metrics
@@ -211,7 +326,7 @@ __global__ void __launch_bounds__(kTCWarps * 32, 2)
     ml = fmaxf(ml, __shfl_xor_sync(0xffffffffu, ml, o));
   }
   if (lane == 0) {
-    float* pp = a.part + ((size_t)b * a.n_parts + (size_t)band * n_tchunks + tci) * 4;
+    float* pp = a.part + ((size_t)b * a.n_parts + (size_t)band * a.n_tch + tci) * 4;
     pp[0] = over;
     pp[1] = cnt;
     pp[2] = ml;
@@ -253,42 +368,44 @@ size_t max_parts(const tto_grid* g) {
 }
 
 template <int TC, int MW, int MODE>
-static int launch_tc(EvalArgs& a, int t0, int tci, int n_tchunks, cudaStream_t s) {
+static int launch_tc(EvalArgs& a, int tci, cudaStream_t s) {
+  using S = Slot<MW, MODE, TC>;
+  const size_t smem = (size_t)kSlots * S::kBytes;
+  TTO_CUDA_TRY(cudaFuncSetAttribute(sweep_tc_kernel<TC, MW, MODE>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int n_bands = a.E_mon_pad / (16 * MW);
   const int n_groups = (a.B + kTCWarps - 1) / kTCWarps;
   const int tiles_b = (n_bands + kSwB - 1) / kSwB, tiles_g = (n_groups + kSwG - 1) / kSwG;
   const size_t blocks = (size_t)tiles_b * tiles_g * kSwB * kSwG;
   if (blocks > 0x7fffffffu) return set_error(TTO_E_ARG, "batch too large for one sweep launch");
-  sweep_tc_kernel<TC, MW, MODE><<<(unsigned)blocks, kTCWarps * 32, 0, s>>>(a, t0, tci, n_tchunks, n_bands, n_groups);
+  sweep_tc_kernel<TC, MW, MODE><<<(unsigned)blocks, kTCWarps * 32, smem, s>>>(a, tci, n_bands, n_groups);
   TTO_CUDA_TRY(cudaGetLastError());
   return TTO_OK;
 }
 
 template <int MODE>
-static int launch_tc_chunk(EvalArgs& a, int tc, int t0, int tci, int n_tchunks, cudaStream_t s) {
-  switch (tc) {
-    case 1: return launch_tc<1, 2, MODE>(a, t0, tci, n_tchunks, s);
-    case 2: return launch_tc<2, 2, MODE>(a, t0, tci, n_tchunks, s);
-    case 4: return launch_tc<4, 2, MODE>(a, t0, tci, n_tchunks, s);
-    case 8: return launch_tc<8, 1, MODE>(a, t0, tci, n_tchunks, s);
+static int launch_tc_chunk(EvalArgs& a, int tci, cudaStream_t s) {
+  switch (a.TC) {
+    case 1: return launch_tc<1, 2, MODE>(a, tci, s);
+    case 2: return launch_tc<2, 2, MODE>(a, tci, s);
+    case 4: return launch_tc<4, 2, MODE>(a, tci, s);
+    case 8: return launch_tc<8, 1, MODE>(a, tci, s);
   }
-  return set_error(TTO_E_ARG, "unsupported timestep chunk %d", tc);
+  return set_error(TTO_E_ARG, "unsupported timestep chunk %d", a.TC);
 }
 
 int launch_sweep_tc(EvalArgs& a, cudaStream_t s) {
-  const int TT = a.TT;
-  const int tc = TT <= 4 ? TT : kMaxTChunk;
-  const int n_tchunks = (TT + tc - 1) / tc;
-  const int mw = tc <= 4 ? 2 : 1;
-  a.n_parts = (a.E_mon_pad / (16 * mw)) * n_tchunks;
-  for (int ci = 0; ci < n_tchunks; ++ci) {
+  if ((a.O_pad >> 3) % kSN != 0) return set_error(TTO_E_ARG, "outage padding is not a multiple of the stage width");
+  const int mw = a.TC <= 4 ? 2 : 1;
+  a.n_parts = (a.E_mon_pad / (16 * mw)) * a.n_tch;
+  for (int ci = 0; ci < a.n_tch; ++ci) {
     int rc;
     if (a.precision == TTO_PREC_TF32X3)
-      rc = launch_tc_chunk<kModeTF32x3>(a, tc, ci * tc, ci, n_tchunks, s);
+      rc = launch_tc_chunk<kModeTF32x3>(a, ci, s);
     else if (a.precision == TTO_PREC_BF16)
-      rc = launch_tc_chunk<kModeBF16>(a, tc, ci * tc, ci, n_tchunks, s);
+      rc = launch_tc_chunk<kModeBF16>(a, ci, s);
     else
-      rc = launch_tc_chunk<kModeBF16x3>(a, tc, ci * tc, ci, n_tchunks, s);
+      rc = launch_tc_chunk<kModeBF16x3>(a, ci, s);
     if (rc) return rc;
   }
   return TTO_OK;
