@@ -31,7 +31,7 @@ from synth import CONFIGS, config_grid, limits_from_flows, random_topologies  # 
 
 METRIC = "N-1 topology evals/s (10k-bus)"
 UNIT = "evals/s"
-LAUNCHES_PER_STEP = 8  # propose, split update, sweep, metrics, 4 insert kernels
+LAUNCHES_PER_STEP = 8  # propose, split update, sweep, metrics, 4 insert kernels (+1 pack on tensor cores)
 
 
 def workload_desc(cfg, B):
@@ -195,7 +195,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="tto10k")
     ap.add_argument("--batch", type=int, default=0)
-    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3", "bf16x3", "bf16"])
+    ap.add_argument("--precision", default="fp16x3", choices=["fp32", "fp16x3", "tf32x3", "bf16x3", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-outages", type=int, default=120)
     args = ap.parse_args()
@@ -209,12 +209,13 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_2605_10128_b300 import Archive, PREC_BF16, PREC_BF16X3, PREC_FP32, PREC_TF32X3
+    from paper_2605_10128_b300 import Archive, PREC_BF16, PREC_BF16X3, PREC_FP16X3, PREC_FP32, PREC_TF32X3
 
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
-    prec = {"fp32": PREC_FP32, "tf32x3": PREC_TF32X3, "bf16x3": PREC_BF16X3, "bf16": PREC_BF16}[args.precision]
+    prec = {"fp32": PREC_FP32, "fp16x3": PREC_FP16X3, "tf32x3": PREC_TF32X3, "bf16x3": PREC_BF16X3,
+            "bf16": PREC_BF16}[args.precision]
     c = CONFIGS[args.config]
     B = args.batch or c["batch"]
     ds, dm = c["archive"]
@@ -317,7 +318,7 @@ def main():
                                   "metrics": stage_ms[2] / max(ncalls, 1)},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(B * g.k_max * 4),
                     "d2h_bytes_per_step": int(B * 4)},
-            "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+            "gpu_launches": (LAUNCHES_PER_STEP + (0 if prec == PREC_FP32 else 1)) * args.steps,
             "clocks": clk,
             "cpu_baseline": cpu,
         }

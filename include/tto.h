@@ -45,6 +45,8 @@ extern "C" {
 #define TTO_PREC_BF16X3 1  /* tensor cores, BF16 hi/lo split (3 products), FP32 accumulate */
 #define TTO_PREC_BF16 2    /* tensor cores, single BF16 product, FP32 accumulate */
 #define TTO_PREC_TF32X3 3  /* tensor cores, TF32 hi/lo split (3 products), FP32 accumulate */
+#define TTO_PREC_FP16X3 4  /* tensor cores, FP16 hi/lo split (3 products in 2 mma), FP32 accumulate;
+                              U and V are balanced per topology by a power-of-two scale */
 
 #define TTO_FIT_WORKLOAD 0 /* fitness = -(lambda_o + max loading) */
 #define TTO_FIT_F1 1       /* fitness = lambda_f1 = -(lambda_o + 200 lambda_c0 + 50 lambda_c) */

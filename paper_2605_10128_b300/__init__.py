@@ -11,7 +11,7 @@ import numpy as np
 
 from . import _lib
 from ._lib import (  # noqa: F401
-    TTOError, PREC_FP32, PREC_BF16X3, PREC_BF16, PREC_TF32X3, FIT_WORKLOAD, FIT_F1,
+    TTOError, PREC_FP32, PREC_BF16X3, PREC_BF16, PREC_TF32X3, PREC_FP16X3, FIT_WORKLOAD, FIT_F1,
 )
 
 DEFAULT_MUTATION = (0.2, 0.2, 0.5, 0.1, 2.0)  # p_add, p_remove, p_change, p_identity, N_mutmean

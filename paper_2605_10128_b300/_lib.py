@@ -20,7 +20,7 @@ TTO_E_CUDA = -3
 TTO_E_NOMEM = -4
 TTO_E_TOPOLOGY = -5
 TTO_E_TIMEOUT = -6
-PREC_FP32, PREC_BF16X3, PREC_BF16, PREC_TF32X3 = 0, 1, 2, 3
+PREC_FP32, PREC_BF16X3, PREC_BF16, PREC_TF32X3, PREC_FP16X3 = 0, 1, 2, 3, 4
 FIT_WORKLOAD, FIT_F1 = 0, 1
 
 _i32p = C.POINTER(C.c_int32)

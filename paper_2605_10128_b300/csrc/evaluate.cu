@@ -24,111 +24,27 @@
 #include <math.h>
 #include <stdio.h>
 
-#include <cuda_bf16.h>
-
 #include "sweep.cuh"
 #include "tto_internal.h"
 
 namespace tto {
 
 // ------------------------------------------------------- factor layouts
-// FP32 sweep: U [B][E_mon_pad][KP], V [B][O_pad][KP], g [B][O_pad][TT].
-// Tensor-core sweep, mma fragment order (lane = 4 g + q):
-//   bf16 (m16n8k16): A = [U_hi | U_lo] per 16-row tile, Ua [B][E_mon_pad/16][lane][4 x bf16x2];
-//     B per 8-outage tile, Vb [B][O_pad/8][lane][2] = (V_hi pair, V_lo pair).
-//   tf32 (m16n8k8): Ua [B][E_mon_pad/16][lane][8] = (U_hi a0..a3, U_lo a0..a3);
-//     Vb [B][O_pad/8][lane][4] = (V_hi b0 b1, V_lo b0 b1).
-//   g [B][n_tch][O_pad/8][q][TC][2]: per chunk of TC timesteps, the two outage
-//     columns 2q, 2q+1 a lane owns.
-__device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
-  const uint32_t a = __bfloat16_as_ushort(__float2bfloat16_rn(lo_elem));
-  const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn(hi_elem));
-  return a | (b << 16);
+// U [B][E_mon_pad][8], V [B][O_pad][8], g [B][O_pad][TT] in FP32; the
+// tensor-core sweep repacks them into mma fragment order (sweep_tc.cu).
+__device__ __forceinline__ void store_row_factors(const EvalArgs& a, int b, int l, const float* u) {
+  float4* Urow = reinterpret_cast<float4*>(a.U + ((size_t)b * a.E_mon_pad + l) * 8);
+  Urow[0] = make_float4(u[0], u[1], u[2], u[3]);
+  Urow[1] = make_float4(u[4], u[5], u[6], u[7]);
 }
 
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-
-__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-  hi = to_tf32(x);
-  lo = to_tf32(x - __uint_as_float(hi));
-}
-
-__device__ __forceinline__ void split_bf16(float x, float& hi, float& lo) {
-  hi = __bfloat162float(__float2bfloat16_rn(x));
-  lo = x - hi;
-}
-
-__device__ void store_row_factors(const EvalArgs& a, int b, int l, const float* u) {
-  if (a.precision == TTO_PREC_FP32) {
-    float* Urow = a.U + ((size_t)b * a.E_mon_pad + l) * a.KP;
-    for (int j = 0; j < a.KP; ++j) Urow[j] = u[j];
-    return;
-  }
-  const int mt = l >> 4, r = l & 15, g = r & 7, half = r >> 3;
-  if (a.precision == TTO_PREC_TF32X3) {
-    uint32_t hi[TTO_MAX_K], lo[TTO_MAX_K];
-    for (int j = 0; j < TTO_MAX_K; ++j) split_tf32(u[j], hi[j], lo[j]);
-    uint32_t* base = reinterpret_cast<uint32_t*>(a.U) + ((size_t)b * (a.E_mon_pad >> 4) + mt) * 256;
-    for (int q = 0; q < 4; ++q) {
-      uint32_t* w = base + (g * 4 + q) * 8;
-      w[half] = hi[q];
-      w[2 + half] = hi[q + 4];
-      w[4 + half] = lo[q];
-      w[6 + half] = lo[q + 4];
-    }
-    return;
-  }
-  float hi[TTO_MAX_K], lo[TTO_MAX_K];
-  for (int j = 0; j < TTO_MAX_K; ++j) split_bf16(u[j], hi[j], lo[j]);
-  uint32_t* base = reinterpret_cast<uint32_t*>(a.U) + ((size_t)b * (a.E_mon_pad >> 4) + mt) * 128;
-  for (int q = 0; q < 4; ++q) {
-    uint32_t* w = base + (g * 4 + q) * 4;
-    w[half] = pack_bf16(hi[2 * q], hi[2 * q + 1]);
-    w[2 + half] = pack_bf16(lo[2 * q], lo[2 * q + 1]);
-  }
-}
-
-__device__ void store_col_factors(const EvalArgs& a, int b, int c, const float* v, const float* gv) {
-  const int TT = a.TT;
-  if (a.precision == TTO_PREC_FP32) {
-    float* Vrow = a.V + ((size_t)b * a.O_pad + c) * a.KP;
-    for (int j = 0; j < a.KP; ++j) Vrow[j] = v[j];
-    float* grow = a.gg + ((size_t)b * a.O_pad + c) * TT;
-    for (int t = 0; t < TT; ++t) grow[t] = gv[t];
-    return;
-  }
-  const int ntl = c >> 3, cc = c & 7;
-  const size_t tile = (size_t)b * (a.O_pad >> 3) + ntl;
-  if (a.precision == TTO_PREC_TF32X3) {
-    uint32_t hi[TTO_MAX_K], lo[TTO_MAX_K];
-    for (int j = 0; j < TTO_MAX_K; ++j) split_tf32(v[j], hi[j], lo[j]);
-    uint32_t* vb = reinterpret_cast<uint32_t*>(a.V) + tile * 128;
-    for (int q = 0; q < 4; ++q) {
-      uint32_t* w = vb + (cc * 4 + q) * 4;
-      w[0] = hi[q];
-      w[1] = hi[q + 4];
-      w[2] = lo[q];
-      w[3] = lo[q + 4];
-    }
-  } else {
-    float hi[TTO_MAX_K], lo[TTO_MAX_K];
-    for (int j = 0; j < TTO_MAX_K; ++j) split_bf16(v[j], hi[j], lo[j]);
-    uint32_t* vb = reinterpret_cast<uint32_t*>(a.V) + tile * 64;
-    for (int q = 0; q < 4; ++q) {
-      vb[(cc * 4 + q) * 2 + 0] = pack_bf16(hi[2 * q], hi[2 * q + 1]);
-      vb[(cc * 4 + q) * 2 + 1] = pack_bf16(lo[2 * q], lo[2 * q + 1]);
-    }
-  }
-  const int TC = a.TC, n_nt = a.O_pad >> 3;
-  for (int t = 0; t < TT; ++t) {
-    const int ci = t / TC, tt = t - ci * TC;
-    const size_t slab = ((size_t)b * a.n_tch + ci) * n_nt + ntl;
-    a.gg[((slab * 4 + (cc >> 1)) * TC + tt) * 2 + (cc & 1)] = gv[t];
-  }
+__device__ __forceinline__ void store_col_factors(const EvalArgs& a, int b, int c, const float* v,
+                                                  const float* gv) {
+  float4* Vrow = reinterpret_cast<float4*>(a.V + ((size_t)b * a.O_pad + c) * 8);
+  Vrow[0] = make_float4(v[0], v[1], v[2], v[3]);
+  Vrow[1] = make_float4(v[4], v[5], v[6], v[7]);
+  float* grow = a.gg + ((size_t)b * a.O_pad + c) * a.TT;
+  for (int t = 0; t < a.TT; ++t) grow[t] = gv[t];
 }
 
 // ---------------------------------------------------------------- split update
@@ -148,6 +64,7 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
   __shared__ double s_psi[TTO_MAX_T][TTO_MAX_K];
   __shared__ double s_sb[TTO_MAX_K];
   __shared__ int s_cnt_c0, s_cnt_isl;
+  __shared__ float s_umax, s_vmax;
 
   if (tid == 0) {
     int k = 0, ne = 0, bad = 0, ns = 0, nm = 0;
@@ -195,6 +112,8 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
     s_island = bad;
     s_cnt_c0 = 0;
     s_cnt_isl = 0;
+    s_umax = 0.f;
+    s_vmax = 0.f;
     if (bad) atomicExch(a.status, TTO_E_TOPOLOGY);
   }
   __syncthreads();
@@ -276,6 +195,7 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
   const int TT = a.TT;
   const float qnan = __int_as_float(0x7fc00000);
   int c0cnt = 0;
+  float umax = 0.f, vmax = 0.f;
   // monitored rows: f', U
   for (int l = tid; l < a.E_mon_pad; l += blockDim.x) {
     const int lr = min(l, a.E_mon - 1);
@@ -298,6 +218,7 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
       if (jj < k)
         for (int j = 0; j < k; ++j) uu += W[j] * s_Ki[j][jj];
       u[jj] = (float)uu;
+      umax = fmaxf(umax, fabsf(u[jj]));
     }
     store_row_factors(a, b, l, u);
     const float lim = a.lim[lr];
@@ -337,7 +258,10 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
       for (int j = 0; j < k; ++j) uu += W[j] * s_Ki[j][jj];
       npcc -= uu * (W[jj] / be);
     }
-    for (int jj = 0; jj < TTO_MAX_K; ++jj) v[jj] = jj < k ? (float)(W[jj] / be) : 0.f;
+    for (int jj = 0; jj < TTO_MAX_K; ++jj) {
+      v[jj] = jj < k ? (float)(W[jj] / be) : 0.f;
+      vmax = fmaxf(vmax, fabsf(v[jj]));
+    }
     const bool isl = !(npcc > kIslandTol);
     if (isl && c < a.O) ++islcnt;
     for (int t = 0; t < TT; ++t) {
@@ -357,6 +281,9 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
   }
   if (c0cnt) atomicAdd(&s_cnt_c0, c0cnt);
   if (islcnt) atomicAdd(&s_cnt_isl, islcnt);
+  // magnitudes are >= 0, so the float bit patterns order like the values
+  if (umax > 0.f) atomicMax(reinterpret_cast<int*>(&s_umax), __float_as_int(umax));
+  if (vmax > 0.f) atomicMax(reinterpret_cast<int*>(&s_vmax), __float_as_int(vmax));
   __syncthreads();
   if (tid == 0) {
     TopoInfo inf;
@@ -365,7 +292,9 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
     inf.ns = s_ns;
     inf.nm = s_nm;
     inf.lambda_c0 = dead ? 0.f : (float)s_cnt_c0;
-    inf.pad0 = inf.pad1 = inf.pad2 = 0.f;
+    inf.umax = s_umax;
+    inf.vmax = s_vmax;
+    inf.pad = 0.f;
     a.info[b] = inf;
   }
 }
@@ -411,7 +340,7 @@ __global__ void fitness_kernel(EvalArgs a) {
 // ---------------------------------------------------------------- workspace
 void free_workspace(tto_grid* g) {
   Workspace& w = g->ws;
-  void* ptrs[] = {w.U, w.V, w.fp, w.gg, w.info, w.part, w.fit, w.cell, w.desc, w.island, w.topo};
+  void* ptrs[] = {w.U, w.V, w.Ua, w.Vb, w.gq, w.fp, w.gg, w.info, w.part, w.fit, w.cell, w.desc, w.island, w.topo};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   w = Workspace();
@@ -424,8 +353,11 @@ int ensure_workspace(tto_grid* g, int B, int T) {
   int nT = T > w.cap_T ? T : w.cap_T;
   free_workspace(g);
   const size_t Ep = g->E_mon_pad, Op = g->O_pad;
-  TTO_CUDA_TRY(cudaMalloc(&w.U, (size_t)nB * Ep * 16 * sizeof(float)));
-  TTO_CUDA_TRY(cudaMalloc(&w.V, (size_t)nB * Op * 16 * sizeof(float)));
+  TTO_CUDA_TRY(cudaMalloc(&w.U, (size_t)nB * Ep * 8 * sizeof(float)));
+  TTO_CUDA_TRY(cudaMalloc(&w.V, (size_t)nB * Op * 8 * sizeof(float)));
+  TTO_CUDA_TRY(cudaMalloc(&w.Ua, (size_t)nB * Ep * 16 * sizeof(uint32_t)));
+  TTO_CUDA_TRY(cudaMalloc(&w.Vb, (size_t)nB * Op * 16 * sizeof(uint32_t)));
+  TTO_CUDA_TRY(cudaMalloc(&w.gq, (size_t)nB * Op * nT * sizeof(float)));
   TTO_CUDA_TRY(cudaMalloc(&w.fp, (size_t)nB * nT * Ep * sizeof(float)));
   TTO_CUDA_TRY(cudaMalloc(&w.gg, (size_t)nB * Op * nT * sizeof(float)));
   TTO_CUDA_TRY(cudaMalloc(&w.info, (size_t)nB * sizeof(TopoInfo)));
@@ -456,7 +388,7 @@ int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, 
   if (B < 0) return set_error(TTO_E_ARG, "negative batch");
   if (B > 0 && (!topo || !fitness)) return set_error(TTO_E_ARG, "null topology or fitness buffer");
   if (o->d_split < 1 || o->d_moved < 1) return set_error(TTO_E_ARG, "archive extents must be >= 1");
-  if (o->precision < TTO_PREC_FP32 || o->precision > TTO_PREC_TF32X3) return set_error(TTO_E_ARG, "unknown precision");
+  if (o->precision < TTO_PREC_FP32 || o->precision > TTO_PREC_FP16X3) return set_error(TTO_E_ARG, "unknown precision");
   if (o->fitness_kind != TTO_FIT_WORKLOAD && o->fitness_kind != TTO_FIT_F1) return set_error(TTO_E_ARG, "unknown fitness kind");
   if (n_t < 0 || n_t > TTO_MAX_T || (tsel == nullptr && g->T > TTO_MAX_T))
     return set_error(TTO_E_ARG, "n_t must be in [1, %d]", TTO_MAX_T);
@@ -515,6 +447,9 @@ int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, 
   a.V = w.V;
   a.fp = w.fp;
   a.gg = w.gg;
+  a.Ua = w.Ua;
+  a.Vb = w.Vb;
+  a.gq = w.gq;
   a.info = w.info;
   a.part = w.part;
   a.fitness = fitness;

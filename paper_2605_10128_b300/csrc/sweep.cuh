@@ -44,6 +44,9 @@ struct EvalArgs {
   float* V;
   float* fp;
   float* gg;
+  uint32_t* Ua;
+  uint32_t* Vb;
+  float* gq;
   TopoInfo* info;
   float* part;
   // outputs

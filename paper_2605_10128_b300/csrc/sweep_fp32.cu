@@ -1,4 +1,4 @@
-// Fused N-1 sweep on the CUDA cores (FP32 throughout).
+// Fused N-1 sweep on the CUDA cores (FP32 throughout; TTO_PREC_FP32).
 //
 // CTA = one tile of 128 monitored rows x a group of G topologies; thread = row.
 // The CTA walks all outage columns in chunks of 32: the per-topology column
@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(kRowTile) sweep_fp32_kernel(EvalArgs a) {
 #pragma unroll
   for (int gi = 0; gi < G; ++gi) {
     const int bb = min(b0 + gi, a.B - 1);
-    const float* ur = a.U + ((size_t)bb * Ep + l) * KP;
+    const float* ur = a.U + ((size_t)bb * Ep + l) * 8;
 #pragma unroll
     for (int j = 0; j < KP; ++j) sU[gi][tid][j] = ur[j];
 #pragma unroll
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kRowTile) sweep_fp32_kernel(EvalArgs a) {
     for (int i = tid; i < G * kCC * KP; i += kRowTile) {
       const int gi = i / (kCC * KP), r = i % (kCC * KP);
       const int bb = min(b0 + gi, a.B - 1);
-      (&sV[gi][0][0])[r] = a.V[((size_t)bb * Op + c0) * KP + r];
+      (&sV[gi][0][0])[r] = a.V[((size_t)bb * Op + c0 + r / KP) * 8 + r % KP];
     }
     for (int i = tid; i < G * kCC * TT; i += kRowTile) {
       const int gi = i / (kCC * TT), r = i % (kCC * TT);

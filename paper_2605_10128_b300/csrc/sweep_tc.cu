@@ -4,46 +4,59 @@
 //     N'_lc = N_lc - U_l . V_c        (rank k <= 8)
 // and the post-contingency flow of every timestep is
 //     F_lc[t] = f'_l[t] - N'_lc g_c[t],     fmax_l[t] = max_c |F_lc[t]|.
-// Per 16 x 8 tile, mma.sync accumulates the split products of U and V onto an
+// Per 16 x 8 tile, mma.sync accumulates split products of U and V onto an
 // accumulator preloaded with -N (stored once per grid in C-fragment order), so
-// D = U V^T - N = -N'.  Modes: TF32X3 = three m16n8k8 tf32 products
-// U_hi V_hi + U_lo V_hi + U_hi V_lo (about 2^-22 relative error of the low-rank
-// term); BF16X3 = two m16n8k16 bf16 products [U_hi|U_lo][V_hi;V_hi] and
-// [U_hi|U_lo][V_lo;0] (about 2^-16); BF16 = U_hi V_hi only.  The accumulator
-// registers hold each lane's four (l, c) entries, and the epilogue runs on them
-// directly: F = fma(D, g_c[t], f'_l[t]) and a max of |F| per row and timestep,
-// two FP32 instructions per (l, c, t).  Islanding outages carry g = NaN, which
-// fmaxf ignores.
+// D = U V^T - N = -N'.  Modes (hi/lo = leading and residual part of a split):
+//   FP16X3: [U_hi|U_lo][V_hi;V_hi] + [U_hi|U_lo][V_lo;0], two m16n8k16 fp16
+//           products, about 2^-21 relative error of the low-rank term; U and V
+//           are first balanced by a power-of-two scale per topology (exact),
+//           which keeps both inside the fp16 range;
+//   TF32X3: U_hi V_hi + U_lo V_hi + U_hi V_lo, three m16n8k8 tf32 products,
+//           about 2^-21;
+//   BF16X3: as FP16X3 in bf16, about 2^-16;  BF16: U_hi V_hi only.
+// The accumulator registers hold each lane's four (l, c) entries and the
+// epilogue runs on them directly: F = fma(D, g_c[t], f'_l[t]) and a max of |F|
+// per row and timestep, two FP32 instructions per (l, c, t).  Islanding
+// outages carry g = NaN, which fmaxf ignores.
 //
-// CTA = 8 warps = 8 topologies on one band of 16*MW monitored rows; each warp
-// walks every outage column of its topology, so the running maxima stay in
-// registers and every warp reduces its own rows at the end (no atomics).
-// Operands stream through a two-slot shared-memory ring filled by TMA bulk
-// copies (cp.async.bulk, completion counted on an mbarrier): per stage of 8
-// outage tiles, the -N slab of the band (read once, used by all 8 warps) and
-// each warp's column factors V and g.  One lane of warp 0 issues the copies of
-// stage s+2 once every warp has released stage s (a second mbarrier).  Every
-// wait is bounded; a wait that gives up sets the status word to TTO_E_TIMEOUT,
-// drains the copies already issued, and ends the kernel.  The launch order is
-// tiled (16 row bands x 16 topology groups) so that the -N band and the
-// column factors of co-resident CTAs stay in L2.
+// CTA = 16 warps = 8 topologies x 2 row halves of one band of 32*MW monitored
+// rows.  Each warp walks every outage column of its topology for 16*MW rows,
+// so its running maxima stay in registers and it reduces its own rows at the
+// end (no atomics).  Operands stream through a three-slot shared-memory ring
+// filled by TMA bulk copies (cp.async.bulk, completion counted on an mbarrier):
+// per stage of 8 outage tiles, the -N slab of the band (shared by the 8
+// topologies) and each topology's column factors V and g (shared by its two
+// warps).  One lane of warp 0 refills a slot once every warp has released it
+// (a second mbarrier).  Every wait is bounded; a wait that gives up sets the
+// status word to TTO_E_TIMEOUT, lets the copies already issued land, and ends
+// the kernel.  The launch order is tiled (16 row bands x 16 topology groups)
+// so that the -N band and the column factors of co-resident CTAs stay in L2.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "sweep.cuh"
 
 namespace tto {
 
-constexpr int kTCWarps = 8;           // topologies per CTA
+constexpr int kTopo = 8;              // topologies per CTA
+constexpr int kWarps = 2 * kTopo;     // two row halves per topology
 constexpr int kSwB = 16, kSwG = 16;   // launch-order tile: row bands x topology groups
 constexpr int kMaxTChunk = 8;         // timesteps per sweep pass
 constexpr int kSN = 8;                // outage tiles (8 columns each) per pipeline stage
-constexpr int kSlots = 2;             // pipeline depth
+constexpr int kSlots = 3;             // pipeline depth
 constexpr long long kWaitCycles = 1ll << 31;  // give up after ~1 s at 2 GHz
 
-enum { kModeBF16x3 = 0, kModeBF16 = 1, kModeTF32x3 = 2 };
+enum { kModeBF16x3 = 0, kModeBF16 = 1, kModeTF32x3 = 2, kModeFP16x3 = 3 };
 
 __device__ __forceinline__ void mma_bf16(float4& d, const uint32_t* a, uint32_t b0, uint32_t b1) {
   asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d.x), "+f"(d.y), "+f"(d.z), "+f"(d.w)
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void mma_fp16(float4& d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
       "{%0,%1,%2,%3};"
       : "+f"(d.x), "+f"(d.y), "+f"(d.z), "+f"(d.w)
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
@@ -104,22 +117,22 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t b
 
 template <int MODE>
 struct TCMode {
-  static constexpr int AW = MODE == kModeTF32x3 ? 8 : 4;  // A-fragment words per lane
-  static constexpr int BW = MODE == kModeTF32x3 ? 4 : 2;  // B-fragment words per lane
+  static constexpr int AW = MODE == kModeTF32x3 ? 8 : 4;  // A-fragment words per lane and m-tile
+  static constexpr int BW = MODE == kModeTF32x3 ? 4 : 2;  // B-fragment words per lane and n-tile
 };
 
 // Shared-memory layout of one pipeline slot.
 template <int MW, int MODE, int TC>
 struct Slot {
-  static constexpr uint32_t kNf = MW * kSN * 32 * 16;                     // -N fragments of the band
-  static constexpr uint32_t kVb = kSN * 32 * TCMode<MODE>::BW * 4;        // per warp
-  static constexpr uint32_t kG = kSN * 4 * TC * 2 * 4;                    // per warp
-  static constexpr uint32_t kWarp = kVb + kG;
-  static constexpr uint32_t kBytes = kNf + kTCWarps * kWarp;
+  static constexpr uint32_t kNf = 2 * MW * kSN * 512;                 // -N tiles of the band
+  static constexpr uint32_t kVb = kSN * 32 * TCMode<MODE>::BW * 4;    // per topology
+  static constexpr uint32_t kG = kSN * 4 * TC * 2 * 4;                // per topology
+  static constexpr uint32_t kTopoBytes = kVb + kG;
+  static constexpr uint32_t kBytes = kNf + kTopo * kTopoBytes;
 };
 
 template <int TC, int MW, int MODE>
-__global__ void __launch_bounds__(kTCWarps * 32, 2)
+__global__ void __launch_bounds__(kWarps * 32, 1)
     sweep_tc_kernel(EvalArgs a, int tci, int n_bands, int n_groups) {
   using S = Slot<MW, MODE, TC>;
   constexpr int AW = TCMode<MODE>::AW, BW = TCMode<MODE>::BW;
@@ -127,25 +140,27 @@ __global__ void __launch_bounds__(kTCWarps * 32, 2)
   __shared__ __align__(8) uint64_t full[kSlots], empty[kSlots];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  const int tw = warp >> 1, half = warp & 1;
   const int tiles_b = (n_bands + kSwB - 1) / kSwB;
   const int tile = blockIdx.x / (kSwB * kSwG), within = blockIdx.x % (kSwB * kSwG);
   const int band = (tile % tiles_b) * kSwB + within % kSwB;
   const int grp = (tile / tiles_b) * kSwG + within / kSwB;
   if (band >= n_bands || grp >= n_groups) return;  // CTA-uniform
-  const int n_active = min(kTCWarps, a.B - grp * kTCWarps);
-  const int b = grp * kTCWarps + warp;
+  const int n_topo = min(kTopo, a.B - grp * kTopo);
+  const int b = grp * kTopo + tw;
   const int TT = a.TT;
   const int t0 = tci * TC;
   const int n_mt = a.E_mon_pad >> 4, n_nt = a.O_pad >> 3;
   const int n_stages = n_nt / kSN;
-  const int mt0 = band * MW;
+  const int mt_band = band * 2 * MW;        // first m-tile of the band
+  const int mt0 = mt_band + half * MW;      // first m-tile of this warp
   const size_t Ep = a.E_mon_pad;
   const bool producer = threadIdx.x == 0;
 
   if (producer) {
     for (int sl = 0; sl < kSlots; ++sl) {
       mbar_init(&full[sl], 1);
-      mbar_init(&empty[sl], n_active);
+      mbar_init(&empty[sl], 2 * n_topo);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -155,27 +170,26 @@ __global__ void __launch_bounds__(kTCWarps * 32, 2)
   auto issue = [&](int s) {
     const int sl = s % kSlots;
     unsigned char* base = smem + (size_t)sl * S::kBytes;
-    mbar_expect_tx(&full[sl], S::kNf + n_active * S::kWarp);
+    mbar_expect_tx(&full[sl], S::kNf + n_topo * S::kTopoBytes);
     const int nt0 = s * kSN;
-    for (int i = 0; i < MW; ++i)
-      bulk_copy(base + i * (kSN * 512), a.Nf + ((size_t)(mt0 + i) * n_nt + nt0) * 32, kSN * 512, &full[sl]);
-    for (int w = 0; w < n_active; ++w) {
-      const int bw = grp * kTCWarps + w;
-      unsigned char* wb = base + S::kNf + w * S::kWarp;
-      bulk_copy(wb, reinterpret_cast<const uint32_t*>(a.V) + ((size_t)bw * n_nt + nt0) * 32 * BW, S::kVb,
+    for (int i = 0; i < 2 * MW; ++i)
+      bulk_copy(base + i * (kSN * 512), a.Nf + ((size_t)(mt_band + i) * n_nt + nt0) * 32, kSN * 512,
                 &full[sl]);
-      bulk_copy(wb + S::kVb, a.gg + (((size_t)bw * a.n_tch + tci) * n_nt + nt0) * 4 * TC * 2, S::kG,
-                &full[sl]);
+    for (int w = 0; w < n_topo; ++w) {
+      const size_t bw = (size_t)grp * kTopo + w;
+      unsigned char* wb = base + S::kNf + w * S::kTopoBytes;
+      bulk_copy(wb, a.Vb + (bw * n_nt + nt0) * 32 * BW, S::kVb, &full[sl]);
+      bulk_copy(wb + S::kVb, a.gq + ((bw * a.n_tch + tci) * n_nt + nt0) * 4 * TC * 2, S::kG, &full[sl]);
     }
   };
   if (producer)
     for (int s = 0; s < kSlots && s < n_stages; ++s) issue(s);
 
-  if (warp >= n_active) return;  // past the batch end; not counted by the empty barriers
+  if (tw >= n_topo) return;  // past the batch end; not counted by the empty barriers
 
   uint32_t A[MW][AW];
   float f[MW][2][TC], m[MW][2][TC];
-  const uint4* Ua = reinterpret_cast<const uint4*>(a.U);
+  const uint4* Ua = reinterpret_cast<const uint4*>(a.Ua);
 #pragma unroll
   for (int i = 0; i < MW; ++i) {
 #pragma unroll
@@ -210,9 +224,9 @@ __global__ void __launch_bounds__(kTCWarps * 32, 2)
     }
     pending = s + 1;
     const unsigned char* base = smem + (size_t)sl * S::kBytes;
-    const float4* nfs = reinterpret_cast<const float4*>(base) + lane;
-    const uint32_t* vbs = reinterpret_cast<const uint32_t*>(base + S::kNf + warp * S::kWarp) + lane * BW;
-    const float* gs = reinterpret_cast<const float*>(base + S::kNf + warp * S::kWarp + S::kVb) + q * TC * 2;
+    const float4* nfs = reinterpret_cast<const float4*>(base) + half * MW * kSN * 32 + lane;
+    const uint32_t* vbs = reinterpret_cast<const uint32_t*>(base + S::kNf + tw * S::kTopoBytes) + lane * BW;
+    const float* gs = reinterpret_cast<const float*>(base + S::kNf + tw * S::kTopoBytes + S::kVb) + q * TC * 2;
 #pragma unroll
     for (int j = 0; j < kSN; ++j) {
       uint32_t vb[BW];
@@ -249,9 +263,12 @@ __global__ void __launch_bounds__(kTCWarps * 32, 2)
           mma_tf32(d, &A[i][0], vb[0], vb[1]);  // U_hi V_hi
           mma_tf32(d, &A[i][4], vb[0], vb[1]);  // U_lo V_hi
           mma_tf32(d, &A[i][0], vb[2], vb[3]);  // U_hi V_lo
+        } else if (MODE == kModeFP16x3) {
+          mma_fp16(d, &A[i][0], vb[0], vb[0]);  // [U_hi | U_lo] [V_hi ; V_hi]
+          mma_fp16(d, &A[i][0], vb[1], 0u);     // [U_hi | U_lo] [V_lo ; 0]
         } else if (MODE == kModeBF16x3) {
-          mma_bf16(d, &A[i][0], vb[0], vb[0]);  // [U_hi | U_lo] [V_hi ; V_hi]
-          mma_bf16(d, &A[i][0], vb[1], 0u);     // [U_hi | U_lo] [V_lo ; 0]
+          mma_bf16(d, &A[i][0], vb[0], vb[0]);
+          mma_bf16(d, &A[i][0], vb[1], 0u);
         } else {
           mma_bf16(d, &A[i][0], vb[0], 0u);     // U_hi V_hi
         }
@@ -273,7 +290,7 @@ __global__ void __launch_bounds__(kTCWarps * 32, 2)
         ++issued;
       }
     }
-    if (!__shfl_sync(0xffffffffu, refill, 0)) {  // reconverges warp 0 after the producer step
+    if (!__shfl_sync(0xffffffffu, refill, 0)) {  // also reconverges warp 0 after the producer step
       ok = false;
       break;
     }
@@ -326,11 +343,134 @@ __global__ void __launch_bounds__(kTCWarps * 32, 2)
     ml = fmaxf(ml, __shfl_xor_sync(0xffffffffu, ml, o));
   }
   if (lane == 0) {
-    float* pp = a.part + ((size_t)b * a.n_parts + (size_t)band * a.n_tch + tci) * 4;
+    float* pp = a.part + ((size_t)b * a.n_parts + (size_t)(band * 2 + half) * a.n_tch + tci) * 4;
     pp[0] = over;
     pp[1] = cnt;
     pp[2] = ml;
     pp[3] = 0.f;
+  }
+}
+
+// ------------------------------------------------------------ fragment packing
+// Rows l of U (FP32 [B][E_mon_pad][8]) go to A fragments of 16-row tiles, lane
+// = 4 g + q with g = l % 8:
+//   16-bit modes (m16n8k16, K = [hi 0..7 | lo 0..7]): word (l % 16) / 8 holds
+//     (hi[2q], hi[2q+1]), word 2 + (l % 16) / 8 holds (lo[2q], lo[2q+1]);
+//   tf32 (m16n8k8): words (l%16)/8 and 2+(l%16)/8 hold hi[q], hi[q+4], words
+//     4+... and 6+... the same for lo.
+// Columns c of V go to B fragments of 8-outage tiles, lane = 4 (c % 8) + q:
+//   16-bit modes: (hi[2q], hi[2q+1]), (lo[2q], lo[2q+1]); tf32: hi[q], hi[q+4], lo[q], lo[q+4].
+// g [B][O_pad][TT] goes to [B][n_tch][O_pad/8][q][TC][2].
+__device__ __forceinline__ uint32_t pack_half2(float lo_elem, float hi_elem, bool fp16) {
+  uint32_t a, b;
+  if (fp16) {
+    a = __half_as_ushort(__float2half_rn(lo_elem));
+    b = __half_as_ushort(__float2half_rn(hi_elem));
+  } else {
+    a = __bfloat16_as_ushort(__float2bfloat16_rn(lo_elem));
+    b = __bfloat16_as_ushort(__float2bfloat16_rn(hi_elem));
+  }
+  return a | (b << 16);
+}
+
+__device__ __forceinline__ void split16(float x, bool fp16, float& hi, float& lo) {
+  hi = fp16 ? __half2float(__float2half_rn(x)) : __bfloat162float(__float2bfloat16_rn(x));
+  lo = x - hi;
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// Power-of-two exponent that balances max|U| 2^e and max|V| 2^-e.
+__device__ __forceinline__ int balance_exponent(float umax, float vmax) {
+  if (!(umax > 0.f) || !(vmax > 0.f)) return 0;
+  int eu, ev;
+  frexpf(umax, &eu);
+  frexpf(vmax, &ev);
+  return (ev - eu) / 2;
+}
+
+__global__ void pack_factors_kernel(EvalArgs a, int mode) {
+  const int rows = a.E_mon_pad, cols = a.O_pad;
+  const size_t per = (size_t)rows + cols;
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= per * a.B) return;
+  const int b = (int)(i / per);
+  const int x = (int)(i % per);
+  const TopoInfo inf = a.info[b];
+  const bool fp16 = mode == kModeFP16x3;
+  const int e = fp16 ? balance_exponent(inf.umax, inf.vmax) : 0;
+  if (fp16 && (ldexpf(inf.umax, e) > 16384.f || ldexpf(inf.vmax, -e) > 16384.f))
+    atomicExch(a.status, TTO_E_ARG);  // low-rank factors beyond the fp16 range
+  if (x < rows) {
+    const int l = x;
+    const float4* ur = reinterpret_cast<const float4*>(a.U + ((size_t)b * rows + l) * 8);
+    const float4 u0 = ur[0], u1 = ur[1];
+    float u[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+    const int mt = l >> 4, r = l & 15, gg = r & 7, hf = r >> 3;
+    if (mode == kModeTF32x3) {
+      uint32_t hi[8], lo[8];
+      for (int j = 0; j < 8; ++j) {
+        hi[j] = to_tf32(u[j]);
+        lo[j] = to_tf32(u[j] - __uint_as_float(hi[j]));
+      }
+      uint32_t* base = a.Ua + ((size_t)b * (rows >> 4) + mt) * 256;
+      for (int q = 0; q < 4; ++q) {
+        uint32_t* w = base + (gg * 4 + q) * 8;
+        w[hf] = hi[q];
+        w[2 + hf] = hi[q + 4];
+        w[4 + hf] = lo[q];
+        w[6 + hf] = lo[q + 4];
+      }
+    } else {
+      float hi[8], lo[8];
+      for (int j = 0; j < 8; ++j) split16(ldexpf(u[j], e), fp16, hi[j], lo[j]);
+      uint32_t* base = a.Ua + ((size_t)b * (rows >> 4) + mt) * 128;
+      for (int q = 0; q < 4; ++q) {
+        uint32_t* w = base + (gg * 4 + q) * 4;
+        w[hf] = pack_half2(hi[2 * q], hi[2 * q + 1], fp16);
+        w[2 + hf] = pack_half2(lo[2 * q], lo[2 * q + 1], fp16);
+      }
+    }
+    return;
+  }
+  const int c = x - rows;
+  const float4* vr = reinterpret_cast<const float4*>(a.V + ((size_t)b * cols + c) * 8);
+  const float4 v0 = vr[0], v1 = vr[1];
+  float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+  const int ntl = c >> 3, cc = c & 7, n_nt = cols >> 3;
+  const size_t tl = (size_t)b * n_nt + ntl;
+  if (mode == kModeTF32x3) {
+    uint32_t hi[8], lo[8];
+    for (int j = 0; j < 8; ++j) {
+      hi[j] = to_tf32(v[j]);
+      lo[j] = to_tf32(v[j] - __uint_as_float(hi[j]));
+    }
+    uint32_t* vb = a.Vb + tl * 128;
+    for (int q = 0; q < 4; ++q) {
+      uint32_t* w = vb + (cc * 4 + q) * 4;
+      w[0] = hi[q];
+      w[1] = hi[q + 4];
+      w[2] = lo[q];
+      w[3] = lo[q + 4];
+    }
+  } else {
+    float hi[8], lo[8];
+    for (int j = 0; j < 8; ++j) split16(ldexpf(v[j], -e), fp16, hi[j], lo[j]);
+    uint32_t* vb = a.Vb + tl * 64;
+    for (int q = 0; q < 4; ++q) {
+      vb[(cc * 4 + q) * 2 + 0] = pack_half2(hi[2 * q], hi[2 * q + 1], fp16);
+      vb[(cc * 4 + q) * 2 + 1] = pack_half2(lo[2 * q], lo[2 * q + 1], fp16);
+    }
+  }
+  const float* gr = a.gg + ((size_t)b * cols + c) * a.TT;
+  for (int t = 0; t < a.TT; ++t) {
+    const int ci = t / a.TC, tt = t - ci * a.TC;
+    const size_t slab = ((size_t)b * a.n_tch + ci) * n_nt + ntl;
+    a.gq[((slab * 4 + (cc >> 1)) * a.TC + tt) * 2 + (cc & 1)] = gr[t];
   }
 }
 
@@ -373,12 +513,12 @@ static int launch_tc(EvalArgs& a, int tci, cudaStream_t s) {
   const size_t smem = (size_t)kSlots * S::kBytes;
   TTO_CUDA_TRY(cudaFuncSetAttribute(sweep_tc_kernel<TC, MW, MODE>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int n_bands = a.E_mon_pad / (16 * MW);
-  const int n_groups = (a.B + kTCWarps - 1) / kTCWarps;
+  const int n_bands = a.E_mon_pad / (32 * MW);
+  const int n_groups = (a.B + kTopo - 1) / kTopo;
   const int tiles_b = (n_bands + kSwB - 1) / kSwB, tiles_g = (n_groups + kSwG - 1) / kSwG;
   const size_t blocks = (size_t)tiles_b * tiles_g * kSwB * kSwG;
   if (blocks > 0x7fffffffu) return set_error(TTO_E_ARG, "batch too large for one sweep launch");
-  sweep_tc_kernel<TC, MW, MODE><<<(unsigned)blocks, kTCWarps * 32, smem, s>>>(a, tci, n_bands, n_groups);
+  sweep_tc_kernel<TC, MW, MODE><<<(unsigned)blocks, kWarps * 32, smem, s>>>(a, tci, n_bands, n_groups);
   TTO_CUDA_TRY(cudaGetLastError());
   return TTO_OK;
 }
@@ -394,18 +534,32 @@ static int launch_tc_chunk(EvalArgs& a, int tci, cudaStream_t s) {
   return set_error(TTO_E_ARG, "unsupported timestep chunk %d", a.TC);
 }
 
+static int tc_mode(int precision) {
+  switch (precision) {
+    case TTO_PREC_TF32X3: return kModeTF32x3;
+    case TTO_PREC_FP16X3: return kModeFP16x3;
+    case TTO_PREC_BF16: return kModeBF16;
+    default: return kModeBF16x3;
+  }
+}
+
 int launch_sweep_tc(EvalArgs& a, cudaStream_t s) {
   if ((a.O_pad >> 3) % kSN != 0) return set_error(TTO_E_ARG, "outage padding is not a multiple of the stage width");
+  if ((a.E_mon_pad >> 4) % 4 != 0) return set_error(TTO_E_ARG, "monitored padding is not a multiple of the band");
+  const int mode = tc_mode(a.precision);
+  const size_t threads = ((size_t)a.E_mon_pad + a.O_pad) * a.B;
+  pack_factors_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a, mode);
+  TTO_CUDA_TRY(cudaGetLastError());
   const int mw = a.TC <= 4 ? 2 : 1;
   a.n_parts = (a.E_mon_pad / (16 * mw)) * a.n_tch;
   for (int ci = 0; ci < a.n_tch; ++ci) {
     int rc;
-    if (a.precision == TTO_PREC_TF32X3)
-      rc = launch_tc_chunk<kModeTF32x3>(a, ci, s);
-    else if (a.precision == TTO_PREC_BF16)
-      rc = launch_tc_chunk<kModeBF16>(a, ci, s);
-    else
-      rc = launch_tc_chunk<kModeBF16x3>(a, ci, s);
+    switch (mode) {
+      case kModeTF32x3: rc = launch_tc_chunk<kModeTF32x3>(a, ci, s); break;
+      case kModeFP16x3: rc = launch_tc_chunk<kModeFP16x3>(a, ci, s); break;
+      case kModeBF16: rc = launch_tc_chunk<kModeBF16>(a, ci, s); break;
+      default: rc = launch_tc_chunk<kModeBF16x3>(a, ci, s); break;
+    }
     if (rc) return rc;
   }
   return TTO_OK;

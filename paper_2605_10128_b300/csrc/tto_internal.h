@@ -33,15 +33,19 @@ struct TopoInfo {
   int ns;            // split stations
   int nm;            // moved assets
   float lambda_c0;   // N-0 critical branches (summed over timesteps)
-  float pad0, pad1, pad2;
+  float umax, vmax;  // largest |U| (monitored rows) and |V| (outage columns)
+  float pad;
 };
 
 // Evaluation workspace, grown on demand (or once by tto_grid_reserve).
 struct Workspace {
   int cap_B = 0;
   int cap_T = 0;
-  float* U = nullptr;        // [B][E_mon_pad][8] FP32 row factors, or bf16 A fragments
-  float* V = nullptr;        // [B][O_pad][8] FP32 column factors, or bf16 B fragments
+  float* U = nullptr;        // [B][E_mon_pad][8] FP32 row factors U = W K^-1
+  float* V = nullptr;        // [B][O_pad][8]     FP32 column factors V_c = W_c / b_c
+  uint32_t* Ua = nullptr;    // [B][E_mon_pad/16][lane][<=8] A fragments (tensor-core sweep)
+  uint32_t* Vb = nullptr;    // [B][O_pad/8][lane][<=4]      B fragments (tensor-core sweep)
+  float* gq = nullptr;       // [B][n_tch][O_pad/8][q][TC][2] g in lane order (tensor-core sweep)
   float* fp = nullptr;       // [B][TT][E_mon_pad]  post-split N-0 flows
   float* gg = nullptr;       // [B][O_pad][TT]      f'_c / N'_cc (NaN: outage islands)
   TopoInfo* info = nullptr;  // [B]

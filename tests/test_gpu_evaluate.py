@@ -55,7 +55,8 @@ def test_three_bus_golden_through_library():
     assert list(out["cell"]) == [0, 9, 9]
 
 
-PRECISIONS = [("fp32", 0, parity.TOL_FP32), ("tf32x3", 3, parity.TOL_FP32), ("bf16x3", 1, parity.TOL_BF16)]
+PRECISIONS = [("fp32", 0, parity.TOL_FP32), ("tf32x3", 3, parity.TOL_FP32), ("fp16x3", 4, parity.TOL_FP32),
+              ("bf16x3", 1, parity.TOL_BF16)]
 
 
 def check_all_precisions(label, sg, g, topo, idx, refs, plain_bf16=True, **kw):
@@ -182,7 +183,7 @@ def test_invalid_genomes_reported():
     g.sync_status()  # cleared
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
 def test_deterministic_and_order_independent(prec):
     sg = with_limits(config_grid("tto30", seed=4), 5)
     topo = random_topologies(sg, 200, seed=8)

@@ -133,20 +133,22 @@ def test_mapelites_trajectory_tto30():
         fgot = fit_t.cpu().numpy().astype(np.float64)
         fin = np.isfinite(fref)
         assert np.array_equal(fin, np.isfinite(fgot))
-        assert np.all(np.abs(fgot[fin] - fref[fin]) <= tol)
+        err = float(np.max(np.abs(fgot[fin] - fref[fin]), initial=0.0))
+        assert err <= tol
+        # every FP32 fitness is within err of its FP64 value, so an FP64 gap
+        # wider than 2 err between different genomes fixes the GPU's decision
+        # too; a narrower gap is a near-tie that ends the comparison
+        gap = 2.0 * err + 1e-12
         cells = np.array([r["cell"] for r in res])
-        # near-tie check: a decision between different genomes whose fitness
-        # lies within the tolerance ends the comparison (identical genomes
-        # tie harmlessly)
         tie = False
         for cc in np.unique(cells[fin]):
             ids = np.flatnonzero(fin & (cells == cc))
             top = ids[np.argmax(fref[ids])]
             for j in ids:
-                if j != top and fref[top] - fref[j] <= 2 * tol and not np.array_equal(ref_topo[j], ref_topo[top]):
+                if j != top and fref[top] - fref[j] <= gap and not np.array_equal(ref_topo[j], ref_topo[top]):
                     tie = True
             inc = arch.elites.get(int(cc))
-            if inc is not None and abs(fref[top] - inc[0]) <= 2 * tol and not np.array_equal(inc[1], ref_topo[top]):
+            if inc is not None and abs(fref[top] - inc[0]) <= gap and not np.array_equal(inc[1], ref_topo[top]):
                 tie = True
         arch.insert(cells, fref, ref_topo)
         if tie:
