@@ -195,7 +195,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="tto10k")
     ap.add_argument("--batch", type=int, default=0)
-    ap.add_argument("--precision", default="fp16x3", choices=["fp32", "fp16x3", "tf32x3", "bf16x3", "bf16"])
+    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "fp16x3", "tf32x3", "bf16x3", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-outages", type=int, default=120)
     args = ap.parse_args()

@@ -26,8 +26,8 @@
 // filled by TMA bulk copies (cp.async.bulk, completion counted on an mbarrier):
 // per stage of 8 outage tiles, the -N slab of the band (shared by the 8
 // topologies) and each topology's column factors V and g (shared by its two
-// warps).  One lane of warp 0 refills a slot once every warp has released it
-// (a second mbarrier).  Every wait is bounded; a wait that gives up sets the
+// warps).  The last warp to release a slot (a shared counter) refills it, its
+// lanes issuing the stage's copies in parallel.  Every wait is bounded; a wait that gives up sets the
 // status word to TTO_E_TIMEOUT, lets the copies already issued land, and ends
 // the kernel.  The launch order is tiled (16 row bands x 16 topology groups)
 // so that the -N band and the column factors of co-resident CTAs stay in L2.
@@ -43,7 +43,6 @@ constexpr int kWarps = 2 * kTopo;     // two row halves per topology
 constexpr int kSwB = 16, kSwG = 16;   // launch-order tile: row bands x topology groups
 constexpr int kMaxTChunk = 8;         // timesteps per sweep pass
 constexpr int kSN = 8;                // outage tiles (8 columns each) per pipeline stage
-constexpr int kSlots = 3;             // pipeline depth
 constexpr long long kWaitCycles = 1ll << 31;  // give up after ~1 s at 2 GHz
 
 enum { kModeBF16x3 = 0, kModeBF16 = 1, kModeTF32x3 = 2, kModeFP16x3 = 3 };
@@ -89,20 +88,22 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
       : "=r"(ok)
       : "r"(smem_addr(bar)), "r"(parity)
       : "memory");
   return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity to complete.
+// Bounded wait for the phase with the given parity to complete: a test, then
+// short sleeps between tests so that waiting warps leave the issue slots to
+// the warps that compute.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   if (mbar_test(bar, parity)) return true;
   const long long t0 = clock64();
   for (;;) {
-    for (int i = 0; i < 64; ++i)
-      if (mbar_test(bar, parity)) return true;
+    __nanosleep(64);  // yield issue slots to the warps that have data
+    if (mbar_test(bar, parity)) return true;
     if (clock64() - t0 > kWaitCycles) return false;
   }
 }
@@ -119,6 +120,7 @@ template <int MODE>
 struct TCMode {
   static constexpr int AW = MODE == kModeTF32x3 ? 8 : 4;  // A-fragment words per lane and m-tile
   static constexpr int BW = MODE == kModeTF32x3 ? 4 : 2;  // B-fragment words per lane and n-tile
+  static constexpr int kSlots = MODE == kModeTF32x3 ? 3 : 4;  // pipeline depth (shared memory bound)
 };
 
 // Shared-memory layout of one pipeline slot.
@@ -135,9 +137,11 @@ template <int TC, int MW, int MODE>
 __global__ void __launch_bounds__(kWarps * 32, 1)
     sweep_tc_kernel(EvalArgs a, int tci, int n_bands, int n_groups) {
   using S = Slot<MW, MODE, TC>;
-  constexpr int AW = TCMode<MODE>::AW, BW = TCMode<MODE>::BW;
+  constexpr int AW = TCMode<MODE>::AW, BW = TCMode<MODE>::BW, kSlots = TCMode<MODE>::kSlots;
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full[kSlots], empty[kSlots];
+  __shared__ __align__(8) uint64_t full[kSlots];
+  __shared__ int released[kSlots];  // warps done with the slot's current stage
+  __shared__ int s_issued;          // stages issued so far
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
   const int tw = warp >> 1, half = warp & 1;
@@ -160,30 +164,38 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
   if (producer) {
     for (int sl = 0; sl < kSlots; ++sl) {
       mbar_init(&full[sl], 1);
-      mbar_init(&empty[sl], 2 * n_topo);
+      released[sl] = 0;
     }
+    s_issued = kSlots < n_stages ? kSlots : n_stages;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
 
-  // stage s -> slot s % kSlots
+  // stage s -> slot s % kSlots; run by all lanes of warp 0, one copy per lane
   auto issue = [&](int s) {
     const int sl = s % kSlots;
     unsigned char* base = smem + (size_t)sl * S::kBytes;
-    mbar_expect_tx(&full[sl], S::kNf + n_topo * S::kTopoBytes);
+    if (lane == 0) mbar_expect_tx(&full[sl], S::kNf + n_topo * S::kTopoBytes);
+    __syncwarp();
     const int nt0 = s * kSN;
-    for (int i = 0; i < 2 * MW; ++i)
-      bulk_copy(base + i * (kSN * 512), a.Nf + ((size_t)(mt_band + i) * n_nt + nt0) * 32, kSN * 512,
-                &full[sl]);
-    for (int w = 0; w < n_topo; ++w) {
-      const size_t bw = (size_t)grp * kTopo + w;
-      unsigned char* wb = base + S::kNf + w * S::kTopoBytes;
-      bulk_copy(wb, a.Vb + (bw * n_nt + nt0) * 32 * BW, S::kVb, &full[sl]);
-      bulk_copy(wb + S::kVb, a.gq + ((bw * a.n_tch + tci) * n_nt + nt0) * 4 * TC * 2, S::kG, &full[sl]);
+    const int n_copies = 2 * MW + 2 * n_topo;
+    for (int c = lane; c < n_copies; c += 32) {
+      if (c < 2 * MW) {
+        bulk_copy(base + c * (kSN * 512), a.Nf + ((size_t)(mt_band + c) * n_nt + nt0) * 32, kSN * 512, &full[sl]);
+      } else {
+        const int w = (c - 2 * MW) >> 1;
+        const size_t bw = (size_t)grp * kTopo + w;
+        unsigned char* wb = base + S::kNf + w * S::kTopoBytes;
+        if (((c - 2 * MW) & 1) == 0)
+          bulk_copy(wb, a.Vb + (bw * n_nt + nt0) * 32 * BW, S::kVb, &full[sl]);
+        else
+          bulk_copy(wb + S::kVb, a.gq + ((bw * a.n_tch + tci) * n_nt + nt0) * 4 * TC * 2, S::kG, &full[sl]);
+      }
     }
   };
-  if (producer)
+  if (warp == 0)
     for (int s = 0; s < kSlots && s < n_stages; ++s) issue(s);
+  __syncthreads();  // stages 0.. are in flight and the release counters are set
 
   if (tw >= n_topo) return;  // past the batch end; not counted by the empty barriers
 
@@ -212,7 +224,6 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
   }
 
   bool ok = true;
-  int issued = kSlots < n_stages ? kSlots : n_stages;
   int pending = 0;  // first stage whose copies may still be in flight
   for (int s = 0; s < n_stages; ++s) {
     const int sl = s % kSlots;
@@ -280,27 +291,29 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         }
       }
     }
+    // release the slot; the last warp to release it issues the refill
     __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[sl]);
-    int refill = 1;
-    if (producer && s + kSlots < n_stages) {
-      refill = mbar_wait(&empty[sl], par) ? 1 : 0;
-      if (refill) {
-        issue(s + kSlots);
-        ++issued;
+    int last = 0;
+    if (lane == 0) {
+      __threadfence_block();  // this warp's reads of the slot precede the release
+      last = atomicAdd(&released[sl], 1) == 2 * n_topo - 1;
+      if (last) {
+        atomicExch(&released[sl], 0);
+        __threadfence_block();  // the reset precedes the refill that other warps wait for
       }
     }
-    if (!__shfl_sync(0xffffffffu, refill, 0)) {  // also reconverges warp 0 after the producer step
-      ok = false;
-      break;
+    if (__shfl_sync(0xffffffffu, last, 0) && s + kSlots < n_stages) {
+      issue(s + kSlots);
+      if (lane == 0) atomicMax(&s_issued, s + kSlots + 1);
     }
   }
 
   if (!ok) {
     atomicExch(a.status, TTO_E_TIMEOUT);
-    if (producer) {
+    if (lane == 0) {
       // let the copies already in flight land before the CTA releases its
-      // shared memory
+      // shared memory (bounded like every other wait)
+      const int issued = atomicAdd(&s_issued, 0);
       for (int s = pending; s < issued; ++s) mbar_wait(&full[s % kSlots], (uint32_t)(s / kSlots) & 1u);
     }
     return;
@@ -510,7 +523,7 @@ size_t max_parts(const tto_grid* g) {
 template <int TC, int MW, int MODE>
 static int launch_tc(EvalArgs& a, int tci, cudaStream_t s) {
   using S = Slot<MW, MODE, TC>;
-  const size_t smem = (size_t)kSlots * S::kBytes;
+  const size_t smem = (size_t)TCMode<MODE>::kSlots * S::kBytes;
   TTO_CUDA_TRY(cudaFuncSetAttribute(sweep_tc_kernel<TC, MW, MODE>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int n_bands = a.E_mon_pad / (32 * MW);

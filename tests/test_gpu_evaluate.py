@@ -55,7 +55,9 @@ def test_three_bus_golden_through_library():
     assert list(out["cell"]) == [0, 9, 9]
 
 
-PRECISIONS = [("fp32", 0, parity.TOL_FP32), ("tf32x3", 3, parity.TOL_FP32), ("fp16x3", 4, parity.TOL_FP32),
+# FP32 flows with an FP32 or TF32-split low-rank term meet the FP32 bar; the
+# 16-bit splits meet the BF16 bar (their measured error is printed).
+PRECISIONS = [("fp32", 0, parity.TOL_FP32), ("tf32x3", 3, parity.TOL_FP32), ("fp16x3", 4, parity.TOL_BF16),
               ("bf16x3", 1, parity.TOL_BF16)]
 
 

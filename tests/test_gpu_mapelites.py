@@ -145,7 +145,11 @@ def test_mapelites_trajectory_tto30():
             ids = np.flatnonzero(fin & (cells == cc))
             top = ids[np.argmax(fref[ids])]
             for j in ids:
-                if j != top and fref[top] - fref[j] <= gap and not np.array_equal(ref_topo[j], ref_topo[top]):
+                if j == top or np.array_equal(ref_topo[j], ref_topo[top]):
+                    continue
+                if fref[j] == fref[top] and fgot[j] == fgot[top]:
+                    continue  # exact tie on both sides: both keep the lower index
+                if fref[top] - fref[j] <= gap:
                     tie = True
             inc = arch.elites.get(int(cc))
             if inc is not None and abs(fref[top] - inc[0]) <= gap and not np.array_equal(inc[1], ref_topo[top]):
