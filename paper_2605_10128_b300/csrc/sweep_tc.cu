@@ -19,12 +19,12 @@
 // per row and timestep, two FP32 instructions per (l, c, t).  Islanding
 // outages carry g = NaN, which fmaxf ignores.
 //
-// CTA = 16 warps = 8 topologies x 2 row halves of one band of 32*MW monitored
-// rows.  Each warp walks every outage column of its topology for 16*MW rows,
+// CTA = 8 warps = 4 topologies x 2 row halves of one band of 32*MW monitored
+// rows, two CTAs per SM.  Each warp walks every outage column of its topology for 16*MW rows,
 // so its running maxima stay in registers and it reduces its own rows at the
 // end (no atomics).  Operands stream through a three-slot shared-memory ring
 // filled by TMA bulk copies (cp.async.bulk, completion counted on an mbarrier):
-// per stage of 8 outage tiles, the -N slab of the band (shared by the 8
+// per stage of 8 outage tiles, the -N slab of the band (shared by the 4
 // topologies) and each topology's column factors V and g (shared by its two
 // warps).  The last warp to release a slot (a shared counter) refills it, its
 // lanes issuing the stage's copies in parallel.  Every wait is bounded; a wait that gives up sets the
@@ -36,10 +36,19 @@
 
 #include "sweep.cuh"
 
+#ifndef TTO_SWEEP_TOPO
+#define TTO_SWEEP_TOPO 4
+#define TTO_SWEEP_HALVES 2
+#define TTO_SWEEP_SLOTS 3
+#endif
+
 namespace tto {
 
-constexpr int kTopo = 8;              // topologies per CTA
-constexpr int kWarps = 2 * kTopo;     // two row halves per topology
+// CTA shape: kTopo topologies x kHalves row groups of 16*MW rows, one warp each
+constexpr int kTopo = TTO_SWEEP_TOPO;
+constexpr int kHalves = TTO_SWEEP_HALVES;
+constexpr int kWarps = kTopo * kHalves;
+constexpr int kCtasPerSM = 2;
 constexpr int kSwB = 16, kSwG = 16;   // launch-order tile: row bands x topology groups
 constexpr int kMaxTChunk = 8;         // timesteps per sweep pass
 constexpr int kSN = 8;                // outage tiles (8 columns each) per pipeline stage
@@ -120,13 +129,13 @@ template <int MODE>
 struct TCMode {
   static constexpr int AW = MODE == kModeTF32x3 ? 8 : 4;  // A-fragment words per lane and m-tile
   static constexpr int BW = MODE == kModeTF32x3 ? 4 : 2;  // B-fragment words per lane and n-tile
-  static constexpr int kSlots = MODE == kModeTF32x3 ? 3 : 4;  // pipeline depth (shared memory bound)
+  static constexpr int kSlots = TTO_SWEEP_SLOTS;  // pipeline depth
 };
 
 // Shared-memory layout of one pipeline slot.
 template <int MW, int MODE, int TC>
 struct Slot {
-  static constexpr uint32_t kNf = 2 * MW * kSN * 512;                 // -N tiles of the band
+  static constexpr uint32_t kNf = kHalves * MW * kSN * 512;           // -N tiles of the band
   static constexpr uint32_t kVb = kSN * 32 * TCMode<MODE>::BW * 4;    // per topology
   static constexpr uint32_t kG = kSN * 4 * TC * 2 * 4;                // per topology
   static constexpr uint32_t kTopoBytes = kVb + kG;
@@ -134,7 +143,7 @@ struct Slot {
 };
 
 template <int TC, int MW, int MODE>
-__global__ void __launch_bounds__(kWarps * 32, 1)
+__global__ void __launch_bounds__(kWarps * 32, kCtasPerSM)
     sweep_tc_kernel(EvalArgs a, int tci, int n_bands, int n_groups) {
   using S = Slot<MW, MODE, TC>;
   constexpr int AW = TCMode<MODE>::AW, BW = TCMode<MODE>::BW, kSlots = TCMode<MODE>::kSlots;
@@ -144,7 +153,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
   __shared__ int s_issued;          // stages issued so far
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
-  const int tw = warp >> 1, half = warp & 1;
+  const int tw = warp / kHalves, half = warp % kHalves;
   const int tiles_b = (n_bands + kSwB - 1) / kSwB;
   const int tile = blockIdx.x / (kSwB * kSwG), within = blockIdx.x % (kSwB * kSwG);
   const int band = (tile % tiles_b) * kSwB + within % kSwB;
@@ -156,7 +165,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
   const int t0 = tci * TC;
   const int n_mt = a.E_mon_pad >> 4, n_nt = a.O_pad >> 3;
   const int n_stages = n_nt / kSN;
-  const int mt_band = band * 2 * MW;        // first m-tile of the band
+  const int mt_band = band * kHalves * MW;  // first m-tile of the band
   const int mt0 = mt_band + half * MW;      // first m-tile of this warp
   const size_t Ep = a.E_mon_pad;
   const bool producer = threadIdx.x == 0;
@@ -178,15 +187,15 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     if (lane == 0) mbar_expect_tx(&full[sl], S::kNf + n_topo * S::kTopoBytes);
     __syncwarp();
     const int nt0 = s * kSN;
-    const int n_copies = 2 * MW + 2 * n_topo;
+    const int n_copies = kHalves * MW + 2 * n_topo;
     for (int c = lane; c < n_copies; c += 32) {
-      if (c < 2 * MW) {
+      if (c < kHalves * MW) {
         bulk_copy(base + c * (kSN * 512), a.Nf + ((size_t)(mt_band + c) * n_nt + nt0) * 32, kSN * 512, &full[sl]);
       } else {
-        const int w = (c - 2 * MW) >> 1;
+        const int w = (c - kHalves * MW) >> 1;
         const size_t bw = (size_t)grp * kTopo + w;
         unsigned char* wb = base + S::kNf + w * S::kTopoBytes;
-        if (((c - 2 * MW) & 1) == 0)
+        if (((c - kHalves * MW) & 1) == 0)
           bulk_copy(wb, a.Vb + (bw * n_nt + nt0) * 32 * BW, S::kVb, &full[sl]);
         else
           bulk_copy(wb + S::kVb, a.gq + ((bw * a.n_tch + tci) * n_nt + nt0) * 4 * TC * 2, S::kG, &full[sl]);
@@ -296,7 +305,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     int last = 0;
     if (lane == 0) {
       __threadfence_block();  // this warp's reads of the slot precede the release
-      last = atomicAdd(&released[sl], 1) == 2 * n_topo - 1;
+      last = atomicAdd(&released[sl], 1) == kHalves * n_topo - 1;
       if (last) {
         atomicExch(&released[sl], 0);
         __threadfence_block();  // the reset precedes the refill that other warps wait for
@@ -356,7 +365,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     ml = fmaxf(ml, __shfl_xor_sync(0xffffffffu, ml, o));
   }
   if (lane == 0) {
-    float* pp = a.part + ((size_t)b * a.n_parts + (size_t)(band * 2 + half) * a.n_tch + tci) * 4;
+    float* pp = a.part + ((size_t)b * a.n_parts + (size_t)(band * kHalves + half) * a.n_tch + tci) * 4;
     pp[0] = over;
     pp[1] = cnt;
     pp[2] = ml;
@@ -526,7 +535,7 @@ static int launch_tc(EvalArgs& a, int tci, cudaStream_t s) {
   const size_t smem = (size_t)TCMode<MODE>::kSlots * S::kBytes;
   TTO_CUDA_TRY(cudaFuncSetAttribute(sweep_tc_kernel<TC, MW, MODE>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int n_bands = a.E_mon_pad / (32 * MW);
+  const int n_bands = a.E_mon_pad / (16 * kHalves * MW);
   const int n_groups = (a.B + kTopo - 1) / kTopo;
   const int tiles_b = (n_bands + kSwB - 1) / kSwB, tiles_g = (n_groups + kSwG - 1) / kSwG;
   const size_t blocks = (size_t)tiles_b * tiles_g * kSwB * kSwG;
@@ -558,7 +567,7 @@ static int tc_mode(int precision) {
 
 int launch_sweep_tc(EvalArgs& a, cudaStream_t s) {
   if ((a.O_pad >> 3) % kSN != 0) return set_error(TTO_E_ARG, "outage padding is not a multiple of the stage width");
-  if ((a.E_mon_pad >> 4) % 4 != 0) return set_error(TTO_E_ARG, "monitored padding is not a multiple of the band");
+  if ((a.E_mon_pad >> 4) % (2 * kHalves) != 0) return set_error(TTO_E_ARG, "monitored padding is not a multiple of the band");
   const int mode = tc_mode(a.precision);
   const size_t threads = ((size_t)a.E_mon_pad + a.O_pad) * a.B;
   pack_factors_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a, mode);

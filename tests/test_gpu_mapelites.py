@@ -107,7 +107,11 @@ def test_scatter_insert_equals_sequential():
 
 def test_mapelites_trajectory_tto30():
     """20 fused iterations (propose, exact evaluation, insert) against the
-    oracle, compared while no insert decision is a near-tie."""
+    oracle.  Proposals must match bit for bit.  Each cell's new elite must be
+    the oracle's choice, or, where FP32 rounding can reorder candidates whose
+    FP64 fitness lies within twice the largest observed FP32 error (a
+    near-tie between different genomes), one of the tied genomes; the oracle
+    then continues from the GPU's archive."""
     from paper_2605_10128_b300 import Grid, Archive
     c = CONFIGS["tto30"]
     sg = grid30()
@@ -117,17 +121,15 @@ def test_mapelites_trajectory_tto30():
     arch = me.Archive(ds, dm)
     tab = me.ActionTable(sg)
     B = c["batch"]
-    lim_sum = float(sg.limit.sum())
-    tol = parity.TOL_FP32 * lim_sum + parity.TOL_FP32
+    tol = parity.TOL_FP32 * float(sg.limit.sum()) + parity.TOL_FP32
     topo_t = torch.empty(B, sg.k_max, dtype=torch.int32, device="cuda")
     fit_t = torch.empty(B, dtype=torch.float32, device="cuda")
-    compared = 0
+    n_ties = 0
     for it in range(c["iterations"]):
         ref_topo = me.propose(arch, tab, 77, it, B, sg.k_max)
         A.step(77, it, B, topo_out=topo_t, fitness_out=fit_t)
         g.sync_status()
-        got_topo = topo_t.cpu().numpy()
-        np.testing.assert_array_equal(got_topo, ref_topo)
+        np.testing.assert_array_equal(topo_t.cpu().numpy(), ref_topo)
         res = dcflow.evaluate_many(sg, list(ref_topo), processes=parity.n_procs(), d_split=ds, d_moved=dm)
         fref = np.array([r["fitness"] for r in res])
         fgot = fit_t.cpu().numpy().astype(np.float64)
@@ -135,35 +137,30 @@ def test_mapelites_trajectory_tto30():
         assert np.array_equal(fin, np.isfinite(fgot))
         err = float(np.max(np.abs(fgot[fin] - fref[fin]), initial=0.0))
         assert err <= tol
-        # every FP32 fitness is within err of its FP64 value, so an FP64 gap
-        # wider than 2 err between different genomes fixes the GPU's decision
-        # too; a narrower gap is a near-tie that ends the comparison
         gap = 2.0 * err + 1e-12
         cells = np.array([r["cell"] for r in res])
-        tie = False
-        for cc in np.unique(cells[fin]):
-            ids = np.flatnonzero(fin & (cells == cc))
-            top = ids[np.argmax(fref[ids])]
-            for j in ids:
-                if j == top or np.array_equal(ref_topo[j], ref_topo[top]):
-                    continue
-                if fref[j] == fref[top] and fgot[j] == fgot[top]:
-                    continue  # exact tie on both sides: both keep the lower index
-                if fref[top] - fref[j] <= gap:
-                    tie = True
-            inc = arch.elites.get(int(cc))
-            if inc is not None and abs(fref[top] - inc[0]) <= gap and not np.array_equal(inc[1], ref_topo[top]):
-                tie = True
-        arch.insert(cells, fref, ref_topo)
-        if tie:
-            break
         f, gg, fl = A.export()
-        assert set(np.flatnonzero(fl)) == set(arch.elites)
-        for cc, (fv, gv) in arch.elites.items():
-            np.testing.assert_array_equal(gg[cc], gv)
-            assert abs(float(f[cc]) - fv) <= tol
-        # continue from identical archives: the oracle takes the GPU's fitness
+        new_cells = {int(cc) for cc in np.unique(cells[fin])}
+        for cc in range(ds * dm):
+            inc = arch.elites.get(cc)
+            if cc not in new_cells:
+                assert bool(fl[cc]) == (inc is not None)
+                if inc is not None:
+                    np.testing.assert_array_equal(gg[cc], inc[1])
+                continue
+            ids = np.flatnonzero(fin & (cells == cc))
+            best = fref[ids].max()
+            # genomes an exact FP64 insert could keep, widened by the tie gap
+            ok = [ref_topo[j] for j in ids if best - fref[j] <= gap]
+            if inc is not None and inc[0] >= best - gap:
+                ok.append(inc[1])
+            exact = ids[np.argmax(fref[ids])]
+            oracle_pick = inc[1] if (inc is not None and inc[0] >= fref[exact]) else ref_topo[exact]
+            assert fl[cc] == 1
+            assert any(np.array_equal(gg[cc], x) for x in ok), f"cell {cc} holds an invalid elite"
+            if not np.array_equal(gg[cc], oracle_pick):
+                n_ties += 1
+        # continue from the GPU's archive
         arch.elites = {int(cc): (float(f[cc]), gg[cc].copy()) for cc in np.flatnonzero(fl)}
-        compared += 1
-    print(f"tto30 MapElites iterations compared: {compared}")
-    assert compared >= 3
+    print(f"tto30 MapElites: {c['iterations']} iterations checked, {n_ties} near-tie decisions")
+    assert n_ties <= c["iterations"]
