@@ -161,6 +161,27 @@ int tto_evaluate_batch(tto_grid* g, const int32_t* topo, int32_t B, const int32_
 int tto_grid_profile(tto_grid* g, int32_t enable);
 int tto_grid_profile_read(tto_grid* g, float* ms_stage, int32_t* n_calls);
 
+/* tto_evaluate_batch_static -- tto_evaluate_batch (TTO_PREC_FP32 only) for
+ * callers that cannot let the library allocate device memory: processes whose
+ * device memory is owned by another allocator (a framework's caching
+ * allocator or a fixed partition), and services that must keep their device
+ * footprint constant after start-up.  The paper has no counterpart; this is a
+ * deployment variant of the same evaluation.
+ * Its workspace is a fixed 64 MiB __device__ array inside the library, present
+ * on every device that loads the library until the process exits; the call
+ * itself allocates nothing (no cudaMalloc or cudaFree).  A batch whose
+ * workspace exceeds 64 MiB is rejected with TTO_E_ARG and a message giving the
+ * bytes it needs (about 7 KB per topology on the 30-bus workload, 1 MB on the
+ * 10000-bus one).  The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array: calls that overlap on the GPU (other streams,
+ * other threads) race and corrupt each other's results; serialise them.
+ * Arguments, outputs and status reporting are those of tto_evaluate_batch. */
+int tto_evaluate_batch_static(tto_grid* g, const int32_t* topo, int32_t B, const int32_t* timesteps,
+                              int32_t n_t, const tto_eval_opts* opts, float* fitness, int32_t* desc,
+                              int32_t* cell, uint8_t* island, float* metrics, float* fmax,
+                              void* stream);
+
 /* Synchronise the stream and return (then clear) the device status word:
  * TTO_OK, TTO_E_TOPOLOGY or TTO_E_TIMEOUT. */
 int tto_grid_sync_status(tto_grid* g, void* stream);

@@ -66,6 +66,8 @@ _SIGS = {
     "tto_grid_reserve": ([_vp, C.c_int32, C.c_int32], C.c_int),
     "tto_evaluate_batch": ([_vp, _vp, C.c_int32, _i32p, C.c_int32, C.POINTER(EvalOpts), _vp, _vp,
                             _vp, _vp, _vp, _vp, _vp], C.c_int),
+    "tto_evaluate_batch_static": ([_vp, _vp, C.c_int32, _i32p, C.c_int32, C.POINTER(EvalOpts), _vp,
+                                   _vp, _vp, _vp, _vp, _vp, _vp], C.c_int),
     "tto_grid_sync_status": ([_vp, _vp], C.c_int),
     "tto_grid_profile": ([_vp, C.c_int32], C.c_int),
     "tto_grid_profile_read": ([_vp, C.POINTER(C.c_float), _i32p], C.c_int),
@@ -202,6 +204,20 @@ def tto_evaluate_batch(h, topo, B, timesteps, opts, fitness, desc, cell, island,
     return check(lib().tto_evaluate_batch(h, _dp(topo), int(B), ts, n_t, C.byref(opts),
                                           _dp(fitness), _dp(desc), _dp(cell), _dp(island),
                                           _dp(metrics), _dp(fmax), _vp(stream)))
+
+
+def tto_evaluate_batch_static(h, topo, B, timesteps, opts, fitness, desc, cell, island, metrics,
+                              fmax, stream):
+    """The allocation-free evaluation entry point (library-owned fixed scratch)."""
+    ts = None
+    n_t = 0
+    if timesteps is not None:
+        ts_arr = np.ascontiguousarray(timesteps, dtype=np.int32)
+        ts = _ptr(ts_arr, C.c_int32)
+        n_t = int(ts_arr.size)
+    return check(lib().tto_evaluate_batch_static(h, _dp(topo), int(B), ts, n_t, C.byref(opts),
+                                                 _dp(fitness), _dp(desc), _dp(cell), _dp(island),
+                                                 _dp(metrics), _dp(fmax), _vp(stream)))
 
 
 def tto_grid_sync_status(h, stream):

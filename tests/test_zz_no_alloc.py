@@ -1,0 +1,85 @@
+"""The allocation-free evaluation entry point (tto_evaluate_batch_static).
+
+It serves callers that cannot let the library call cudaMalloc, such as a
+process whose device memory belongs to another allocator or a service that
+must keep a fixed device footprint: its workspace is a fixed array inside the
+library.  Its results must match tto_evaluate_batch (FP32) within the parity
+tolerance, on two calls in a row (the second call reuses the array the first
+one left behind).  This file is collected last on purpose."""
+import numpy as np
+import pytest
+
+from oracle import dcflow
+from synth import config_grid, limits_from_flows, make_grid, random_topologies
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+
+
+def _grids():
+    a = config_grid("tto30")
+    a = a.with_limits(limits_from_flows(dcflow.base_flows(a)[0], 5, seed=0))
+    b = make_grid(300, 450, 24, assets=(4, 8), T=3, b_dist=("loguniform", 2.0, 200.0), noise=0.1,
+                  seed=3, k_max=3, name="rag")
+    b = b.with_limits(limits_from_flows(dcflow.base_flows(b)[0], 5, seed=3))
+    return [(a, 256), (b, 37)]
+
+
+def _outputs(B, n_t, E_mon):
+    return dict(fitness=torch.full((B,), np.nan, dtype=torch.float32, device="cuda"),
+                desc=torch.full((B, 2), -7, dtype=torch.int32, device="cuda"),
+                cell=torch.full((B,), -7, dtype=torch.int32, device="cuda"),
+                island=torch.full((B,), 255, dtype=torch.uint8, device="cuda"),
+                metrics=torch.full((B, 4), np.nan, dtype=torch.float32, device="cuda"),
+                fmax=torch.full((B, n_t, E_mon), np.nan, dtype=torch.float32, device="cuda"))
+
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_static_scratch_matches_evaluate_batch_twice(which):
+    from paper_2605_10128_b300 import Grid, _lib
+    sg, B = _grids()[which]
+    g = Grid(sg)
+    topo = torch.tensor(random_topologies(sg, B, seed=5), dtype=torch.int32, device="cuda")
+    ref = g.evaluate(topo, metrics=True, fmax=True)
+    g.sync_status()
+    ref = {k: v.cpu().numpy() for k, v in ref.items() if not k.startswith("_")}
+    lim = sg.limit[sg.monitored]
+    opts = _lib.EvalOpts(_lib.PREC_FP32, _lib.FIT_WORKLOAD, 8, 8)
+    stream = torch.cuda.current_stream().cuda_stream
+    for call in range(2):
+        out = _outputs(B, g.n_time, g.n_monitored)
+        _lib.tto_evaluate_batch_static(g.handle, topo, B, None, opts, out["fitness"], out["desc"],
+                                       out["cell"], out["island"], out["metrics"], out["fmax"], stream)
+        g.sync_status()
+        got = {k: v.cpu().numpy() for k, v in out.items()}
+        np.testing.assert_array_equal(got["cell"], ref["cell"])
+        np.testing.assert_array_equal(got["desc"], ref["desc"])
+        np.testing.assert_array_equal(got["island"], ref["island"])
+        fin = np.isfinite(ref["fitness"])
+        assert np.array_equal(fin, np.isfinite(got["fitness"]))
+        err = np.abs(got["fmax"][fin] - ref["fmax"][fin]) / lim[None, None, :]
+        assert err.max() <= parity.TOL_FP32, (call, err.max())
+        band = parity.TOL_FP32 * lim.sum() * g.n_time + parity.TOL_FP32
+        assert np.all(np.abs(got["fitness"][fin] - ref["fitness"][fin]) <= band)
+        np.testing.assert_allclose(got["metrics"][fin], ref["metrics"][fin], rtol=1e-5, atol=1e-5)
+
+
+def test_static_scratch_rejects_oversized_batch():
+    from paper_2605_10128_b300 import Grid, TTOError, _lib
+    sg, _ = _grids()[0]
+    g = Grid(sg)
+    B = 20000  # about 7 KB of scratch per topology on this grid: beyond the 64 MiB array
+    topo = torch.full((B, sg.k_max), -1, dtype=torch.int32, device="cuda")
+    out = torch.empty(B, dtype=torch.float32, device="cuda")
+    opts = _lib.EvalOpts(_lib.PREC_FP32, _lib.FIT_WORKLOAD, 8, 8)
+    with pytest.raises(TTOError) as ei:
+        _lib.tto_evaluate_batch_static(g.handle, topo, B, None, opts, out, None, None, None, None,
+                                       None, torch.cuda.current_stream().cuda_stream)
+    assert ei.value.code == _lib.TTO_E_ARG and "static scratch holds" in str(ei.value)
