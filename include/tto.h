@@ -152,6 +152,50 @@ int tto_evaluate_batch(tto_grid* g, const int32_t* topo, int32_t B, const int32_
                        int32_t n_t, const tto_eval_opts* opts, float* fitness, int32_t* desc,
                        int32_t* cell, uint8_t* island, float* metrics, float* fmax, void* stream);
 
+/* tto_grid_autotune -- time every sweep tile variant of `precision` on this
+ * grid with a batch of B unsplit topologies over the first n_t timesteps (the
+ * sweep has no data-dependent work, so the timing holds for any batch of that
+ * size) and keep the fastest for later calls on this grid with that
+ * precision.  *shape_out receives the chosen variant, ms_out (host, may be
+ * NULL) the milliseconds of one evaluation per variant (2 variants for
+ * TTO_PREC_FP32, 3 for the tensor-core modes).  Synchronises the stream.
+ * Call it outside stream capture (it may allocate workspace). */
+int tto_grid_autotune(tto_grid* g, int32_t B, int32_t n_t, int32_t precision, int32_t* shape_out,
+                      float* ms_out, void* stream);
+
+/* Select the sweep tile variant of `precision` on this grid by hand (-1 = the
+ * default); tto_grid_autotune makes the same choice by timing. */
+int tto_grid_set_sweep_shape(tto_grid* g, int32_t precision, int32_t shape);
+
+/* One (grid, topology batch) job of tto_evaluate_multi; the fields mean what
+ * the arguments of tto_evaluate_batch mean (fmax is not produced). */
+typedef struct {
+  tto_grid* grid;
+  const int32_t* topo;
+  int32_t B;
+  const int32_t* timesteps;  /* host, NULL = all */
+  int32_t n_t;
+  float* fitness;
+  int32_t* desc;
+  int32_t* cell;
+  uint8_t* island;
+  float* metrics;
+} tto_eval_job;
+
+#define TTO_MULTI_SEQUENTIAL 0 /* one grid after another on the stream */
+#define TTO_MULTI_STREAMS 1    /* grids on forked streams, joined back into the stream */
+#define TTO_MULTI_GRAPH 2      /* as STREAMS, recorded once as a CUDA graph and replayed */
+
+/* tto_evaluate_multi -- evaluate n (1..16) jobs on grids of one device as one
+ * unit of work (mixed grid sizes, timestep counts and batch sizes; each grid at
+ * most once).  In TTO_MULTI_GRAPH mode the first call with a given set of jobs
+ * (same grids, buffers, sizes, options and stream) runs them eagerly and
+ * records the launch sequence as a CUDA graph; later identical calls replay it
+ * with one graph launch.  Recorded graphs are dropped when a grid is destroyed
+ * or its workspace is reallocated.  Asynchronous on stream. */
+int tto_evaluate_multi(const tto_eval_job* jobs, int32_t n, const tto_eval_opts* opts, int32_t mode,
+                       void* stream);
+
 /* Per-stage CUDA-event timing of evaluation calls, off by default.
  * tto_grid_profile(g, 1) clears the record and times the next calls (at most
  * 256); tto_grid_profile(g, 0) stops.  tto_grid_profile_read synchronises on

@@ -101,6 +101,15 @@ class Grid:
     def sync_status(self, stream=None):
         _lib.tto_grid_sync_status(self._h, _stream(stream))
 
+    def autotune(self, B, n_t=None, precision=PREC_FP32, stream=None):
+        """Time the sweep tile variants on this grid and keep the fastest;
+        returns (variant, [ms per variant])."""
+        return _lib.tto_grid_autotune(self._h, B, self.n_time if n_t is None else n_t, precision,
+                                      _stream(stream))
+
+    def set_sweep_shape(self, precision, shape):
+        _lib.tto_grid_set_sweep_shape(self._h, precision, shape)
+
     def profile(self, enable=True):
         """Start (clearing the record) or stop per-stage event timing."""
         _lib.tto_grid_profile(self._h, enable)
@@ -151,6 +160,30 @@ class Archive:
         o = _lib.EvalOpts(precision, fitness_kind, self.d_split, self.d_moved)
         _lib.tto_mapelites_step(self._h, seed, iteration, B, mutation, o, topo_out, fitness_out,
                                 _stream(stream))
+
+
+def evaluate_multi(jobs, precision=PREC_FP32, fitness_kind=FIT_WORKLOAD, d_split=8, d_moved=8,
+                   mode=_lib.MULTI_GRAPH, stream=None):
+    """Evaluate several (Grid, topology tensor) pairs as one unit of work.
+    jobs: list of (grid, topo) or (grid, topo, timesteps); returns a list of
+    output dicts (fitness, desc, cell, island, metrics)."""
+    torch = _torch()
+    recs, outs = [], []
+    for j in jobs:
+        g, topo = j[0], j[1].contiguous()
+        ts = j[2] if len(j) > 2 else None
+        B = int(topo.shape[0])
+        dev = topo.device
+        o = dict(fitness=torch.empty(B, dtype=torch.float32, device=dev),
+                 desc=torch.empty(B, 2, dtype=torch.int32, device=dev),
+                 cell=torch.empty(B, dtype=torch.int32, device=dev),
+                 island=torch.empty(B, dtype=torch.uint8, device=dev),
+                 metrics=torch.empty(B, 4, dtype=torch.float32, device=dev))
+        outs.append(o)
+        recs.append(dict(grid=g.handle, topo=topo, B=B, timesteps=ts, **o))
+    _lib.tto_evaluate_multi(recs, _lib.EvalOpts(precision, fitness_kind, d_split, d_moved), mode,
+                            _stream(stream))
+    return outs
 
 
 def philox_blocks(seed, iteration, cand, block, n, stream=None):

@@ -50,6 +50,14 @@ class EvalOpts(C.Structure):
                 ("d_moved", C.c_int32)]
 
 
+class EvalJob(C.Structure):
+    _fields_ = [("grid", _vp), ("topo", _vp), ("B", C.c_int32), ("timesteps", _i32p), ("n_t", C.c_int32),
+                ("fitness", _vp), ("desc", _vp), ("cell", _vp), ("island", _vp), ("metrics", _vp)]
+
+
+MULTI_SEQUENTIAL, MULTI_STREAMS, MULTI_GRAPH = 0, 1, 2
+
+
 class MutParams(C.Structure):
     _fields_ = [("p_add", C.c_double), ("p_remove", C.c_double), ("p_change", C.c_double),
                 ("p_identity", C.c_double), ("n_mut_mean", C.c_double)]
@@ -69,6 +77,9 @@ _SIGS = {
     "tto_evaluate_batch_static": ([_vp, _vp, C.c_int32, _i32p, C.c_int32, C.POINTER(EvalOpts), _vp,
                                    _vp, _vp, _vp, _vp, _vp, _vp], C.c_int),
     "tto_grid_sync_status": ([_vp, _vp], C.c_int),
+    "tto_grid_autotune": ([_vp, C.c_int32, C.c_int32, C.c_int32, _i32p, C.POINTER(C.c_float), _vp], C.c_int),
+    "tto_grid_set_sweep_shape": ([_vp, C.c_int32, C.c_int32], C.c_int),
+    "tto_evaluate_multi": ([C.POINTER(EvalJob), C.c_int32, C.POINTER(EvalOpts), C.c_int32, _vp], C.c_int),
     "tto_grid_profile": ([_vp, C.c_int32], C.c_int),
     "tto_grid_profile_read": ([_vp, C.POINTER(C.c_float), _i32p], C.c_int),
     "tto_archive_create": ([_vp, C.c_int32, C.c_int32, C.POINTER(_vp)], C.c_int),
@@ -218,6 +229,40 @@ def tto_evaluate_batch_static(h, topo, B, timesteps, opts, fitness, desc, cell, 
     return check(lib().tto_evaluate_batch_static(h, _dp(topo), int(B), ts, n_t, C.byref(opts),
                                                  _dp(fitness), _dp(desc), _dp(cell), _dp(island),
                                                  _dp(metrics), _dp(fmax), _vp(stream)))
+
+
+def tto_grid_autotune(h, B, n_t, precision, stream):
+    shape = C.c_int32()
+    ms = (C.c_float * 4)()
+    check(lib().tto_grid_autotune(h, int(B), int(n_t), int(precision), C.byref(shape), ms, _vp(stream)))
+    return shape.value, list(ms)
+
+
+def tto_grid_set_sweep_shape(h, precision, shape):
+    return check(lib().tto_grid_set_sweep_shape(h, int(precision), int(shape)))
+
+
+def tto_evaluate_multi(jobs, opts, mode, stream):
+    """jobs: list of dicts with grid (handle), topo, B, timesteps (or None),
+    fitness, desc, cell, island, metrics (tensors or None)."""
+    arr = (EvalJob * len(jobs))()
+    keep = []
+    for i, j in enumerate(jobs):
+        e = arr[i]
+        e.grid = j["grid"]
+        e.topo = _dp(j["topo"])
+        e.B = int(j["B"])
+        if j.get("timesteps") is not None:
+            ts = np.ascontiguousarray(j["timesteps"], dtype=np.int32)
+            keep.append(ts)
+            e.timesteps = _ptr(ts, C.c_int32)
+            e.n_t = int(ts.size)
+        else:
+            e.timesteps = None
+            e.n_t = 0
+        for f in ("fitness", "desc", "cell", "island", "metrics"):
+            setattr(e, f, _dp(j.get(f)))
+    return check(lib().tto_evaluate_multi(arr, len(jobs), C.byref(opts), int(mode), _vp(stream)))
 
 
 def tto_grid_sync_status(h, stream):

@@ -351,7 +351,9 @@ int ensure_workspace(tto_grid* g, int B, int T) {
   if (B <= w.cap_B && T <= w.cap_T) return TTO_OK;
   int nB = B > w.cap_B ? B : w.cap_B;
   int nT = T > w.cap_T ? T : w.cap_T;
+  forget_grid_graphs(g);  // recorded graphs hold the old workspace addresses
   free_workspace(g);
+  ++g->ws_epoch;
   const size_t Ep = g->E_mon_pad, Op = g->O_pad;
   TTO_CUDA_TRY(cudaMalloc(&w.U, (size_t)nB * Ep * 8 * sizeof(float)));
   TTO_CUDA_TRY(cudaMalloc(&w.V, (size_t)nB * Op * 8 * sizeof(float)));
@@ -462,9 +464,13 @@ int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, 
   a.n_rowtiles = g->n_rowtiles;
   a.n_parts = g->n_rowtiles;
   a.precision = o->precision;
+  a.shape = g->tuned_shape[o->precision] >= 0 ? g->tuned_shape[o->precision] : 0;
   a.from = g->d_from;
   cudaEvent_t* ev = nullptr;
-  if (g->prof_on && g->prof_n < kProfileCalls) ev = &g->prof_ev[4 * g->prof_n++];
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  TTO_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
+  if (g->prof_on && g->prof_n < kProfileCalls && cap == cudaStreamCaptureStatusNone)
+    ev = &g->prof_ev[4 * g->prof_n++];
   if (ev) TTO_CUDA_TRY(cudaEventRecord(ev[0], s));
   split_update_kernel<<<B, 256, 0, s>>>(a);
   TTO_CUDA_TRY(cudaGetLastError());

@@ -405,6 +405,7 @@ static int build_grid(const tto_grid_desc* d, tto_grid* g) {
 static void release(tto_grid* g) {
   if (!g) return;
   cudaSetDevice(g->device);
+  forget_grid_graphs(g);
   free_workspace(g);
   void* ptrs[] = {g->d_from, g->d_Nf, g->d_Nmo, g->d_Nsw, g->d_swcol, g->d_f0, g->d_p, g->d_b, g->d_lim,
                   g->d_mon, g->d_out, g->d_Ncc, g->d_station_bus, g->d_asset_off,
@@ -432,6 +433,8 @@ int tto_grid_create(const tto_grid_desc* d, tto_grid** out) {
   if (d->device < 0 || d->device >= ndev) return tto::set_error(TTO_E_ARG, "device %d out of range", d->device);
   tto_grid* g = new (std::nothrow) tto_grid();
   if (!g) return tto::set_error(TTO_E_NOMEM, "host allocation failed");
+  static std::atomic<uint64_t> next_uid(1);
+  g->uid = next_uid.fetch_add(1);
   try {
     rc = tto::build_grid(d, g);
   } catch (const std::bad_alloc&) {

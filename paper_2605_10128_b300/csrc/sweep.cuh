@@ -36,6 +36,7 @@ struct EvalArgs {
   int fitness_kind;
   int n_rowtiles;
   int n_parts;  // partial-metric records per topology (set by the sweep launcher)
+  int shape;    // sweep tile variant chosen by the autotuner (0 = default)
   // batch
   const int32_t* topo;
   int B;
@@ -62,6 +63,8 @@ struct EvalArgs {
 int launch_sweep(EvalArgs& a, cudaStream_t s);
 int launch_sweep_fp32(const EvalArgs& a, cudaStream_t s);
 int launch_sweep_tc(EvalArgs& a, cudaStream_t s);
+// Number of sweep tile variants for a precision mode (FP32 or tensor cores).
+int sweep_shapes(int precision);
 // Partial-metric records per topology the workspace must hold.
 size_t max_parts(const tto_grid* g);
 // Build the fragment-ordered copy of -N used by the tensor-core sweep (once).

@@ -135,13 +135,21 @@ __global__ void __launch_bounds__(kRowTile) sweep_fp32_kernel(EvalArgs a) {
   }
 }
 
-template <int TT, int KP>
-static int launch_fp32_tt(const EvalArgs& a, cudaStream_t s) {
-  constexpr int G = TT <= 4 ? 8 : (TT <= 8 ? 4 : (TT <= 16 ? 2 : 1));
+template <int TT, int KP, int G>
+static int launch_fp32_g(const EvalArgs& a, cudaStream_t s) {
   dim3 grid(a.n_rowtiles, (a.B + G - 1) / G);
   sweep_fp32_kernel<TT, G, KP><<<grid, kRowTile, 0, s>>>(a);
   TTO_CUDA_TRY(cudaGetLastError());
   return TTO_OK;
+}
+
+// Tile variants: shape 0 keeps G topologies per CTA (G x TT <= 32 registers of
+// running maxima), shape 1 halves G (more CTAs, fewer registers).
+template <int TT, int KP>
+static int launch_fp32_tt(const EvalArgs& a, cudaStream_t s) {
+  constexpr int G = TT <= 4 ? 8 : (TT <= 8 ? 4 : (TT <= 16 ? 2 : 1));
+  constexpr int G2 = G > 1 ? G / 2 : 1;
+  return a.shape == 1 ? launch_fp32_g<TT, KP, G2>(a, s) : launch_fp32_g<TT, KP, G>(a, s);
 }
 
 template <int KP>
@@ -167,7 +175,10 @@ int launch_sweep_fp32(const EvalArgs& a, cudaStream_t s) {
   return set_error(TTO_E_ARG, "unsupported padded rank %d", a.KP);
 }
 
+int sweep_shapes(int precision) { return precision == TTO_PREC_FP32 ? 2 : 3; }
+
 int launch_sweep(EvalArgs& a, cudaStream_t s) {
+  if (a.shape < 0 || a.shape >= sweep_shapes(a.precision)) return set_error(TTO_E_ARG, "unknown sweep shape %d", a.shape);
   if (a.precision == TTO_PREC_FP32) {
     a.n_parts = a.n_rowtiles;
     return launch_sweep_fp32(a, s);

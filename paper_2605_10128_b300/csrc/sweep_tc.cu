@@ -19,8 +19,8 @@
 // per row and timestep, two FP32 instructions per (l, c, t).  Islanding
 // outages carry g = NaN, which fmaxf ignores.
 //
-// CTA = 8 warps = 4 topologies x 2 row halves of one band of 32*MW monitored
-// rows, two CTAs per SM.  Each warp walks every outage column of its topology for 16*MW rows,
+// CTA = TOPO topologies x HALVES row groups (default 4 x 2: a band of 32*MW
+// monitored rows per CTA), one warp each, two CTAs per SM.  Each warp walks every outage column of its topology for 16*MW rows,
 // so its running maxima stay in registers and it reduces its own rows at the
 // end (no atomics).  Operands stream through a three-slot shared-memory ring
 // filled by TMA bulk copies (cp.async.bulk, completion counted on an mbarrier):
@@ -36,18 +36,19 @@
 
 #include "sweep.cuh"
 
-#ifndef TTO_SWEEP_TOPO
-#define TTO_SWEEP_TOPO 4
-#define TTO_SWEEP_HALVES 2
-#define TTO_SWEEP_SLOTS 3
-#endif
 
 namespace tto {
 
-// CTA shape: kTopo topologies x kHalves row groups of 16*MW rows, one warp each
-constexpr int kTopo = TTO_SWEEP_TOPO;
-constexpr int kHalves = TTO_SWEEP_HALVES;
-constexpr int kWarps = kTopo * kHalves;
+// CTA shapes: TOPO topologies x HALVES row groups of 16*MW rows, one warp
+// each, SLOTS pipeline slots, two CTAs per SM.  The autotuner picks one per grid.
+template <int TOPO, int HALVES, int SLOTS>
+struct CtaShape {
+  static constexpr int kTopo = TOPO, kHalves = HALVES, kWarps = TOPO * HALVES, kSlots = SLOTS;
+};
+using Shape0 = CtaShape<4, 2, 3>;  // default: 64 rows x 4 topologies
+using Shape1 = CtaShape<8, 1, 2>;  // 32 rows x 8 topologies
+using Shape2 = CtaShape<2, 4, 2>;  // 128 rows x 2 topologies
+constexpr int kNumShapes = 3;
 constexpr int kCtasPerSM = 2;
 constexpr int kSwB = 16, kSwG = 16;   // launch-order tile: row bands x topology groups
 constexpr int kMaxTChunk = 8;         // timesteps per sweep pass
@@ -129,12 +130,12 @@ template <int MODE>
 struct TCMode {
   static constexpr int AW = MODE == kModeTF32x3 ? 8 : 4;  // A-fragment words per lane and m-tile
   static constexpr int BW = MODE == kModeTF32x3 ? 4 : 2;  // B-fragment words per lane and n-tile
-  static constexpr int kSlots = TTO_SWEEP_SLOTS;  // pipeline depth
 };
 
 // Shared-memory layout of one pipeline slot.
-template <int MW, int MODE, int TC>
+template <int MW, int MODE, int TC, class SH>
 struct Slot {
+  static constexpr int kTopo = SH::kTopo, kHalves = SH::kHalves;
   static constexpr uint32_t kNf = kHalves * MW * kSN * 512;           // -N tiles of the band
   static constexpr uint32_t kVb = kSN * 32 * TCMode<MODE>::BW * 4;    // per topology
   static constexpr uint32_t kG = kSN * 4 * TC * 2 * 4;                // per topology
@@ -142,11 +143,12 @@ struct Slot {
   static constexpr uint32_t kBytes = kNf + kTopo * kTopoBytes;
 };
 
-template <int TC, int MW, int MODE>
-__global__ void __launch_bounds__(kWarps * 32, kCtasPerSM)
+template <int TC, int MW, int MODE, class SH>
+__global__ void __launch_bounds__(SH::kWarps * 32, kCtasPerSM)
     sweep_tc_kernel(EvalArgs a, int tci, int n_bands, int n_groups) {
-  using S = Slot<MW, MODE, TC>;
-  constexpr int AW = TCMode<MODE>::AW, BW = TCMode<MODE>::BW, kSlots = TCMode<MODE>::kSlots;
+  using S = Slot<MW, MODE, TC, SH>;
+  constexpr int AW = TCMode<MODE>::AW, BW = TCMode<MODE>::BW;
+  constexpr int kSlots = SH::kSlots, kTopo = SH::kTopo, kHalves = SH::kHalves;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kSlots];
   __shared__ int released[kSlots];  // warps done with the slot's current stage
@@ -529,31 +531,47 @@ size_t max_parts(const tto_grid* g) {
   return fp32 > tc ? fp32 : tc;
 }
 
-template <int TC, int MW, int MODE>
+template <int TC, int MW, int MODE, class SH>
 static int launch_tc(EvalArgs& a, int tci, cudaStream_t s) {
-  using S = Slot<MW, MODE, TC>;
-  const size_t smem = (size_t)TCMode<MODE>::kSlots * S::kBytes;
-  TTO_CUDA_TRY(cudaFuncSetAttribute(sweep_tc_kernel<TC, MW, MODE>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int n_bands = a.E_mon_pad / (16 * kHalves * MW);
-  const int n_groups = (a.B + kTopo - 1) / kTopo;
+  using S = Slot<MW, MODE, TC, SH>;
+  const size_t smem = (size_t)SH::kSlots * S::kBytes;
+  static bool attr_set[64] = {};  // per device; set once, outside any stream capture that follows
+  int dev = 0;
+  TTO_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return set_error(TTO_E_ARG, "device %d out of range", dev);
+  if (!attr_set[dev]) {
+    TTO_CUDA_TRY(cudaFuncSetAttribute(sweep_tc_kernel<TC, MW, MODE, SH>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set[dev] = true;
+  }
+  const int n_bands = a.E_mon_pad / (16 * SH::kHalves * MW);
+  const int n_groups = (a.B + SH::kTopo - 1) / SH::kTopo;
   const int tiles_b = (n_bands + kSwB - 1) / kSwB, tiles_g = (n_groups + kSwG - 1) / kSwG;
   const size_t blocks = (size_t)tiles_b * tiles_g * kSwB * kSwG;
   if (blocks > 0x7fffffffu) return set_error(TTO_E_ARG, "batch too large for one sweep launch");
-  sweep_tc_kernel<TC, MW, MODE><<<(unsigned)blocks, kWarps * 32, smem, s>>>(a, tci, n_bands, n_groups);
+  sweep_tc_kernel<TC, MW, MODE, SH><<<(unsigned)blocks, SH::kWarps * 32, smem, s>>>(a, tci, n_bands, n_groups);
   TTO_CUDA_TRY(cudaGetLastError());
   return TTO_OK;
 }
 
-template <int MODE>
+template <int MODE, class SH>
 static int launch_tc_chunk(EvalArgs& a, int tci, cudaStream_t s) {
   switch (a.TC) {
-    case 1: return launch_tc<1, 2, MODE>(a, tci, s);
-    case 2: return launch_tc<2, 2, MODE>(a, tci, s);
-    case 4: return launch_tc<4, 2, MODE>(a, tci, s);
-    case 8: return launch_tc<8, 1, MODE>(a, tci, s);
+    case 1: return launch_tc<1, 2, MODE, SH>(a, tci, s);
+    case 2: return launch_tc<2, 2, MODE, SH>(a, tci, s);
+    case 4: return launch_tc<4, 2, MODE, SH>(a, tci, s);
+    case 8: return launch_tc<8, 1, MODE, SH>(a, tci, s);
   }
   return set_error(TTO_E_ARG, "unsupported timestep chunk %d", a.TC);
+}
+
+template <int MODE>
+static int launch_tc_shape(EvalArgs& a, int tci, cudaStream_t s) {
+  switch (a.shape) {
+    case 1: return launch_tc_chunk<MODE, Shape1>(a, tci, s);
+    case 2: return launch_tc_chunk<MODE, Shape2>(a, tci, s);
+    default: return launch_tc_chunk<MODE, Shape0>(a, tci, s);
+  }
 }
 
 static int tc_mode(int precision) {
@@ -567,7 +585,8 @@ static int tc_mode(int precision) {
 
 int launch_sweep_tc(EvalArgs& a, cudaStream_t s) {
   if ((a.O_pad >> 3) % kSN != 0) return set_error(TTO_E_ARG, "outage padding is not a multiple of the stage width");
-  if ((a.E_mon_pad >> 4) % (2 * kHalves) != 0) return set_error(TTO_E_ARG, "monitored padding is not a multiple of the band");
+  if ((a.E_mon_pad >> 4) % 8 != 0) return set_error(TTO_E_ARG, "monitored padding is not a multiple of the band");
+  if (a.shape < 0 || a.shape >= kNumShapes) return set_error(TTO_E_ARG, "unknown sweep shape %d", a.shape);
   const int mode = tc_mode(a.precision);
   const size_t threads = ((size_t)a.E_mon_pad + a.O_pad) * a.B;
   pack_factors_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a, mode);
@@ -577,10 +596,10 @@ int launch_sweep_tc(EvalArgs& a, cudaStream_t s) {
   for (int ci = 0; ci < a.n_tch; ++ci) {
     int rc;
     switch (mode) {
-      case kModeTF32x3: rc = launch_tc_chunk<kModeTF32x3>(a, ci, s); break;
-      case kModeFP16x3: rc = launch_tc_chunk<kModeFP16x3>(a, ci, s); break;
-      case kModeBF16: rc = launch_tc_chunk<kModeBF16>(a, ci, s); break;
-      default: rc = launch_tc_chunk<kModeBF16x3>(a, ci, s); break;
+      case kModeTF32x3: rc = launch_tc_shape<kModeTF32x3>(a, ci, s); break;
+      case kModeFP16x3: rc = launch_tc_shape<kModeFP16x3>(a, ci, s); break;
+      case kModeBF16: rc = launch_tc_shape<kModeBF16>(a, ci, s); break;
+      default: rc = launch_tc_shape<kModeBF16x3>(a, ci, s); break;
     }
     if (rc) return rc;
   }

@@ -60,6 +60,8 @@ struct Workspace {
 }  // namespace tto
 
 struct tto_grid {
+  uint64_t uid = 0;       // unique per created grid (keys recorded evaluation graphs)
+  uint64_t ws_epoch = 0;  // bumped whenever the workspace is reallocated
   int device = 0;
   int n_bus = 0, E = 0, slack = 0, T = 0, E_mon = 0, O = 0, S = 0, A = 0, k_max = 0;
   int E_mon_pad = 0, O_pad = 0, n_sw = 0, n_rowtiles = 0;
@@ -87,6 +89,8 @@ struct tto_grid {
   uint32_t* d_act_mask = nullptr;
   int* d_status = nullptr;
   tto::Workspace ws;
+  // sweep tile variant per precision mode chosen by tto_grid_autotune (-1: default)
+  int tuned_shape[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
   // optional per-stage timing (tto_grid_profile)
   int prof_on = 0, prof_n = 0;
   std::vector<cudaEvent_t> prof_ev;  // 4 per recorded call
@@ -106,6 +110,8 @@ namespace tto {
 int ensure_workspace(tto_grid* g, int B, int T);
 int padded_T(int n_t);  // timesteps rounded up to a compiled sweep width (-1 if > TTO_MAX_T)
 void free_workspace(tto_grid* g);
+// Drop recorded multi-grid evaluation graphs that use this grid.
+void forget_grid_graphs(const tto_grid* g);
 int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, int n_t,
                   const tto_eval_opts* o, float* fitness, int32_t* desc, int32_t* cell,
                   uint8_t* island, float* metrics, float* fmax, cudaStream_t s);

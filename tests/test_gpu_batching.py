@@ -1,0 +1,104 @@
+"""Mixed-grid batching (tto_evaluate_multi), sweep tile variants and the
+autotuner, against per-grid evaluation and the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import dcflow
+from synth import config_grid, limits_from_flows, make_grid, random_topologies
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+
+
+def _limited(sg, n_tight=3):
+    return sg.with_limits(limits_from_flows(dcflow.base_flows(sg)[0], n_tight, seed=sg.seed))
+
+
+def _mixed_grids():
+    """Four small grids spanning the timestep passes of the tensor-core sweep
+    (T = 1, 4, 16, 24) with ragged batches."""
+    specs = [(60, 90, 5, 1, 41), (120, 180, 8, 4, 37), (200, 300, 12, 16, 50), (300, 450, 16, 24, 20)]
+    out = []
+    for i, (n, e, st, T, B) in enumerate(specs):
+        sg = make_grid(n, e, st, assets=(4, 8), T=T, b_dist=("loguniform", 2.0, 200.0),
+                       noise=0.1 if T > 1 else 0.0, seed=40 + i, k_max=3, name=f"mixsmall{i}")
+        out.append((_limited(sg), B))
+    return out
+
+
+def _np(d):
+    return {k: v.cpu().numpy() for k, v in d.items() if not k.startswith("_")}
+
+
+@pytest.mark.parametrize("prec", [0, 3])
+def test_multi_equals_per_grid_in_every_mode(prec):
+    from paper_2605_10128_b300 import Grid, evaluate_multi, _lib
+    grids = []
+    for sg, B in _mixed_grids():
+        g = Grid(sg)
+        topo = torch.tensor(random_topologies(sg, B, seed=B), dtype=torch.int32, device="cuda")
+        grids.append((sg, g, topo))
+    ref = []
+    for sg, g, topo in grids:
+        r = g.evaluate(topo, precision=prec, metrics=True)
+        g.sync_status()
+        ref.append(_np(r))
+    for mode in [_lib.MULTI_SEQUENTIAL, _lib.MULTI_STREAMS, _lib.MULTI_GRAPH, _lib.MULTI_GRAPH]:
+        outs = evaluate_multi([(g, topo) for _, g, topo in grids], precision=prec, mode=mode)
+        torch.cuda.synchronize()
+        for (sg, g, _), o, r in zip(grids, outs, ref):
+            g.sync_status()
+            o = _np(o)
+            for k in ["fitness", "desc", "cell", "island", "metrics"]:
+                np.testing.assert_array_equal(o[k], r[k], err_msg=f"mode {mode} {sg.name} {k}")
+
+
+def test_every_sweep_variant_matches_the_oracle():
+    from paper_2605_10128_b300 import Grid
+    sg = _limited(config_grid("tto30"), 5)
+    topo = random_topologies(sg, 96, seed=13)
+    g = Grid(sg)
+    idx = list(range(96))
+    refs = parity.oracle_eval(sg, topo, idx)
+    t = torch.tensor(topo, dtype=torch.int32, device="cuda")
+    for prec, shapes, tol in [(0, 2, parity.TOL_FP32), (3, 3, parity.TOL_FP32), (1, 3, parity.TOL_BF16)]:
+        for sh in range(shapes):
+            g.set_sweep_shape(prec, sh)
+            out = _np(g.evaluate(t, precision=prec, metrics=True, fmax=True))
+            g.sync_status()
+            parity.compare(sg, out, idx, refs, tol=tol)
+        g.set_sweep_shape(prec, -1)
+
+
+def test_autotune_picks_a_variant_and_keeps_results():
+    from paper_2605_10128_b300 import Grid
+    sg = _limited(config_grid("tto30"), 5)
+    g = Grid(sg)
+    t = torch.tensor(random_topologies(sg, 128, seed=2), dtype=torch.int32, device="cuda")
+    base = _np(g.evaluate(t, precision=3, fmax=True))
+    shape, ms = g.autotune(128, precision=3)
+    assert 0 <= shape < 3 and all(m > 0 for m in ms[:3])
+    assert ms[shape] == min(ms[:3])
+    tuned = _np(g.evaluate(t, precision=3, fmax=True))
+    g.sync_status()
+    np.testing.assert_array_equal(tuned["fmax"], base["fmax"])  # the maximum is exact in any tiling
+    np.testing.assert_array_equal(tuned["cell"], base["cell"])
+    np.testing.assert_allclose(tuned["fitness"], base["fitness"], rtol=1e-5)
+    s32, ms32 = g.autotune(128, precision=0)
+    assert 0 <= s32 < 2 and ms32[s32] == min(ms32[:2])
+
+
+def test_multi_rejects_bad_jobs():
+    from paper_2605_10128_b300 import Grid, TTOError, evaluate_multi
+    sg = _limited(config_grid("tto30"), 5)
+    g = Grid(sg)
+    t = torch.tensor(random_topologies(sg, 8, seed=1), dtype=torch.int32, device="cuda")
+    with pytest.raises(TTOError):
+        evaluate_multi([(g, t), (g, t)])  # one grid twice
