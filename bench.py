@@ -187,6 +187,56 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+MIX = ["mix500", "mix2k", "mix5k", "mix10k"]
+
+
+def run_mixed(args, prec, pk, pk_kind):
+    """Mixed-grid batching: the four grids of different size, timestep count and
+    batch size evaluated as one unit, per-grid launches vs one recorded graph;
+    each grid's sweep tile variant comes from the autotuner."""
+    import torch
+    from paper_2605_10128_b300 import evaluate_multi, _lib
+    grids, topos, total = [], [], 0
+    tune = {}
+    for i, name in enumerate(MIX):
+        c = CONFIGS[name]
+        sg, g, _ = make_grid(name, 0, seed=0)
+        B = c["batch"]
+        g.reserve(B)
+        tune[name] = g.autotune(min(B, 512), precision=prec)
+        topo = torch.from_numpy(random_topologies(sg, B, seed=11 + i)).cuda()
+        grids.append(g)
+        topos.append(topo)
+        total += B
+    jobs = list(zip(grids, topos))
+    res = {}
+    for label, mode in [("per_grid_launches", _lib.MULTI_SEQUENTIAL), ("one_graph", _lib.MULTI_GRAPH)]:
+        for _ in range(max(1, args.warmup)):
+            evaluate_multi(jobs, precision=prec, mode=mode)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            evaluate_multi(jobs, precision=prec, mode=mode)
+        e1.record()
+        torch.cuda.synchronize()
+        res[label] = e0.elapsed_time(e1) / args.steps
+    for g in grids:
+        g.sync_status()
+    line = {"metric": "N-1 topology evals/s (mixed 500/2000/5000/10000-bus batch)",
+            "value": total / (res["one_graph"] / 1000.0), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["one_graph"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "mix: " + ", ".join(workload_desc(n, CONFIGS[n]["batch"]) for n in MIX),
+                       "precision": args.precision,
+                       "tile_variants": {n: {"chosen": tune[n][0], "ms_per_variant_at_B512": tune[n][1]} for n in MIX}},
+            "per_grid_launches": {"value": total / (res["per_grid_launches"] / 1000.0), "unit": UNIT,
+                                  "ms_per_step": res["per_grid_launches"]},
+            "gpu_launches": None}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -216,6 +266,11 @@ def main():
         dist.init_process_group("nccl")
     prec = {"fp32": PREC_FP32, "fp16x3": PREC_FP16X3, "tf32x3": PREC_TF32X3, "bf16x3": PREC_BF16X3,
             "bf16": PREC_BF16}[args.precision]
+    if args.config == "mix":
+        if rank == 0:
+            pk, pk_kind = peaks()
+            run_mixed(args, prec, pk, pk_kind)
+        return
     c = CONFIGS[args.config]
     B = args.batch or c["batch"]
     ds, dm = c["archive"]

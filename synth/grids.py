@@ -333,7 +333,8 @@ CONFIGS = {
     "tto10k": dict(n_bus=10000, n_branch=15000, n_station=400, assets=(4, 10), T=4,
                    b_dist=("loguniform", 2.0, 200.0), noise=0.1, n_outage=5000, k_max=6,
                    n_tight=150, batch=8192, archive=(20, 20), iterations=1000),
-    # mixed-size members of the one-launch batching workload
+    # mixed-size members of the one-launch batching workload (the two large grids
+    # sample a third of their branches as outages, like the 10000-bus workload)
     "mix500": dict(n_bus=500, n_branch=750, n_station=40, assets=(4, 10), T=1,
                    b_dist=("loguniform", 2.0, 200.0), noise=0.1, n_outage=None, k_max=4,
                    n_tight=8, batch=1024, archive=(8, 8), iterations=20),
@@ -341,10 +342,10 @@ CONFIGS = {
                   b_dist=("loguniform", 2.0, 200.0), noise=0.1, n_outage=None, k_max=4,
                   n_tight=30, batch=2048, archive=(8, 8), iterations=20),
     "mix5k": dict(n_bus=5000, n_branch=7500, n_station=250, assets=(4, 10), T=16,
-                  b_dist=("loguniform", 2.0, 200.0), noise=0.1, n_outage=None, k_max=4,
+                  b_dist=("loguniform", 2.0, 200.0), noise=0.1, n_outage=2500, k_max=4,
                   n_tight=75, batch=4096, archive=(8, 8), iterations=20),
     "mix10k": dict(n_bus=10000, n_branch=15000, n_station=400, assets=(4, 10), T=24,
-                   b_dist=("loguniform", 2.0, 200.0), noise=0.1, n_outage=None, k_max=4,
+                   b_dist=("loguniform", 2.0, 200.0), noise=0.1, n_outage=5000, k_max=4,
                    n_tight=150, batch=8192, archive=(8, 8), iterations=20),
 }
 
