@@ -30,6 +30,10 @@ struct StreamPool {
   std::vector<cudaStream_t> side;
   cudaEvent_t fork = nullptr;
   std::vector<cudaEvent_t> join;
+  // graph mode records and replays on this stream (a legacy default stream,
+  // which callers often pass, cannot be captured), joined to the caller's
+  cudaStream_t cap = nullptr;
+  cudaEvent_t cap_in = nullptr, cap_out = nullptr;
 };
 
 std::recursive_mutex g_mu;  // recursive: workspace growth drops graphs while a call holds it
@@ -39,6 +43,11 @@ int stream_pool(int dev, int n, StreamPool** out) {
   if (dev < 0 || dev >= 64) return set_error(TTO_E_ARG, "device %d out of range", dev);
   StreamPool& p = g_pool[dev];
   if (!p.fork) TTO_CUDA_TRY(cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming));
+  if (!p.cap) {
+    TTO_CUDA_TRY(cudaStreamCreateWithFlags(&p.cap, cudaStreamNonBlocking));
+    TTO_CUDA_TRY(cudaEventCreateWithFlags(&p.cap_in, cudaEventDisableTiming));
+    TTO_CUDA_TRY(cudaEventCreateWithFlags(&p.cap_out, cudaEventDisableTiming));
+  }
   while ((int)p.side.size() < n) {
     cudaStream_t st;
     TTO_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
@@ -63,9 +72,8 @@ struct GraphEntry {
 
 std::map<GraphKey, GraphEntry> g_graphs;
 
-GraphKey make_key(const tto_eval_job* jobs, int n, const tto_eval_opts* o, cudaStream_t s) {
+GraphKey make_key(const tto_eval_job* jobs, int n, const tto_eval_opts* o) {
   GraphKey k;
-  k.words.push_back((uint64_t)(uintptr_t)s);
   k.words.push_back(((uint64_t)o->precision << 48) | ((uint64_t)o->fitness_kind << 32) |
                     ((uint64_t)o->d_split << 16) | (uint64_t)o->d_moved);
   for (int i = 0; i < n; ++i) {
@@ -225,18 +233,25 @@ extern "C" int tto_evaluate_multi(const tto_eval_job* jobs, int32_t n, const tto
       if (rc) return rc;
     }
   }
-  GraphKey key = make_key(jobs, n, opts, s);
+  GraphKey key = make_key(jobs, n, opts);
+  cudaStream_t cs = pool->cap;
+  TTO_CUDA_TRY(cudaEventRecord(pool->cap_in, s));
+  TTO_CUDA_TRY(cudaStreamWaitEvent(cs, pool->cap_in, 0));
   auto it = g_graphs.find(key);
   if (it != g_graphs.end()) {
-    TTO_CUDA_TRY(cudaGraphLaunch(it->second.exec, s));
+    TTO_CUDA_TRY(cudaGraphLaunch(it->second.exec, cs));
+    TTO_CUDA_TRY(cudaEventRecord(pool->cap_out, cs));
+    TTO_CUDA_TRY(cudaStreamWaitEvent(s, pool->cap_out, 0));
     return TTO_OK;
   }
-  rc = run_forked(jobs, n, opts, s, pool);
+  rc = run_forked(jobs, n, opts, cs, pool);
   if (rc) return rc;
-  TTO_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  rc = run_forked(jobs, n, opts, s, pool);
+  TTO_CUDA_TRY(cudaEventRecord(pool->cap_out, cs));
+  TTO_CUDA_TRY(cudaStreamWaitEvent(s, pool->cap_out, 0));
+  TTO_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  rc = run_forked(jobs, n, opts, cs, pool);
   cudaGraph_t graph = nullptr;
-  cudaError_t e = cudaStreamEndCapture(s, &graph);
+  cudaError_t e = cudaStreamEndCapture(cs, &graph);
   if (rc) {
     if (graph) cudaGraphDestroy(graph);
     return rc;
