@@ -272,6 +272,104 @@ int tto_mapelites_step(tto_archive* a, uint64_t seed, uint64_t iteration, int32_
 int tto_philox_blocks(uint64_t seed, uint64_t iteration, uint32_t cand, uint32_t block, int32_t n,
                       uint32_t* out, void* stream);
 
+/* ------------------------------------------------------------ surrogate
+ * A learned screen for MapElites proposals.  The paper has no counterpart; the
+ * network, its inputs and its online training are this library's own.
+ *
+ * Model: y = w4 . h3 + b4,  h3 = relu(W3 h2 + b3),  h2 = relu(W2 h1 + b2),
+ * h1 = relu(W1 x + b1), predicting log1p(-fitness) (lower is better) of a
+ * topology.  Input x (dimension D = 8 S + R, S stations): for every station
+ * split by the genome eight values
+ *   [1, min(|A|,|B|)/m, b(B)/b(station), p_B(t=0) / sum|p(t=0)|,
+ *    branches on B / branches of the station, |B|/m, 0, 0]
+ * (m assets, |B| assets on the second busbar, b() summed branch susceptance),
+ * zero for unsplit stations; then the post-split N-0 loading |f'_l| / fbar_l
+ * at timestep 0 of the R branches with the highest base-case loading (sorted
+ * by loading, descending, ties by branch id; fixed when the surrogate is
+ * created).  Parameters are kept in FP32, packed as W1 [H][D], b1 [H],
+ * W2 [H][H], b2 [H], W3 [H][H], b3 [H], w4 [H], b4 [1]; every product rounds
+ * both operands to BF16 and accumulates in FP32 (tensor cores for the dense
+ * products).  Training: the network fits the standardised target
+ * (log1p(-fitness) - mean) / deviation, mean and population standard
+ * deviation taken over the finite targets in the replay ring (recomputed after
+ * every append; 0 and 1 while it is empty), by mean squared error over a
+ * minibatch drawn uniformly (Philox keyed by the seed) from the ring, and Adam
+ * with bias correction.  All calls are deterministic for a given call
+ * sequence. */
+typedef struct tto_surrogate tto_surrogate;
+
+typedef struct {
+  int32_t hidden;    /* H, multiple of 16 in [16, 1024] */
+  int32_t n_load;    /* R loading features, 1..n_branch */
+  int32_t replay;    /* capacity of the replay ring (pairs) */
+  int32_t minibatch; /* rows per training step */
+  double lr, beta1, beta2, eps; /* Adam */
+  uint64_t seed;     /* initial weights (He-uniform, zero biases) and minibatch draws */
+} tto_surrogate_cfg;
+
+/* Create a surrogate for grid g (which must outlive it).  Errors: TTO_E_ARG
+ * for a configuration out of range, TTO_E_CUDA / TTO_E_NOMEM. */
+int tto_surrogate_create(tto_grid* g, const tto_surrogate_cfg* cfg, tto_surrogate** out);
+int tto_surrogate_destroy(tto_surrogate* s);
+
+/* Sizes: number of packed parameters, input dimension D, pairs in the replay
+ * ring; rows_out (host int32 [R], optional) receives the loading branches and
+ * target_stats (host float [2], optional) the current target mean and
+ * deviation (both synchronise the device).  Any pointer may be NULL. */
+int tto_surrogate_info(const tto_surrogate* s, int64_t* n_params, int32_t* input_dim,
+                       int32_t* replay_fill, int32_t* rows_out, float* target_stats);
+
+/* Copy the packed FP32 parameters to get_host and/or replace them from
+ * set_host (host float [n_params]; either may be NULL).  Setting clears the
+ * Adam moments and step count.  Synchronises the device. */
+int tto_surrogate_params(tto_surrogate* s, float* get_host, const float* set_host);
+
+/* Predicted log1p(-fitness) of B genomes (device int32 [B][k_max]) into score
+ * (device float [B]): mean + deviation * network output, +inf for a genome
+ * whose split islands the grid or that splits a station twice.  Asynchronous
+ * on stream. */
+int tto_surrogate_score(tto_surrogate* s, const int32_t* topo, int32_t B, float* score, void* stream);
+
+/* Host copies of the inputs of the last batch that was scored, added or
+ * differentiated (B of its rows): station of each genome slot si [B][k_max]
+ * (-1 = empty), that station's eight values sf [B][k_max][8], loadings
+ * xd [B][R] and valid [B] (0 = the split islands the grid).  Any pointer may
+ * be NULL.  Synchronises the device. */
+int tto_surrogate_features(tto_surrogate* s, int32_t B, int32_t* si, float* sf, float* xd,
+                           int32_t* valid);
+
+/* Append B exact pairs (device genomes [B][k_max], device fitness [B] from
+ * tto_evaluate_batch) to the replay ring; non-finite fitness is kept without a
+ * target and skipped by the loss.  Asynchronous. */
+int tto_surrogate_add(tto_surrogate* s, const int32_t* topo, int32_t B, const float* fitness,
+                      void* stream);
+
+/* Run `steps` training steps (minibatch forward, backward, Adam).  If loss is
+ * not NULL, synchronises the stream and stores the mean squared error of the
+ * last minibatch before its update.  Errors: TTO_E_ARG if the ring is empty. */
+int tto_surrogate_train(tto_surrogate* s, int32_t steps, float* loss, void* stream);
+
+/* Loss and gradient without an update on B exact pairs (device genomes
+ * [B][k_max], device fitness [B]; non-finite fitness is skipped): features,
+ * forward, standardised targets as in training, backward.  Writes the mean
+ * squared error to *loss and the packed gradient (host float [n_params]) to
+ * grad.  Synchronises the stream. */
+int tto_surrogate_grad(tto_surrogate* s, const int32_t* topo, int32_t B, const float* fitness,
+                       float* loss, float* grad, void* stream);
+
+/* One surrogate-screened MapElites iteration: propose n_propose candidates
+ * (as tto_mapelites_propose), score them, evaluate exactly the n_exact of
+ * lowest predicted score (ties by proposal index; while the replay ring is
+ * empty, the first n_exact proposals that do not island the grid), insert them
+ * into the archive, append them to the replay ring and run train_steps
+ * training steps.  topo_out / fitness_out / score_out (device, optional,
+ * [n_exact]) receive the evaluated genomes, their exact fitness and their
+ * predicted score.  Asynchronous. */
+int tto_mapelites_step_screened(tto_archive* a, tto_surrogate* s, uint64_t seed, uint64_t iteration,
+                                int32_t n_propose, int32_t n_exact, const tto_mut_params* mp,
+                                const tto_eval_opts* opts, int32_t train_steps, int32_t* topo_out,
+                                float* fitness_out, float* score_out, void* stream);
+
 /* Thread-local message of the last failing call ("" if none). */
 const char* tto_last_error(void);
 

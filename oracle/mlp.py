@@ -3,7 +3,8 @@
 The surrogate screens mutated proposals before exact N-1 evaluation.  It is not
 part of the paper; its definition here follows the workload description: an MLP
 with three hidden layers of width H (ReLU), trained with mean squared error and
-Adam (Kingma & Ba, 2015) to predict log1p(-fitness) of a topology.
+Adam (Kingma & Ba, 2015) to predict log1p(-fitness) of a topology, standardised
+by the mean and deviation of the targets it has seen (``target_stats``).
 
 Input (dimension 8 S + R): for every station s, eight values, non-zero only when
 the genome splits s --
@@ -132,3 +133,16 @@ def adam_step(P, G, state, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
 def target(fitness):
     """log1p(-fitness) of a finite (non-positive) fitness."""
     return np.log1p(-np.asarray(fitness, dtype=np.float64))
+
+
+def target_stats(t):
+    """Mean and population standard deviation of the finite targets that the
+    network's training targets are standardised with, (t - mean) / deviation:
+    (0, 1) when there are none, deviation 1 when they are all equal."""
+    t = np.asarray(t, dtype=np.float64)
+    t = t[np.isfinite(t)]
+    if t.size == 0:
+        return 0.0, 1.0
+    mean = float(np.sum(t) / t.size)
+    sd = float(np.sqrt(np.sum((t - mean) ** 2) / t.size))
+    return mean, (sd if sd > 0.0 else 1.0)

@@ -161,6 +161,87 @@ class Archive:
         _lib.tto_mapelites_step(self._h, seed, iteration, B, mutation, o, topo_out, fitness_out,
                                 _stream(stream))
 
+    def step_screened(self, surrogate, seed, iteration, n_propose, n_exact,
+                      mutation=DEFAULT_MUTATION, precision=PREC_FP32, fitness_kind=FIT_WORKLOAD,
+                      train_steps=1, topo_out=None, fitness_out=None, score_out=None, stream=None):
+        """One surrogate-screened iteration: propose n_propose, evaluate the
+        n_exact best-scored exactly, insert, learn from them."""
+        o = _lib.EvalOpts(precision, fitness_kind, self.d_split, self.d_moved)
+        _lib.tto_mapelites_step_screened(self._h, surrogate.handle, seed, iteration, n_propose,
+                                         n_exact, mutation, o, train_steps, topo_out, fitness_out,
+                                         score_out, _stream(stream))
+
+
+class Surrogate:
+    """Learned screen of MapElites proposals on one grid: an MLP (three
+    hidden ReLU layers) predicting log1p(-fitness) from split-station values
+    and post-split loadings, trained online on exact pairs."""
+
+    def __init__(self, grid: Grid, hidden=512, n_load=256, replay=262144, minibatch=8192,
+                 lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, seed=0):
+        _torch()
+        self.grid = grid
+        self.hidden = hidden
+        self.n_load = n_load
+        self._h = _lib.tto_surrogate_create(grid.handle, hidden, n_load, replay, minibatch, lr,
+                                            beta1, beta2, eps, seed)
+        info = _lib.tto_surrogate_info(self._h, n_load)
+        self.n_params = info["n_params"]
+        self.input_dim = info["input_dim"]
+        self.rows = info["rows"]
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None:
+            _lib.tto_surrogate_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def replay_fill(self):
+        return _lib.tto_surrogate_info(self._h, self.n_load)["replay_fill"]
+
+    def target_stats(self):
+        """(mean, deviation) that standardise the training targets."""
+        i = _lib.tto_surrogate_info(self._h, self.n_load)
+        return i["target_mean"], i["target_std"]
+
+    def params(self, set_values=None):
+        """Packed FP32 parameters W1, b1, W2, b2, W3, b3, w4, b4 (numpy)."""
+        return _lib.tto_surrogate_params(self._h, self.n_params, set_values)
+
+    def score(self, topo, stream=None):
+        torch = _torch()
+        topo = topo.contiguous()
+        out = torch.empty(int(topo.shape[0]), dtype=torch.float32, device=topo.device)
+        _lib.tto_surrogate_score(self._h, topo, int(topo.shape[0]), out, _stream(stream))
+        return out
+
+    def features(self, B):
+        """(station per slot, eight values per slot, loadings, valid) of the
+        last processed batch, as numpy arrays."""
+        return _lib.tto_surrogate_features(self._h, B, self.grid.k_max, self.n_load)
+
+    def add(self, topo, fitness, stream=None):
+        _lib.tto_surrogate_add(self._h, topo.contiguous(), int(topo.shape[0]), fitness.contiguous(),
+                               _stream(stream))
+
+    def train(self, steps=1, want_loss=True, stream=None):
+        return _lib.tto_surrogate_train(self._h, steps, want_loss, _stream(stream))
+
+    def grad(self, topo, fitness, stream=None):
+        """(loss, packed gradient) of the mean squared error on one batch of
+        exact pairs (targets standardised as in training)."""
+        return _lib.tto_surrogate_grad(self._h, topo.contiguous(), int(topo.shape[0]),
+                                       fitness.contiguous(), self.n_params, _stream(stream))
+
 
 def evaluate_multi(jobs, precision=PREC_FP32, fitness_kind=FIT_WORKLOAD, d_split=8, d_moved=8,
                    mode=_lib.MULTI_GRAPH, stream=None):

@@ -63,6 +63,12 @@ class MutParams(C.Structure):
                 ("p_identity", C.c_double), ("n_mut_mean", C.c_double)]
 
 
+class SurrogateCfg(C.Structure):
+    _fields_ = [("hidden", C.c_int32), ("n_load", C.c_int32), ("replay", C.c_int32),
+                ("minibatch", C.c_int32), ("lr", C.c_double), ("beta1", C.c_double),
+                ("beta2", C.c_double), ("eps", C.c_double), ("seed", C.c_uint64)]
+
+
 _lib = None
 
 _SIGS = {
@@ -93,6 +99,18 @@ _SIGS = {
                             C.POINTER(EvalOpts), _vp, _vp, _vp], C.c_int),
     "tto_philox_blocks": ([C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_int32, _vp, _vp],
                           C.c_int),
+    "tto_surrogate_create": ([_vp, C.POINTER(SurrogateCfg), C.POINTER(_vp)], C.c_int),
+    "tto_surrogate_destroy": ([_vp], C.c_int),
+    "tto_surrogate_info": ([_vp, C.POINTER(C.c_int64), _i32p, _i32p, _vp, _vp], C.c_int),
+    "tto_surrogate_params": ([_vp, _vp, _vp], C.c_int),
+    "tto_surrogate_score": ([_vp, _vp, C.c_int32, _vp, _vp], C.c_int),
+    "tto_surrogate_features": ([_vp, C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
+    "tto_surrogate_add": ([_vp, _vp, C.c_int32, _vp, _vp], C.c_int),
+    "tto_surrogate_train": ([_vp, C.c_int32, C.POINTER(C.c_float), _vp], C.c_int),
+    "tto_surrogate_grad": ([_vp, _vp, C.c_int32, _vp, C.POINTER(C.c_float), _vp, _vp], C.c_int),
+    "tto_mapelites_step_screened": ([_vp, _vp, C.c_uint64, C.c_uint64, C.c_int32, C.c_int32,
+                                     C.POINTER(MutParams), C.POINTER(EvalOpts), C.c_int32, _vp, _vp,
+                                     _vp, _vp], C.c_int),
     "tto_last_error": ([], C.c_char_p),
 }
 
@@ -333,6 +351,84 @@ def tto_mapelites_step(a, seed, iteration, B, mut, opts, topo_out, fitness_out, 
 def tto_philox_blocks(seed, iteration, cand, block, n, out, stream):
     return check(lib().tto_philox_blocks(int(seed), int(iteration), int(cand), int(block), int(n),
                                          _dp(out), _vp(stream)))
+
+
+def tto_surrogate_create(grid_h, hidden, n_load, replay, minibatch, lr, beta1, beta2, eps, seed):
+    cfg = SurrogateCfg(int(hidden), int(n_load), int(replay), int(minibatch), float(lr), float(beta1),
+                       float(beta2), float(eps), int(seed))
+    h = _vp()
+    check(lib().tto_surrogate_create(grid_h, C.byref(cfg), C.byref(h)))
+    return h
+
+
+def tto_surrogate_destroy(h):
+    return check(lib().tto_surrogate_destroy(h))
+
+
+def tto_surrogate_info(h, n_load):
+    n = C.c_int64()
+    d = C.c_int32()
+    fill = C.c_int32()
+    rows = np.zeros(n_load, dtype=np.int32)
+    stats = np.zeros(2, dtype=np.float32)
+    check(lib().tto_surrogate_info(h, C.byref(n), C.byref(d), C.byref(fill), rows.ctypes.data,
+                                   stats.ctypes.data))
+    return dict(n_params=n.value, input_dim=d.value, replay_fill=fill.value, rows=rows,
+                target_mean=float(stats[0]), target_std=float(stats[1]))
+
+
+def tto_surrogate_params(h, n_params, set_values=None):
+    """Returns the packed FP32 parameters (after setting them, if given)."""
+    out = np.zeros(n_params, dtype=np.float32)
+    src = None
+    if set_values is not None:
+        src = np.ascontiguousarray(set_values, dtype=np.float32)
+        if src.size != n_params:
+            raise TTOError(TTO_E_ARG, f"expected {n_params} parameters, got {src.size}")
+    check(lib().tto_surrogate_params(h, out.ctypes.data, None if src is None else src.ctypes.data))
+    return out
+
+
+def tto_surrogate_score(h, topo, B, score, stream):
+    return check(lib().tto_surrogate_score(h, _dp(topo), int(B), _dp(score), _vp(stream)))
+
+
+def tto_surrogate_features(h, B, k_max, n_load):
+    si = np.zeros((B, k_max), dtype=np.int32)
+    sf = np.zeros((B, k_max, 8), dtype=np.float32)
+    xd = np.zeros((B, n_load), dtype=np.float32)
+    valid = np.zeros(B, dtype=np.int32)
+    check(lib().tto_surrogate_features(h, int(B), si.ctypes.data, sf.ctypes.data, xd.ctypes.data,
+                                       valid.ctypes.data))
+    return si, sf, xd, valid
+
+
+def tto_surrogate_add(h, topo, B, fitness, stream):
+    return check(lib().tto_surrogate_add(h, _dp(topo), int(B), _dp(fitness), _vp(stream)))
+
+
+def tto_surrogate_train(h, steps, want_loss, stream):
+    loss = C.c_float()
+    check(lib().tto_surrogate_train(h, int(steps), C.byref(loss) if want_loss else None,
+                                    _vp(stream)))
+    return loss.value if want_loss else None
+
+
+def tto_surrogate_grad(h, topo, B, fitness, n_params, stream):
+    loss = C.c_float()
+    grad = np.zeros(n_params, dtype=np.float32)
+    check(lib().tto_surrogate_grad(h, _dp(topo), int(B), _dp(fitness), C.byref(loss),
+                                   grad.ctypes.data, _vp(stream)))
+    return loss.value, grad
+
+
+def tto_mapelites_step_screened(a, s, seed, iteration, n_propose, n_exact, mut, opts, train_steps,
+                                topo_out, fitness_out, score_out, stream):
+    m = _mut(mut)
+    return check(lib().tto_mapelites_step_screened(a, s, int(seed), int(iteration), int(n_propose),
+                                                   int(n_exact), C.byref(m), C.byref(opts),
+                                                   int(train_steps), _dp(topo_out), _dp(fitness_out),
+                                                   _dp(score_out), _vp(stream)))
 
 
 def tto_last_error():

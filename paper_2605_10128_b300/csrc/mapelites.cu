@@ -13,6 +13,7 @@
 #include <math.h>
 #include <string.h>
 
+#include "philox.cuh"
 #include "sweep.cuh"
 #include "tto_internal.h"
 
@@ -20,24 +21,7 @@ namespace tto {
 
 namespace {
 
-constexpr uint32_t kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u;
-constexpr uint32_t kW0 = 0x9E3779B9u, kW1 = 0xBB67AE85u;
 enum { kAdd = 0, kRemove = 1, kChange = 2, kIdentity = 3 };
-
-__host__ __device__ inline uint4 philox4x32_10(uint4 c, uint2 k) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    if (r) {
-      k.x += kW0;
-      k.y += kW1;
-    }
-    const uint64_t p0 = (uint64_t)kM0 * c.x;
-    const uint64_t p1 = (uint64_t)kM1 * c.z;
-    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k.x, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k.y,
-                   (uint32_t)p0);
-  }
-  return c;
-}
 
 struct Words {
   uint2 key;
@@ -277,6 +261,8 @@ int check_mut(const tto_mut_params* mp) {
   return TTO_OK;
 }
 
+}  // namespace
+
 int propose_impl(tto_archive* ar, uint64_t seed, uint64_t it, int B, const tto_mut_params* mp,
                  int32_t* out, cudaStream_t s) {
   int rc = check_mut(mp);
@@ -318,8 +304,6 @@ int insert_impl(tto_archive* ar, const int32_t* topo, int B, const float* fit, c
   TTO_CUDA_TRY(cudaGetLastError());
   return TTO_OK;
 }
-
-}  // namespace
 
 }  // namespace tto
 

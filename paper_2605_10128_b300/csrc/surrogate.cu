@@ -1,0 +1,1227 @@
+// Learned surrogate screen for MapElites proposals (the paper has no
+// counterpart; the network, its inputs and its online training are this
+// library's own).
+//
+// An MLP with three hidden ReLU layers predicts log1p(-fitness) of a topology
+// from (a) eight values of every split station and (b) the post-split N-0
+// loading |f'_l| / fbar_l at timestep 0 of the R branches that are most loaded
+// in the unsplit grid.  The screened MapElites step proposes many more
+// candidates than it evaluates, scores them all, evaluates exactly only the
+// best-scored ones, and trains the network online (mean squared error, Adam)
+// on the exact pairs it has produced, kept in a replay ring.  The network
+// learns the targets standardised by the mean and standard deviation of the
+// ring's targets (recomputed after every append): the fitness of most splits of
+// a large grid differs by a fraction of a percent, which an unscaled target
+// would leave below the training noise.  Scores are returned unscaled.
+//
+// Numerics: parameters and Adam moments are FP32; every product rounds both
+// operands to BF16 and accumulates in FP32 (mma.sync m16n8k16 for the dense
+// products).  The station block of the input holds at most k_max non-zero
+// 8-value slices per genome, so the first layer adds those slices of W1
+// directly instead of multiplying a mostly-zero matrix, and its gradient is a
+// per-station segmented sum.  Every reduction runs in a fixed order (no
+// floating-point atomics), so results are reproducible call for call.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "philox.cuh"
+#include "sweep.cuh"
+#include "tto_internal.h"
+
+struct tto_surrogate {
+  tto_grid* g = nullptr;
+  int H = 0, R = 0, S = 0, D = 0, k = 0;
+  int cap = 0, mb = 0;
+  double lr = 1e-3, beta1 = 0.9, beta2 = 0.999, eps = 1e-8;
+  uint64_t seed = 0;
+  long long step = 0;  // Adam steps taken
+  size_t n_params = 0, oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, oW3 = 0, ob3 = 0, ow4 = 0, ob4 = 0;
+  float* P = nullptr;     // packed parameters (FP32)
+  float* G = nullptr;     // packed gradient
+  float* Am = nullptr;    // Adam first moment
+  float* Av = nullptr;    // Adam second moment
+  float* W1sT = nullptr;  // [8S][H] station block of W1, transposed (refreshed after every update)
+  int* rows = nullptr;    // [R] branch ids of the loading features
+  double* row_lim = nullptr;  // [R] their thermal limits
+  double* Nsr = nullptr;  // [n_sw][R] N[rows[r]][movable branch] (the movable columns at those rows)
+  double psum = 1.0;      // sum |p(t=0)|
+  // per-batch buffers (capacity bcap rows)
+  int bcap = 0;
+  int* SI = nullptr;      // [bcap][k] station of each genome slot, -1 = empty
+  float* SF = nullptr;    // [bcap][k][8] that station's eight values
+  float* XD = nullptr;    // [bcap][R] loadings
+  int* valid = nullptr;   // [bcap] 0 = the split islands the grid (or the genome is invalid)
+  float *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *Y = nullptr;
+  float *dH1 = nullptr, *dH2 = nullptr, *dH3 = nullptr, *dY = nullptr, *T = nullptr;
+  int32_t* mb_topo = nullptr;  // [bcap][k] genomes of a training minibatch
+  float* loss = nullptr;       // [2]: sum of squared errors, rows counted
+  float* stats = nullptr;      // [3]: mean, standard deviation, 1 / deviation of the ring's targets
+  // replay ring
+  int rep_n = 0, rep_head = 0;
+  int32_t* rep_genome = nullptr;  // [cap][k]
+  float* rep_xd = nullptr;        // [cap][R]
+  float* rep_t = nullptr;         // [cap] log1p(-fitness), NaN = no target
+  // screening
+  int pcap = 0;
+  int32_t* prop = nullptr;              // [pcap][k] proposals
+  unsigned long long* keys = nullptr;   // [keys_n] (score, index) sort keys
+  int keys_n = 0;
+};
+
+namespace tto {
+namespace {
+
+constexpr int kBM = 64, kBN = 64, kBK = 32, kPadK = kBK + 8;
+constexpr int kMaxHidden = 1024;
+constexpr int kSortChunk = 2048;  // keys sorted per CTA in shared memory
+
+__device__ __forceinline__ float bf(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// ------------------------------------------------------------------ GEMM
+// C[M][N] (ldc) = opA(A) opB(B) + bias[n], then zeroed where mask[m][n] <= 0
+// (mask has C's layout) and/or clamped at 0 (relu).
+// opA(m, k) = TA ? A[k lda + m] : A[m lda + k];
+// opB(k, n) = TB ? B[n ldb + k] : B[k ldb + n].
+// 64x64 output tile per 128-thread CTA (2x2 warps of 32x32), K in steps of 32;
+// operands are rounded to BF16 when staged in shared memory.
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(128) gemm_bf16_kernel(int M, int N, int K, const float* __restrict__ A,
+                                                        int lda, const float* __restrict__ B, int ldb,
+                                                        float* C, int ldc, const float* __restrict__ bias,
+                                                        const float* __restrict__ mask, int relu) {
+  __shared__ __align__(16) __nv_bfloat16 As[kBM][kPadK];
+  __shared__ __align__(16) __nv_bfloat16 Bs[kBN][kPadK];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, q = lane & 3;
+  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  float d[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) d[i][j][r] = 0.f;
+  for (int k0 = 0; k0 < K; k0 += kBK) {
+    // consecutive threads read consecutive global addresses in both layouts
+    for (int e = tid; e < kBM * kBK; e += 128) {
+      const int r = TA ? e % kBM : e / kBK, c = TA ? e / kBM : e % kBK;
+      const int m = m0 + r, kk = k0 + c;
+      float v = 0.f;
+      if (m < M && kk < K) v = TA ? A[(size_t)kk * lda + m] : A[(size_t)m * lda + kk];
+      As[r][c] = __float2bfloat16_rn(v);
+    }
+    for (int e = tid; e < kBN * kBK; e += 128) {
+      const int r = TB ? e / kBK : e % kBN, c = TB ? e % kBK : e / kBN;
+      const int n = n0 + r, kk = k0 + c;
+      float v = 0.f;
+      if (n < N && kk < K) v = TB ? B[(size_t)n * ldb + kk] : B[(size_t)kk * ldb + n];
+      Bs[r][c] = __float2bfloat16_rn(v);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < kBK; ks += 16) {
+      uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm + 16 * i + g;
+        af[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][ks + 2 * q]);
+        af[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + 2 * q]);
+        af[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][ks + 2 * q + 8]);
+        af[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + 2 * q + 8]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int n = wn + 8 * j + g;
+        bfr[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[n][ks + 2 * q]);
+        bfr[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[n][ks + 2 * q + 8]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          asm volatile(
+              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+              "{%8,%9}, {%0,%1,%2,%3};"
+              : "+f"(d[i][j][0]), "+f"(d[i][j][1]), "+f"(d[i][j][2]), "+f"(d[i][j][3])
+              : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bfr[j][0]),
+                "r"(bfr[j][1]));
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int m = m0 + wm + 16 * i + g + (r >= 2 ? 8 : 0);
+        const int n = n0 + wn + 8 * j + 2 * q + (r & 1);
+        if (m >= M || n >= N) continue;
+        float v = d[i][j][r];
+        if (bias) v += bias[n];
+        if (mask && !(mask[(size_t)m * ldc + n] > 0.f)) v = 0.f;
+        if (relu) v = fmaxf(v, 0.f);
+        C[(size_t)m * ldc + n] = v;
+      }
+}
+
+template <bool TA, bool TB>
+int gemm(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
+         const float* bias, const float* mask, bool relu, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return TTO_OK;
+  const dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM);
+  if (grid.y > 65535) return set_error(TTO_E_ARG, "surrogate batch too large for one product");
+  gemm_bf16_kernel<TA, TB><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, mask, relu ? 1 : 0);
+  TTO_CUDA_TRY(cudaGetLastError());
+  return TTO_OK;
+}
+
+// ------------------------------------------------------------------ features
+struct FeatArgs {
+  const int32_t* topo;
+  int k, A, R, E;
+  const int* act_st;
+  const uint32_t* act_mask;
+  const int* station_bus;
+  const int* asset_off;
+  const int* asset_br;
+  const int* from;
+  const double* b;
+  const double* p;    // [T][n_bus]; timestep 0 is used
+  const double* f0;   // [T][E]
+  const double* Nsw;  // [n_sw][E]
+  const int* swcol;   // [E]
+  const double* Nsr;  // [n_sw][R]
+  const int* rows;
+  const double* row_lim;
+  double psum;
+  int with_loads;     // 0: station values only (the loadings come from the replay ring)
+  int* SI;
+  float* SF;
+  float* XD;
+  int* valid;
+};
+
+// One CTA per genome.  Decodes the genome as the evaluation does (an
+// out-of-range action or a station split twice makes it invalid), writes the
+// station values, and with_loads solves the split at timestep 0 --
+// K = S^T N D S in FP64, LDL^T with the same islanding pivot test,
+// psi = K^-1 (p_M - S^T f0) -- for f'_r = f0_r + sum_j W_rj psi_j on the R
+// loading rows.
+__global__ void __launch_bounds__(128) features_kernel(FeatArgs a) {
+  const int bi = blockIdx.x, tid = threadIdx.x;
+  __shared__ int s_k, s_isl;
+  __shared__ int s_slot[TTO_MAX_K + 1];
+  __shared__ int s_e[kMaxMoved], s_sw[kMaxMoved];
+  __shared__ double s_sign[kMaxMoved], s_coef[kMaxMoved];
+  __shared__ int s_injbus[TTO_MAX_K];
+  __shared__ double s_K[TTO_MAX_K][TTO_MAX_K], s_rhs[TTO_MAX_K], s_psi[TTO_MAX_K], s_sb[TTO_MAX_K];
+  if (tid == 0) {
+    int k = 0, ne = 0, bad = 0;
+    int seen[TTO_MAX_K];
+    s_slot[0] = 0;
+    for (int j = 0; j < a.k; ++j) {
+      a.SI[(size_t)bi * a.k + j] = -1;
+      float* sf = a.SF + ((size_t)bi * a.k + j) * 8;
+      for (int c = 0; c < 8; ++c) sf[c] = 0.f;
+    }
+    for (int j = 0; j < a.k; ++j) {
+      const int act = a.topo[(size_t)bi * a.k + j];
+      if (act < 0) continue;
+      if (act >= a.A) {
+        bad = 1;
+        break;
+      }
+      const int st = a.act_st[act];
+      for (int q = 0; q < k; ++q)
+        if (seen[q] == st) bad = 1;
+      if (bad) break;
+      seen[k] = st;
+      const uint32_t mask = a.act_mask[act];
+      const int bus = a.station_bus[st], a0 = a.asset_off[st], m = a.asset_off[st + 1] - a0;
+      const int nb = __popc(mask);
+      double b_all = 0.0, b_b = 0.0, pb = 0.0;
+      int br = 0, br_b = 0;
+      s_injbus[k] = -1;
+      for (int i = 0; i < m; ++i) {
+        const int e = a.asset_br[a0 + i];
+        const bool onb = (mask >> i) & 1u;
+        if (e < 0) {
+          if (onb) {
+            pb += a.p[bus];
+            s_injbus[k] = bus;
+          }
+          continue;
+        }
+        ++br;
+        b_all += a.b[e];
+        if (!onb) continue;
+        ++br_b;
+        b_b += a.b[e];
+        const double sg = (a.from[e] == bus) ? 1.0 : -1.0;
+        s_e[ne] = e;
+        s_sw[ne] = a.swcol[e];
+        s_sign[ne] = sg;
+        s_coef[ne] = sg * a.b[e];
+        ++ne;
+      }
+      a.SI[(size_t)bi * a.k + j] = st;
+      float* sf = a.SF + ((size_t)bi * a.k + j) * 8;
+      sf[0] = 1.f;
+      sf[1] = (float)((double)min(nb, m - nb) / m);
+      sf[2] = (float)(b_b / b_all);
+      sf[3] = (float)(pb / a.psum);
+      sf[4] = (float)((double)br_b / br);
+      sf[5] = (float)((double)nb / m);
+      ++k;
+      s_slot[k] = ne;
+    }
+    if (bad)
+      for (int j = 0; j < a.k; ++j) a.SI[(size_t)bi * a.k + j] = -1;
+    s_k = bad ? 0 : k;
+    s_isl = bad;
+  }
+  __syncthreads();
+  if (!a.with_loads) {
+    if (tid == 0) a.valid[bi] = s_isl ? 0 : 1;
+    return;
+  }
+  const int k = s_k;
+  if (tid < k * k) {
+    const int i = tid / k, j = tid % k;
+    double acc = 0.0;
+    for (int q = s_slot[i]; q < s_slot[i + 1]; ++q) {
+      double w = 0.0;
+      for (int r = s_slot[j]; r < s_slot[j + 1]; ++r) w += s_coef[r] * a.Nsw[(size_t)s_sw[r] * a.E + s_e[q]];
+      acc += s_sign[q] * w;
+    }
+    s_K[i][j] = acc;
+  }
+  if (tid < k) {
+    double st = 0.0, sb = 0.0;
+    for (int q = s_slot[tid]; q < s_slot[tid + 1]; ++q) {
+      st += s_sign[q] * a.f0[s_e[q]];
+      sb += a.b[s_e[q]];
+    }
+    s_rhs[tid] = (s_injbus[tid] >= 0 ? a.p[s_injbus[tid]] : 0.0) - st;
+    s_sb[tid] = sb;
+  }
+  __syncthreads();
+  if (tid == 0 && k > 0 && !s_isl) {
+    double L[TTO_MAX_K][TTO_MAX_K], Dg[TTO_MAX_K], x[TTO_MAX_K];
+    int isl = 0;
+    for (int j = 0; j < k; ++j) {
+      double dj = s_K[j][j];
+      for (int q = 0; q < j; ++q) dj -= L[j][q] * L[j][q] * Dg[q];
+      Dg[j] = dj;
+      if (!(dj > kIslandTol * s_sb[j])) {
+        isl = 1;
+        break;
+      }
+      for (int i = j + 1; i < k; ++i) {
+        double v = s_K[i][j];
+        for (int q = 0; q < j; ++q) v -= L[i][q] * L[j][q] * Dg[q];
+        L[i][j] = v / dj;
+      }
+    }
+    if (!isl) {
+      for (int i = 0; i < k; ++i) {
+        double v = s_rhs[i];
+        for (int q = 0; q < i; ++q) v -= L[i][q] * x[q];
+        x[i] = v;
+      }
+      for (int i = 0; i < k; ++i) x[i] /= Dg[i];
+      for (int i = k - 1; i >= 0; --i) {
+        double v = x[i];
+        for (int q = i + 1; q < k; ++q) v -= L[q][i] * x[q];
+        x[i] = v;
+      }
+      for (int i = 0; i < k; ++i) s_psi[i] = x[i];
+    }
+    s_isl = isl;
+  }
+  __syncthreads();
+  const bool dead = s_isl != 0;
+  if (tid == 0) a.valid[bi] = dead ? 0 : 1;
+  for (int r = tid; r < a.R; r += blockDim.x) {
+    float v = 0.f;
+    if (!dead) {
+      double f = a.f0[a.rows[r]];
+      for (int j = 0; j < k; ++j) {
+        double w = 0.0;
+        for (int q = s_slot[j]; q < s_slot[j + 1]; ++q) w += s_coef[q] * a.Nsr[(size_t)s_sw[q] * a.R + r];
+        f += w * s_psi[j];
+      }
+      v = (float)(fabs(f) / a.row_lim[r]);
+    }
+    a.XD[(size_t)bi * a.R + r] = v;
+  }
+}
+
+// Nsr[sw][r] = Nsw[sw][rows[r]]
+__global__ void gather_rows_kernel(int n_sw, int E, int R, const double* Nsw, const int* rows, double* Nsr) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)n_sw * R) return;
+  const size_t sw = i / R;
+  Nsr[i] = Nsw[sw * E + rows[i % R]];
+}
+
+// out[c][h] = W1[h][c] for the station columns c < C (32x32 tiles).
+__global__ void transpose_station_kernel(int H, int D, int C, const float* W1, float* out) {
+  __shared__ float t[32][33];
+  const int c0 = blockIdx.x * 32, h0 = blockIdx.y * 32;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int h = h0 + y, c = c0 + threadIdx.x;
+    t[y][threadIdx.x] = (h < H && c < C) ? W1[(size_t)h * D + c] : 0.f;
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int c = c0 + y, h = h0 + threadIdx.x;
+    if (c < C && h < H) out[(size_t)c * H + h] = t[threadIdx.x][y];
+  }
+}
+
+// ------------------------------------------------------------------ layers
+// H1[row][h] = relu(Z1[row][h] + sum over split stations s of the row, c < 8,
+// of W1[h][8 s + c] f_c), in place (Z1 holds the dense part and the bias).
+__global__ void station_terms_relu_kernel(int M, int H, int k, const int* SI, const float* SF,
+                                          const float* W1sT, float* Z) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)M * H) return;
+  const int row = (int)(i / H), h = (int)(i % H);
+  float v = Z[i];
+  for (int j = 0; j < k; ++j) {
+    const int st = SI[(size_t)row * k + j];
+    if (st < 0) continue;
+    const float* f = SF + ((size_t)row * k + j) * 8;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) v += bf(W1sT[(size_t)(8 * st + c) * H + h]) * bf(f[c]);
+  }
+  Z[i] = fmaxf(v, 0.f);
+}
+
+// y = w4 . h3 + b4 (one warp per row); with stats, mean + deviation * y and
+// +inf where valid is 0.
+__global__ void output_kernel(int M, int H, const float* H3, const float* w4, const float* b4, const int* valid,
+                              const float* stats, float* Y) {
+  const int row = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (row >= M) return;
+  float s = 0.f;
+  for (int h = lane; h < H; h += 32) s += bf(H3[(size_t)row * H + h]) * bf(w4[h]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    const float y = s + b4[0];
+    Y[row] = (valid && !valid[row]) ? INFINITY : (stats ? fmaf(stats[1], y, stats[0]) : y);
+  }
+}
+
+// Y = 0 where valid, +inf elsewhere (ranking before the network has data).
+__global__ void valid_only_kernel(int M, const int* valid, float* Y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < M) Y[i] = valid[i] ? 0.f : INFINITY;
+}
+
+// loss[0] = sum (y - t)^2 and loss[1] = rows, over the rows with a finite
+// target; dY = 2 (y - t) / loss[1] there, 0 elsewhere.  One CTA, fixed order.
+__global__ void __launch_bounds__(1024) loss_kernel(int M, const float* Y, const float* T, float* dY,
+                                                    float* loss) {
+  __shared__ float s_sum[32], s_cnt[32];
+  __shared__ float s_n;
+  float sum = 0.f, cnt = 0.f;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    const float t = T[i], y = Y[i];
+    if (isfinite(t) && isfinite(y)) {
+      const float r = y - t;
+      sum += r * r;
+      cnt += 1.f;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_sum[threadIdx.x >> 5] = sum;
+    s_cnt[threadIdx.x >> 5] = cnt;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float a = 0.f, c = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += s_sum[w];
+      c += s_cnt[w];
+    }
+    loss[0] = a;
+    loss[1] = c;
+    s_n = c;
+  }
+  __syncthreads();
+  const float n = fmaxf(s_n, 1.f);
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    const float t = T[i], y = Y[i];
+    dY[i] = (isfinite(t) && isfinite(y)) ? 2.f * (y - t) / n : 0.f;
+  }
+}
+
+// dH3[row][h] = dY[row] w4[h] where h3 > 0.
+__global__ void out_back_kernel(int M, int H, const float* dY, const float* w4, const float* H3, float* dH3) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)M * H) return;
+  const int row = (int)(i / H), h = (int)(i % H);
+  dH3[i] = H3[i] > 0.f ? dY[row] * bf(w4[h]) : 0.f;
+}
+
+// out[n] = sum_m A[m][n] (w ? w[m] : 1), fixed order: 32 columns x 32 row
+// groups per CTA, then the groups summed in order.
+__global__ void __launch_bounds__(1024) colsum_kernel(int M, int N, const float* A, const float* w, float* out) {
+  __shared__ float s[32][33];
+  const int n = blockIdx.x * 32 + threadIdx.x;
+  float acc = 0.f;
+  if (n < N)
+    for (int m = threadIdx.y; m < M; m += 32) acc += A[(size_t)m * N + n] * (w ? w[m] : 1.f);
+  s[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && n < N) {
+    float t = 0.f;
+    for (int y = 0; y < 32; ++y) t += s[y][threadIdx.x];
+    out[n] = t;
+  }
+}
+
+// Gradient of the station block of W1: one CTA per station s,
+// G1[h][8 s + c] = sum over genome slots holding s (in row order) of
+// dH1[row][h] f_c.  The slots of s are compacted in order, 256 at a time.
+__global__ void __launch_bounds__(256) station_grad_kernel(int M, int H, int D, int k, const int* SI,
+                                                           const float* SF, const float* dH1, float* G1) {
+  const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ int s_row[256];
+  __shared__ float s_f[256][8];
+  __shared__ int s_wcnt[8];
+  float acc[kMaxHidden / 256][8];
+#pragma unroll
+  for (int u = 0; u < kMaxHidden / 256; ++u)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[u][c] = 0.f;
+  const int n_ent = M * k;
+  for (int base = 0; base < n_ent; base += 256) {
+    const int e = base + tid;
+    const bool hit = e < n_ent && SI[e] == s;
+    const unsigned bal = __ballot_sync(0xffffffffu, hit);
+    if (lane == 0) s_wcnt[warp] = __popc(bal);
+    __syncthreads();
+    int off = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      off += w < warp ? s_wcnt[w] : 0;
+      tot += s_wcnt[w];
+    }
+    if (hit) {
+      const int pos = off + __popc(bal & ((1u << lane) - 1u));
+      s_row[pos] = e / k;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) s_f[pos][c] = bf(SF[(size_t)e * 8 + c]);
+    }
+    __syncthreads();
+    for (int i = 0; i < tot; ++i) {
+      const float* dr = dH1 + (size_t)s_row[i] * H;
+#pragma unroll
+      for (int u = 0; u < kMaxHidden / 256; ++u) {
+        const int h = tid + 256 * u;
+        if (h < H) {
+          const float dv = dr[h];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) acc[u][c] += dv * s_f[i][c];
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < kMaxHidden / 256; ++u) {
+    const int h = tid + 256 * u;
+    if (h < H)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) G1[(size_t)h * D + 8 * s + c] = acc[u][c];
+  }
+}
+
+// Adam with bias correction: c1 = 1 - beta1^t, c2 = 1 - beta2^t.
+__global__ void adam_kernel(size_t n, float* P, const float* G, float* m, float* v, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = G[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// ------------------------------------------------------------------ top-k
+// Sort keys (orderable score bits << 32 | proposal index), ascending: the best
+// predicted scores first, ties by index; NaN scores rank as +inf.
+__device__ __forceinline__ uint32_t orderable(float f) {
+  const uint32_t u = __float_as_uint(f + 0.0f);  // -0 -> +0
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__global__ void keys_kernel(int n, int npad, const float* Y, unsigned long long* keys) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npad) return;
+  keys[i] = i < n ? (((unsigned long long)orderable(isnan(Y[i]) ? INFINITY : Y[i]) << 32) | (uint32_t)i)
+                  : ~0ull;
+}
+
+// One compare-exchange stage (kk, jj) of the bitonic network over the array.
+__global__ void bitonic_global_kernel(int npad, int kk, int jj, unsigned long long* keys) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npad) return;
+  const int p = i ^ jj;
+  if (p <= i) return;
+  const unsigned long long x = keys[i], y = keys[p];
+  if ((x > y) == ((i & kk) == 0)) {
+    keys[i] = y;
+    keys[p] = x;
+  }
+}
+
+// The stages of the bitonic network that stay inside one 2048-key chunk: for
+// kk_from = 0, every stage with kk <= 2048; else the stages jj = 1024 .. 1 of
+// kk = kk_from.  1024 threads, one pair each per stage.
+__global__ void __launch_bounds__(1024) bitonic_shared_kernel(int kk_from, unsigned long long* keys) {
+  __shared__ unsigned long long s[kSortChunk];
+  const int base = blockIdx.x * kSortChunk, t = threadIdx.x;
+  s[t] = keys[base + t];
+  s[t + 1024] = keys[base + t + 1024];
+  __syncthreads();
+  const int kk_lo = kk_from ? kk_from : 2, kk_hi = kk_from ? kk_from : kSortChunk;
+  for (int kk = kk_lo; kk <= kk_hi; kk <<= 1) {
+    for (int jj = min(kk >> 1, kSortChunk >> 1); jj > 0; jj >>= 1) {
+      const int i = 2 * jj * (t / jj) + (t % jj), p = i + jj;
+      const unsigned long long x = s[i], y = s[p];
+      if ((x > y) == (((base + i) & kk) == 0)) {
+        s[i] = y;
+        s[p] = x;
+      }
+      __syncthreads();
+    }
+  }
+  keys[base + t] = s[t];
+  keys[base + t + 1024] = s[t + 1024];
+}
+
+__global__ void gather_topo_kernel(int n, int k, const unsigned long long* keys, const int32_t* src, int32_t* dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const size_t j = (size_t)(keys[i] & 0xffffffffu);
+  for (int c = 0; c < k; ++c) dst[(size_t)i * k + c] = src[j * k + c];
+}
+
+__global__ void gather_score_kernel(int n, const unsigned long long* keys, const float* Y, float* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = Y[keys[i] & 0xffffffffu];
+}
+
+// ------------------------------------------------------------------ replay
+// Target of an exact fitness: log1p(-fitness) (NaN when not finite).
+__device__ __forceinline__ float raw_target(float f) {
+  return isfinite(f) ? log1pf(-f) : __int_as_float(0x7fc00000);
+}
+
+// Standardised target: (t - mean) / deviation.
+__device__ __forceinline__ float scaled_target(float t, const float* stats) { return (t - stats[0]) * stats[2]; }
+
+// stats = mean, population standard deviation and its reciprocal over the
+// finite entries of rt[0 .. n) (FP64, fixed order); (0, 1, 1) when there are
+// none, deviation 1 when they are all equal.
+__global__ void __launch_bounds__(1024) target_stats_kernel(int n, const float* rt, float* stats) {
+  __shared__ double s_a[32], s_b[32];
+  __shared__ double s_mean;
+  double sum = 0.0, cnt = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float t = rt[i];
+    if (isfinite(t)) {
+      sum += t;
+      cnt += 1.0;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_a[threadIdx.x >> 5] = sum;
+    s_b[threadIdx.x >> 5] = cnt;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, c = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += s_a[w];
+      c += s_b[w];
+    }
+    s_mean = c > 0.0 ? a / c : 0.0;
+    s_b[0] = c;
+  }
+  __syncthreads();
+  const double mean = s_mean, count = s_b[0];
+  __syncthreads();
+  double sq = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float t = rt[i];
+    if (isfinite(t)) sq += ((double)t - mean) * ((double)t - mean);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if ((threadIdx.x & 31) == 0) s_a[threadIdx.x >> 5] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += s_a[w];
+    double sd = count > 0.0 ? sqrt(a / count) : 1.0;
+    if (!(sd > 0.0)) sd = 1.0;
+    stats[0] = (float)mean;
+    stats[1] = (float)sd;
+    stats[2] = (float)(1.0 / sd);
+  }
+}
+
+// T[i] = standardised target of fitness fit[i].
+__global__ void targets_kernel(int n, const float* fit, const float* stats, float* T) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) T[i] = scaled_target(raw_target(fit[i]), stats);
+}
+
+// Append n pairs at the ring head: genome i, the loadings of batch row
+// (keys ? the index in keys[i] : i), target log1p(-fitness) or NaN.
+__global__ void replay_append_kernel(int n, int k, int R, int cap, int head, const int32_t* topo,
+                                     const unsigned long long* keys, const float* XD, const float* fit,
+                                     int32_t* rg, float* rx, float* rt) {
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  const size_t slot = (size_t)((head + i) % cap);
+  const size_t src = keys ? (size_t)(keys[i] & 0xffffffffu) : (size_t)i;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) rx[slot * R + r] = XD[src * R + r];
+  if (threadIdx.x < k) rg[slot * k + threadIdx.x] = topo[(size_t)i * k + threadIdx.x];
+  if (threadIdx.x == 0) rt[slot] = raw_target(fit[i]);
+}
+
+// Minibatch row i: ring entry i when the ring holds at most M pairs, else a
+// uniform draw from Philox4x32-10 (key = seed, counter = (i, ~0, step));
+// its target standardised.
+__global__ void sample_kernel(int M, int n_rep, int k, int R, uint2 key, uint32_t st_lo, uint32_t st_hi,
+                              const int32_t* rg, const float* rx, const float* rt, const float* stats,
+                              int32_t* topo, float* XD, float* T) {
+  const int i = blockIdx.x;
+  if (i >= M) return;
+  size_t src = (size_t)i;
+  if (n_rep > M) {
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)i, 0xffffffffu, st_lo, st_hi), key);
+    src = (size_t)(((uint64_t)w.x * (uint32_t)n_rep) >> 32);
+  }
+  for (int r = threadIdx.x; r < R; r += blockDim.x) XD[(size_t)i * R + r] = rx[src * R + r];
+  if (threadIdx.x < k) topo[(size_t)i * k + threadIdx.x] = rg[src * k + threadIdx.x];
+  if (threadIdx.x == 0) T[i] = scaled_target(rt[src], stats);
+}
+
+// ------------------------------------------------------------------ host side
+int alloc_batch(tto_surrogate* s, int B) {
+  if (B <= s->bcap) return TTO_OK;
+  void* old[] = {s->SI, s->SF, s->XD, s->valid, s->H1, s->H2, s->H3, s->Y, s->dH1, s->dH2, s->dH3, s->dY, s->T,
+                 s->mb_topo};
+  for (void* p : old)
+    if (p) cudaFree(p);
+  s->SI = nullptr;
+  s->SF = s->XD = s->H1 = s->H2 = s->H3 = s->Y = s->dH1 = s->dH2 = s->dH3 = s->dY = s->T = nullptr;
+  s->valid = nullptr;
+  s->mb_topo = nullptr;
+  s->bcap = 0;
+  const size_t b = B, H = s->H;
+  TTO_CUDA_TRY(cudaMalloc(&s->SI, b * s->k * sizeof(int)));
+  TTO_CUDA_TRY(cudaMalloc(&s->SF, b * s->k * 8 * sizeof(float)));
+  TTO_CUDA_TRY(cudaMalloc(&s->XD, b * s->R * sizeof(float)));
+  TTO_CUDA_TRY(cudaMalloc(&s->valid, b * sizeof(int)));
+  TTO_CUDA_TRY(cudaMalloc(&s->H1, b * H * sizeof(float)));
+  TTO_CUDA_TRY(cudaMalloc(&s->H2, b * H * sizeof(float)));
+  TTO_CUDA_TRY(cudaMalloc(&s->H3, b * H * sizeof(float)));
+  TTO_CUDA_TRY(cudaMalloc(&s->Y, b * sizeof(float)));
+  TTO_CUDA_TRY(cudaMalloc(&s->dH1, b * H * sizeof(float)));
+  TTO_CUDA_TRY(cudaMalloc(&s->dH2, b * H * sizeof(float)));
+  TTO_CUDA_TRY(cudaMalloc(&s->dH3, b * H * sizeof(float)));
+  TTO_CUDA_TRY(cudaMalloc(&s->dY, b * sizeof(float)));
+  TTO_CUDA_TRY(cudaMalloc(&s->T, b * sizeof(float)));
+  TTO_CUDA_TRY(cudaMalloc(&s->mb_topo, b * s->k * sizeof(int32_t)));
+  s->bcap = B;
+  return TTO_OK;
+}
+
+FeatArgs feat_args(const tto_surrogate* s, const int32_t* topo, int with_loads) {
+  const tto_grid* g = s->g;
+  FeatArgs a;
+  a.topo = topo;
+  a.k = s->k;
+  a.A = g->A;
+  a.R = s->R;
+  a.E = g->E;
+  a.act_st = g->d_act_st;
+  a.act_mask = g->d_act_mask;
+  a.station_bus = g->d_station_bus;
+  a.asset_off = g->d_asset_off;
+  a.asset_br = g->d_asset_br;
+  a.from = g->d_from;
+  a.b = g->d_b;
+  a.p = g->d_p;
+  a.f0 = g->d_f0;
+  a.Nsw = g->d_Nsw;
+  a.swcol = g->d_swcol;
+  a.Nsr = s->Nsr;
+  a.rows = s->rows;
+  a.row_lim = s->row_lim;
+  a.psum = s->psum;
+  a.with_loads = with_loads;
+  a.SI = s->SI;
+  a.SF = s->SF;
+  a.XD = s->XD;
+  a.valid = s->valid;
+  return a;
+}
+
+int features(tto_surrogate* s, const int32_t* topo, int B, int with_loads, cudaStream_t st) {
+  if (B <= 0) return TTO_OK;
+  features_kernel<<<B, 128, 0, st>>>(feat_args(s, topo, with_loads));
+  TTO_CUDA_TRY(cudaGetLastError());
+  return TTO_OK;
+}
+
+int refresh_station_weights(tto_surrogate* s, cudaStream_t st) {
+  const int C = 8 * s->S;
+  const dim3 grid((C + 31) / 32, (s->H + 31) / 32);
+  transpose_station_kernel<<<grid, dim3(32, 8), 0, st>>>(s->H, s->D, C, s->P + s->oW1, s->W1sT);
+  TTO_CUDA_TRY(cudaGetLastError());
+  return TTO_OK;
+}
+
+// Forward pass over the first B rows of the batch buffers (SI, SF, XD).
+int forward(tto_surrogate* s, int B, const int* valid, cudaStream_t st) {
+  const float* P = s->P;
+  const int H = s->H, D = s->D, R = s->R;
+  int rc = gemm<false, true>(B, H, R, s->XD, R, P + s->oW1 + 8 * (size_t)s->S, D, s->H1, H, P + s->ob1, nullptr,
+                             false, st);
+  if (rc) return rc;
+  const size_t n = (size_t)B * H;
+  station_terms_relu_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(B, H, s->k, s->SI, s->SF, s->W1sT, s->H1);
+  TTO_CUDA_TRY(cudaGetLastError());
+  if ((rc = gemm<false, true>(B, H, H, s->H1, H, P + s->oW2, H, s->H2, H, P + s->ob2, nullptr, true, st))) return rc;
+  if ((rc = gemm<false, true>(B, H, H, s->H2, H, P + s->oW3, H, s->H3, H, P + s->ob3, nullptr, true, st))) return rc;
+  output_kernel<<<(unsigned)(((size_t)B * 32 + 255) / 256), 256, 0, st>>>(B, H, s->H3, P + s->ow4, P + s->ob4, valid,
+                                                                         valid ? s->stats : nullptr, s->Y);
+  TTO_CUDA_TRY(cudaGetLastError());
+  return TTO_OK;
+}
+
+// Loss of the first M rows against s->T and the packed gradient into s->G
+// (after a forward pass over the same rows).  Every gradient entry is written.
+int backward(tto_surrogate* s, int M, cudaStream_t st) {
+  const float* P = s->P;
+  float* G = s->G;
+  const int H = s->H, D = s->D, R = s->R;
+  const unsigned nb = (unsigned)(((size_t)M * H + 255) / 256);
+  const unsigned ncs = (unsigned)((H + 31) / 32);
+  const dim3 cs(32, 32);
+  loss_kernel<<<1, 1024, 0, st>>>(M, s->Y, s->T, s->dY, s->loss);
+  colsum_kernel<<<ncs, cs, 0, st>>>(M, H, s->H3, s->dY, G + s->ow4);
+  colsum_kernel<<<1, cs, 0, st>>>(M, 1, s->dY, nullptr, G + s->ob4);
+  out_back_kernel<<<nb, 256, 0, st>>>(M, H, s->dY, P + s->ow4, s->H3, s->dH3);
+  TTO_CUDA_TRY(cudaGetLastError());
+  int rc;
+  if ((rc = gemm<true, false>(H, H, M, s->dH3, H, s->H2, H, G + s->oW3, H, nullptr, nullptr, false, st))) return rc;
+  colsum_kernel<<<ncs, cs, 0, st>>>(M, H, s->dH3, nullptr, G + s->ob3);
+  if ((rc = gemm<false, false>(M, H, H, s->dH3, H, P + s->oW3, H, s->dH2, H, nullptr, s->H2, false, st))) return rc;
+  if ((rc = gemm<true, false>(H, H, M, s->dH2, H, s->H1, H, G + s->oW2, H, nullptr, nullptr, false, st))) return rc;
+  colsum_kernel<<<ncs, cs, 0, st>>>(M, H, s->dH2, nullptr, G + s->ob2);
+  if ((rc = gemm<false, false>(M, H, H, s->dH2, H, P + s->oW2, H, s->dH1, H, nullptr, s->H1, false, st))) return rc;
+  if ((rc = gemm<true, false>(H, R, M, s->dH1, H, s->XD, R, G + s->oW1 + 8 * (size_t)s->S, D, nullptr, nullptr,
+                              false, st)))
+    return rc;
+  colsum_kernel<<<ncs, cs, 0, st>>>(M, H, s->dH1, nullptr, G + s->ob1);
+  station_grad_kernel<<<s->S, 256, 0, st>>>(M, H, D, s->k, s->SI, s->SF, s->dH1, G + s->oW1);
+  TTO_CUDA_TRY(cudaGetLastError());
+  return TTO_OK;
+}
+
+int adam(tto_surrogate* s, cudaStream_t st) {
+  ++s->step;
+  const double c1 = 1.0 - pow(s->beta1, (double)s->step), c2 = 1.0 - pow(s->beta2, (double)s->step);
+  adam_kernel<<<(unsigned)((s->n_params + 255) / 256), 256, 0, st>>>(s->n_params, s->P, s->G, s->Am, s->Av,
+                                                                     (float)s->lr, (float)s->beta1, (float)s->beta2,
+                                                                     (float)s->eps, (float)c1, (float)c2);
+  TTO_CUDA_TRY(cudaGetLastError());
+  return refresh_station_weights(s, st);
+}
+
+int score(tto_surrogate* s, const int32_t* topo, int B, cudaStream_t st) {
+  int rc = alloc_batch(s, B);
+  if (rc) return rc;
+  if ((rc = features(s, topo, B, 1, st))) return rc;
+  return forward(s, B, s->valid, st);
+}
+
+int train(tto_surrogate* s, int steps, float* loss_host, cudaStream_t st) {
+  if (s->rep_n == 0) return set_error(TTO_E_ARG, "the replay ring is empty");
+  const int M = std::min(s->mb, s->rep_n);
+  int rc = alloc_batch(s, M);
+  if (rc) return rc;
+  const uint2 key = make_uint2((uint32_t)s->seed, (uint32_t)(s->seed >> 32));
+  for (int it = 0; it < steps; ++it) {
+    const uint64_t step = (uint64_t)s->step;
+    sample_kernel<<<M, 128, 0, st>>>(M, s->rep_n, s->k, s->R, key, (uint32_t)step, (uint32_t)(step >> 32),
+                                     s->rep_genome, s->rep_xd, s->rep_t, s->stats, s->mb_topo, s->XD, s->T);
+    TTO_CUDA_TRY(cudaGetLastError());
+    if ((rc = features(s, s->mb_topo, M, 0, st))) return rc;
+    if ((rc = forward(s, M, nullptr, st))) return rc;
+    if ((rc = backward(s, M, st))) return rc;
+    if ((rc = adam(s, st))) return rc;
+  }
+  if (loss_host) {
+    float l[2];
+    TTO_CUDA_TRY(cudaMemcpyAsync(l, s->loss, sizeof(l), cudaMemcpyDeviceToHost, st));
+    TTO_CUDA_TRY(cudaStreamSynchronize(st));
+    *loss_host = l[1] > 0.f ? l[0] / l[1] : 0.f;
+  }
+  return TTO_OK;
+}
+
+// Sort the keys of the first n scores in s->Y (ascending).
+int rank(tto_surrogate* s, int n, cudaStream_t st) {
+  int npad = kSortChunk;
+  while (npad < n) npad <<= 1;
+  if (npad > s->keys_n) {
+    if (s->keys) cudaFree(s->keys);
+    s->keys = nullptr;
+    s->keys_n = 0;
+    TTO_CUDA_TRY(cudaMalloc(&s->keys, (size_t)npad * sizeof(unsigned long long)));
+    s->keys_n = npad;
+  }
+  keys_kernel<<<(npad + 255) / 256, 256, 0, st>>>(n, npad, s->Y, s->keys);
+  const int chunks = npad / kSortChunk;
+  bitonic_shared_kernel<<<chunks, 1024, 0, st>>>(0, s->keys);
+  for (int kk = 2 * kSortChunk; kk <= npad; kk <<= 1) {
+    for (int jj = kk >> 1; jj >= kSortChunk; jj >>= 1)
+      bitonic_global_kernel<<<(npad + 255) / 256, 256, 0, st>>>(npad, kk, jj, s->keys);
+    bitonic_shared_kernel<<<chunks, 1024, 0, st>>>(kk, s->keys);
+  }
+  TTO_CUDA_TRY(cudaGetLastError());
+  return TTO_OK;
+}
+
+// Append n pairs (genomes topo [n][k], fitness fit [n]) whose loadings are
+// batch rows keys[i] (or i) of s->XD.
+int append(tto_surrogate* s, const int32_t* topo, int n, const unsigned long long* keys, const float* XD,
+           const float* fit, cudaStream_t st) {
+  n = std::min(n, s->cap);
+  if (n <= 0) return TTO_OK;
+  replay_append_kernel<<<n, 128, 0, st>>>(n, s->k, s->R, s->cap, s->rep_head, topo, keys, XD, fit, s->rep_genome,
+                                          s->rep_xd, s->rep_t);
+  TTO_CUDA_TRY(cudaGetLastError());
+  s->rep_head = (s->rep_head + n) % s->cap;
+  s->rep_n = std::min(s->cap, s->rep_n + n);
+  target_stats_kernel<<<1, 1024, 0, st>>>(s->rep_n, s->rep_t, s->stats);
+  TTO_CUDA_TRY(cudaGetLastError());
+  return TTO_OK;
+}
+
+void release(tto_surrogate* s) {
+  void* ptrs[] = {s->P,  s->G,     s->Am, s->Av, s->W1sT, s->rows, s->row_lim, s->Nsr, s->SI,  s->SF,
+                  s->XD, s->valid, s->H1, s->H2, s->H3,   s->Y,    s->dH1,     s->dH2, s->dH3, s->dY,
+                  s->T,  s->mb_topo, s->loss, s->stats, s->rep_genome, s->rep_xd, s->rep_t, s->prop, s->keys};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete s;
+}
+
+}  // namespace
+}  // namespace tto
+
+using namespace tto;
+
+extern "C" {
+
+int tto_surrogate_create(tto_grid* g, const tto_surrogate_cfg* cfg, tto_surrogate** out) {
+  if (!g || !cfg || !out) return set_error(TTO_E_ARG, "null argument");
+  *out = nullptr;
+  if (cfg->hidden < 16 || cfg->hidden > kMaxHidden || cfg->hidden % 16 != 0)
+    return set_error(TTO_E_ARG, "hidden must be a multiple of 16 in [16, %d]", kMaxHidden);
+  if (cfg->n_load < 1 || cfg->n_load > g->E) return set_error(TTO_E_ARG, "n_load must be in [1, n_branch]");
+  if (cfg->replay < 1 || cfg->minibatch < 1) return set_error(TTO_E_ARG, "replay and minibatch must be >= 1");
+  if (!(cfg->lr > 0.0) || !(cfg->beta1 >= 0.0 && cfg->beta1 < 1.0) || !(cfg->beta2 >= 0.0 && cfg->beta2 < 1.0) ||
+      !(cfg->eps > 0.0))
+    return set_error(TTO_E_ARG, "Adam needs lr > 0, 0 <= beta < 1, eps > 0");
+  if (g->S < 1 || g->k_max < 1) return set_error(TTO_E_ARG, "the grid has no splittable stations");
+  TTO_CUDA_TRY(cudaSetDevice(g->device));
+  tto_surrogate* s = new (std::nothrow) tto_surrogate();
+  if (!s) return set_error(TTO_E_NOMEM, "host allocation failed");
+  s->g = g;
+  s->H = cfg->hidden;
+  s->R = cfg->n_load;
+  s->S = g->S;
+  s->D = 8 * g->S + s->R;
+  s->k = g->k_max;
+  s->cap = cfg->replay;
+  s->mb = cfg->minibatch;
+  s->lr = cfg->lr;
+  s->beta1 = cfg->beta1;
+  s->beta2 = cfg->beta2;
+  s->eps = cfg->eps;
+  s->seed = cfg->seed;
+  const size_t H = s->H, D = s->D;
+  s->oW1 = 0;
+  s->ob1 = s->oW1 + H * D;
+  s->oW2 = s->ob1 + H;
+  s->ob2 = s->oW2 + H * H;
+  s->oW3 = s->ob2 + H;
+  s->ob3 = s->oW3 + H * H;
+  s->ow4 = s->ob3 + H;
+  s->ob4 = s->ow4 + H;
+  s->n_params = s->ob4 + 1;
+  // loading rows: highest |f0(t=0)| / limit first, ties by branch id
+  std::vector<int> order(g->E);
+  std::vector<double> load(g->E);
+  for (int l = 0; l < g->E; ++l) {
+    order[l] = l;
+    load[l] = fabs(g->f0[l]) / g->limit[l];
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return load[x] > load[y]; });
+  std::vector<int> rows(order.begin(), order.begin() + s->R);
+  std::vector<double> rl(s->R);
+  for (int r = 0; r < s->R; ++r) rl[r] = g->limit[rows[r]];
+  double psum = 0.0;
+  for (int i = 0; i < g->n_bus; ++i) psum += fabs(g->p[i]);
+  s->psum = psum > 0.0 ? psum : 1.0;
+  // He-uniform weights U(-sqrt(6/fan_in), +sqrt(6/fan_in)) from a xorshift64
+  // stream seeded by cfg->seed; zero biases
+  std::vector<float> P(s->n_params, 0.f);
+  uint64_t x = cfg->seed * 0x9E3779B97F4A7C15ull + 0x2545F4914F6CDD1Dull;
+  auto uni = [&]() {
+    x ^= x << 13;
+    x ^= x >> 7;
+    x ^= x << 17;
+    return (double)(x >> 11) * (1.0 / 9007199254740992.0);
+  };
+  auto fill = [&](size_t off, size_t n_out, size_t n_in) {
+    const double lim = sqrt(6.0 / (double)n_in);
+    for (size_t i = 0; i < n_out * n_in; ++i) P[off + i] = (float)((2.0 * uni() - 1.0) * lim);
+  };
+  fill(s->oW1, H, D);
+  fill(s->oW2, H, H);
+  fill(s->oW3, H, H);
+  fill(s->ow4, 1, H);
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+  };
+  A((void**)&s->P, s->n_params * 4);
+  A((void**)&s->G, s->n_params * 4);
+  A((void**)&s->Am, s->n_params * 4);
+  A((void**)&s->Av, s->n_params * 4);
+  A((void**)&s->W1sT, (size_t)8 * s->S * H * 4);
+  A((void**)&s->rows, s->R * sizeof(int));
+  A((void**)&s->row_lim, s->R * sizeof(double));
+  A((void**)&s->Nsr, (size_t)std::max(g->n_sw, 1) * s->R * sizeof(double));
+  A((void**)&s->loss, 2 * sizeof(float));
+  A((void**)&s->stats, 3 * sizeof(float));
+  A((void**)&s->rep_genome, (size_t)s->cap * s->k * sizeof(int32_t));
+  A((void**)&s->rep_xd, (size_t)s->cap * s->R * sizeof(float));
+  A((void**)&s->rep_t, (size_t)s->cap * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpy(s->P, P.data(), s->n_params * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(s->G, 0, s->n_params * 4);
+  if (e == cudaSuccess) e = cudaMemset(s->Am, 0, s->n_params * 4);
+  if (e == cudaSuccess) e = cudaMemset(s->Av, 0, s->n_params * 4);
+  if (e == cudaSuccess) e = cudaMemset(s->loss, 0, 2 * sizeof(float));
+  const float unit[3] = {0.f, 1.f, 1.f};
+  if (e == cudaSuccess) e = cudaMemcpy(s->stats, unit, sizeof(unit), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->rows, rows.data(), s->R * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->row_lim, rl.data(), s->R * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && g->n_sw > 0) {
+    const size_t n = (size_t)g->n_sw * s->R;
+    gather_rows_kernel<<<(unsigned)((n + 255) / 256), 256>>>(g->n_sw, g->E, s->R, g->d_Nsw, s->rows, s->Nsr);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    const int rc = refresh_station_weights(s, 0);
+    if (rc) {
+      release(s);
+      return rc;
+    }
+    e = cudaDeviceSynchronize();
+  }
+  if (e != cudaSuccess) {
+    release(s);
+    return cuda_error(e, "surrogate allocation");
+  }
+  *out = s;
+  return TTO_OK;
+}
+
+int tto_surrogate_destroy(tto_surrogate* s) {
+  if (!s) return TTO_OK;
+  cudaSetDevice(s->g->device);
+  cudaDeviceSynchronize();
+  release(s);
+  return TTO_OK;
+}
+
+int tto_surrogate_info(const tto_surrogate* s, int64_t* n_params, int32_t* input_dim, int32_t* replay_fill,
+                       int32_t* rows_out, float* target_stats) {
+  if (!s) return set_error(TTO_E_ARG, "null surrogate");
+  if (n_params) *n_params = (int64_t)s->n_params;
+  if (input_dim) *input_dim = s->D;
+  if (replay_fill) *replay_fill = s->rep_n;
+  if (rows_out || target_stats) {
+    TTO_CUDA_TRY(cudaSetDevice(s->g->device));
+    TTO_CUDA_TRY(cudaDeviceSynchronize());
+  }
+  if (rows_out) TTO_CUDA_TRY(cudaMemcpy(rows_out, s->rows, s->R * sizeof(int), cudaMemcpyDeviceToHost));
+  if (target_stats) TTO_CUDA_TRY(cudaMemcpy(target_stats, s->stats, 2 * sizeof(float), cudaMemcpyDeviceToHost));
+  return TTO_OK;
+}
+
+int tto_surrogate_params(tto_surrogate* s, float* get_host, const float* set_host) {
+  if (!s) return set_error(TTO_E_ARG, "null surrogate");
+  TTO_CUDA_TRY(cudaSetDevice(s->g->device));
+  TTO_CUDA_TRY(cudaDeviceSynchronize());
+  if (set_host) {
+    TTO_CUDA_TRY(cudaMemcpy(s->P, set_host, s->n_params * 4, cudaMemcpyHostToDevice));
+    TTO_CUDA_TRY(cudaMemset(s->Am, 0, s->n_params * 4));
+    TTO_CUDA_TRY(cudaMemset(s->Av, 0, s->n_params * 4));
+    s->step = 0;
+    const int rc = refresh_station_weights(s, 0);
+    if (rc) return rc;
+    TTO_CUDA_TRY(cudaDeviceSynchronize());
+  }
+  if (get_host) TTO_CUDA_TRY(cudaMemcpy(get_host, s->P, s->n_params * 4, cudaMemcpyDeviceToHost));
+  return TTO_OK;
+}
+
+int tto_surrogate_score(tto_surrogate* s, const int32_t* topo, int32_t B, float* score_out, void* stream) {
+  if (!s || B < 0 || (B > 0 && (!topo || !score_out))) return set_error(TTO_E_ARG, "bad score arguments");
+  if (B == 0) return TTO_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  TTO_CUDA_TRY(cudaSetDevice(s->g->device));
+  const int rc = score(s, topo, B, st);
+  if (rc) return rc;
+  TTO_CUDA_TRY(cudaMemcpyAsync(score_out, s->Y, (size_t)B * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  return TTO_OK;
+}
+
+int tto_surrogate_features(tto_surrogate* s, int32_t B, int32_t* si, float* sf, float* xd, int32_t* valid) {
+  if (!s || B < 0 || B > s->bcap) return set_error(TTO_E_ARG, "B exceeds the last batch");
+  TTO_CUDA_TRY(cudaSetDevice(s->g->device));
+  TTO_CUDA_TRY(cudaDeviceSynchronize());
+  const size_t b = B;
+  if (si) TTO_CUDA_TRY(cudaMemcpy(si, s->SI, b * s->k * sizeof(int), cudaMemcpyDeviceToHost));
+  if (sf) TTO_CUDA_TRY(cudaMemcpy(sf, s->SF, b * s->k * 8 * sizeof(float), cudaMemcpyDeviceToHost));
+  if (xd) TTO_CUDA_TRY(cudaMemcpy(xd, s->XD, b * s->R * sizeof(float), cudaMemcpyDeviceToHost));
+  if (valid) TTO_CUDA_TRY(cudaMemcpy(valid, s->valid, b * sizeof(int), cudaMemcpyDeviceToHost));
+  return TTO_OK;
+}
+
+int tto_surrogate_add(tto_surrogate* s, const int32_t* topo, int32_t B, const float* fitness, void* stream) {
+  if (!s || B < 0 || (B > 0 && (!topo || !fitness))) return set_error(TTO_E_ARG, "bad add arguments");
+  if (B == 0) return TTO_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  TTO_CUDA_TRY(cudaSetDevice(s->g->device));
+  int rc = alloc_batch(s, B);
+  if (rc) return rc;
+  if ((rc = features(s, topo, B, 1, st))) return rc;
+  // a batch larger than the ring leaves its last `cap` pairs
+  const int skip = std::max(0, B - s->cap);
+  return append(s, topo + (size_t)skip * s->k, B - skip, nullptr, s->XD + (size_t)skip * s->R, fitness + skip, st);
+}
+
+int tto_surrogate_train(tto_surrogate* s, int32_t steps, float* loss, void* stream) {
+  if (!s || steps < 0) return set_error(TTO_E_ARG, "bad train arguments");
+  if (steps == 0) return TTO_OK;
+  TTO_CUDA_TRY(cudaSetDevice(s->g->device));
+  return train(s, steps, loss, (cudaStream_t)stream);
+}
+
+int tto_surrogate_grad(tto_surrogate* s, const int32_t* topo, int32_t B, const float* fitness, float* loss,
+                       float* grad, void* stream) {
+  if (!s || B < 1 || !topo || !fitness) return set_error(TTO_E_ARG, "bad grad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  TTO_CUDA_TRY(cudaSetDevice(s->g->device));
+  int rc = alloc_batch(s, B);
+  if (rc) return rc;
+  if ((rc = features(s, topo, B, 1, st))) return rc;
+  targets_kernel<<<(B + 255) / 256, 256, 0, st>>>(B, fitness, s->stats, s->T);
+  TTO_CUDA_TRY(cudaGetLastError());
+  if ((rc = forward(s, B, nullptr, st))) return rc;
+  if ((rc = backward(s, B, st))) return rc;
+  float l[2];
+  TTO_CUDA_TRY(cudaMemcpyAsync(l, s->loss, sizeof(l), cudaMemcpyDeviceToHost, st));
+  TTO_CUDA_TRY(cudaStreamSynchronize(st));
+  if (loss) *loss = l[1] > 0.f ? l[0] / l[1] : 0.f;
+  if (grad) TTO_CUDA_TRY(cudaMemcpy(grad, s->G, s->n_params * 4, cudaMemcpyDeviceToHost));
+  return TTO_OK;
+}
+
+int tto_mapelites_step_screened(tto_archive* a, tto_surrogate* s, uint64_t seed, uint64_t iteration,
+                                int32_t n_propose, int32_t n_exact, const tto_mut_params* mp,
+                                const tto_eval_opts* opts, int32_t train_steps, int32_t* topo_out,
+                                float* fitness_out, float* score_out, void* stream) {
+  if (!a || !s || !mp || !opts || a->g != s->g) return set_error(TTO_E_ARG, "bad screened-step arguments");
+  if (n_exact < 1 || n_propose < n_exact) return set_error(TTO_E_ARG, "need 1 <= n_exact <= n_propose");
+  if (train_steps < 0) return set_error(TTO_E_ARG, "train_steps must be >= 0");
+  if (opts->d_split != a->d_split || opts->d_moved != a->d_moved)
+    return set_error(TTO_E_ARG, "evaluation cell extents differ from the archive's");
+  tto_grid* g = a->g;
+  cudaStream_t st = (cudaStream_t)stream;
+  TTO_CUDA_TRY(cudaSetDevice(g->device));
+  if (g->T > TTO_MAX_T) return set_error(TTO_E_ARG, "grid has more than %d timesteps", TTO_MAX_T);
+  int rc = ensure_workspace(g, n_exact, padded_T(g->T));
+  if (rc) return rc;
+  if (n_propose > s->pcap) {
+    if (s->prop) cudaFree(s->prop);
+    s->prop = nullptr;
+    s->pcap = 0;
+    TTO_CUDA_TRY(cudaMalloc(&s->prop, (size_t)n_propose * g->k_max * sizeof(int32_t)));
+    s->pcap = n_propose;
+  }
+  // one allocation for scoring and training, so neither invalidates the other
+  if ((rc = alloc_batch(s, std::max(n_propose, s->mb)))) return rc;
+  Workspace& w = g->ws;
+  if ((rc = propose_impl(a, seed, iteration, n_propose, mp, s->prop, st))) return rc;
+  if (s->rep_n > 0) {
+    if ((rc = score(s, s->prop, n_propose, st))) return rc;
+  } else {
+    if ((rc = features(s, s->prop, n_propose, 1, st))) return rc;
+    valid_only_kernel<<<(n_propose + 255) / 256, 256, 0, st>>>(n_propose, s->valid, s->Y);
+    TTO_CUDA_TRY(cudaGetLastError());
+  }
+  if ((rc = rank(s, n_propose, st))) return rc;
+  gather_topo_kernel<<<(n_exact + 255) / 256, 256, 0, st>>>(n_exact, g->k_max, s->keys, s->prop, w.topo);
+  if (score_out) gather_score_kernel<<<(n_exact + 255) / 256, 256, 0, st>>>(n_exact, s->keys, s->Y, score_out);
+  TTO_CUDA_TRY(cudaGetLastError());
+  rc = evaluate_impl(g, w.topo, n_exact, nullptr, g->T, opts, w.fit, w.desc, w.cell, w.island, nullptr, nullptr, st);
+  if (rc) return rc;
+  if ((rc = insert_impl(a, w.topo, n_exact, w.fit, w.cell, st))) return rc;
+  if ((rc = append(s, w.topo, n_exact, s->keys, s->XD, w.fit, st))) return rc;
+  if (train_steps > 0 && (rc = train(s, train_steps, nullptr, st))) return rc;
+  if (topo_out)
+    TTO_CUDA_TRY(cudaMemcpyAsync(topo_out, w.topo, (size_t)n_exact * g->k_max * sizeof(int32_t),
+                                 cudaMemcpyDeviceToDevice, st));
+  if (fitness_out)
+    TTO_CUDA_TRY(cudaMemcpyAsync(fitness_out, w.fit, (size_t)n_exact * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  return TTO_OK;
+}
+
+}  // extern "C"

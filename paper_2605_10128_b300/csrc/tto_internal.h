@@ -115,4 +115,9 @@ void forget_grid_graphs(const tto_grid* g);
 int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, int n_t,
                   const tto_eval_opts* o, float* fitness, int32_t* desc, int32_t* cell,
                   uint8_t* island, float* metrics, float* fmax, cudaStream_t s);
+// MapElites building blocks shared by the plain and the surrogate-screened step.
+int propose_impl(tto_archive* ar, uint64_t seed, uint64_t it, int B, const tto_mut_params* mp,
+                 int32_t* out, cudaStream_t s);
+int insert_impl(tto_archive* ar, const int32_t* topo, int B, const float* fit, const int32_t* cell,
+                cudaStream_t s);
 }  // namespace tto

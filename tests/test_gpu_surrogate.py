@@ -1,0 +1,342 @@
+"""GPU surrogate screen against the FP64 oracle (oracle/mlp.py).
+
+Inputs (station values, loadings, validity) must match the oracle to FP32
+rounding.  The network computes every product from BF16-rounded operands with
+FP32 accumulation, unit roundoff u = 2^-9 per operand: an emulation of that
+rounding at these shapes (H = 512, D = 1456, 256 rows) puts the forward pass
+0.6 % and the gradient blocks at most 1.2 % from FP64 (normwise), so the bars
+are 2 % for the output and 4 % per gradient block; a dropped term, a wrong sign
+or a transposed operand moves a block by O(1).  Adam is checked against its
+formula applied to the library's own gradients; the top-k selection, the
+untrained screen and determinism are checked exactly; the last tests show what
+the trained network gains over unscreened proposals.
+"""
+import numpy as np
+import pytest
+
+from oracle import dcflow, mlp
+from synth import config_grid, limits_from_flows, random_topologies, CONFIGS
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL_FWD = 2e-2
+TOL_GRAD = 4e-2
+ORDER = ["W1", "b1", "W2", "b2", "W3", "b3", "w4", "b4"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+
+
+def _grid(name, seed=0):
+    sg = config_grid(name, seed=seed)
+    f0 = dcflow.base_flows(sg)
+    return sg.with_limits(limits_from_flows(f0[0], CONFIGS[name]["n_tight"], seed=seed))
+
+
+@pytest.fixture(scope="module")
+def g2k():
+    from paper_2605_10128_b300 import Grid
+    sg = _grid("tto2k")
+    return sg, Grid(sg)
+
+
+@pytest.fixture(scope="module")
+def g30():
+    from paper_2605_10128_b300 import Grid
+    sg = _grid("tto30")
+    return sg, Grid(sg)
+
+
+def pack(P):
+    return np.concatenate([np.ravel(P[k]) for k in ORDER]).astype(np.float32)
+
+
+def unpack(v, D, H):
+    shapes = dict(W1=(H, D), b1=(H,), W2=(H, H), b2=(H,), W3=(H, H), b3=(H,), w4=(H,), b4=(1,))
+    out, o = {}, 0
+    for k in ORDER:
+        n = int(np.prod(shapes[k]))
+        out[k] = np.asarray(v[o:o + n], dtype=np.float64).reshape(shapes[k])
+        o += n
+    assert o == v.size
+    return out
+
+
+def dense_station_block(si, sf, S):
+    B, k = si.shape
+    X = np.zeros((B, S, 8))
+    for b in range(B):
+        for j in range(k):
+            if si[b, j] >= 0:
+                X[b, si[b, j]] = sf[b, j]
+    return X.reshape(B, 8 * S)
+
+
+def oracle_inputs(sg, topo, rows, skip=()):
+    X, ok = [], []
+    for i, gnm in enumerate(topo):
+        x = None if i in skip else mlp.features(sg, gnm, rows)
+        ok.append(x is not None)
+        X.append(np.zeros(8 * sg.n_station + len(rows)) if x is None else x)
+    return np.array(X), np.array(ok)
+
+
+def nrel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def _surrogate(grid, **kw):
+    from paper_2605_10128_b300 import Surrogate
+    args = dict(hidden=512, n_load=256, replay=4096, minibatch=4096, lr=1e-3, seed=3)
+    args.update(kw)
+    return Surrogate(grid, **args)
+
+
+def _dev(a, dtype=torch.int32):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def test_loading_rows_match_oracle(g2k):
+    sg, g = g2k
+    s = _surrogate(g)
+    assert np.array_equal(s.rows, mlp.top_loaded_branches(sg, 256))
+    assert s.input_dim == 8 * sg.n_station + 256
+    H, D = 512, s.input_dim
+    assert s.n_params == H * D + H + 2 * (H * H + H) + H + 1
+
+
+@pytest.mark.parametrize("name,B", [("tto30", 256), ("tto2k", 96)])
+def test_features_match_oracle(name, B, g30, g2k):
+    sg, g = g30 if name == "tto30" else g2k
+    R = min(256, sg.n_branch)
+    s = _surrogate(g, n_load=R)
+    topo = random_topologies(sg, B, seed=11, min_splits=0)
+    topo[0] = -1  # unsplit genome: base loadings, no station values
+    if sg.n_action > 1:  # the same station split twice: invalid
+        st = sg.action_station
+        a0 = 0
+        a1 = int(np.nonzero(st == st[a0])[0][-1])
+        topo[1] = -1
+        topo[1, 0], topo[1, 1] = a0, a1
+    sc = s.score(_dev(topo)).cpu().numpy()
+    si, sf, xd, valid = s.features(B)
+    X, ok = oracle_inputs(sg, topo, s.rows, skip=(1,) if sg.n_action > 1 else ())
+    assert np.array_equal(valid.astype(bool), ok), np.nonzero(valid.astype(bool) != ok)
+    assert np.all(np.isinf(sc[~ok])) and np.all(np.isfinite(sc[ok]))
+    S = sg.n_station
+    Xs = dense_station_block(si, sf, S)
+    np.testing.assert_allclose(Xs[ok], X[ok, :8 * S], rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(xd[ok], X[ok, 8 * S:], rtol=1e-5, atol=1e-6)
+    base = np.abs(dcflow.base_flows(sg)[0][s.rows]) / sg.limit[s.rows]
+    np.testing.assert_allclose(xd[0], base, rtol=1e-5, atol=1e-6)
+    assert not np.any(sf[0]) and np.all(si[0] == -1)
+    print(f"\n{name}: {int((~ok).sum())} of {B} genomes invalid or islanding")
+
+
+def _params_from_oracle(s, D, H, seed=5):
+    P = mlp.init_params(D, H, seed=seed)
+    rng = np.random.default_rng(seed)
+    for k in ["b1", "b2", "b3", "b4"]:
+        P[k] = rng.normal(0, 0.05, P[k].shape)
+    v = pack(P)
+    s.params(v)
+    return unpack(v, D, H)
+
+
+def test_forward_matches_oracle(g2k):
+    sg, g = g2k
+    s = _surrogate(g)
+    H, D = 512, s.input_dim
+    P = _params_from_oracle(s, D, H)
+    topo = random_topologies(sg, 256, seed=12, min_splits=1)
+    y = s.score(_dev(topo)).cpu().numpy().astype(np.float64)
+    X, ok = oracle_inputs(sg, topo, s.rows)
+    yo, _ = mlp.forward(P, X[ok])
+    e = nrel(y[ok], yo)
+    print(f"\nforward: normwise relative error {e:.2e} ({int(ok.sum())} rows)")
+    assert e <= TOL_FWD
+
+
+def test_gradients_match_oracle(g2k):
+    sg, g = g2k
+    s = _surrogate(g)
+    H, D = 512, s.input_dim
+    P = _params_from_oracle(s, D, H)
+    topo = random_topologies(sg, 256, seed=13, min_splits=1)
+    X, ok = oracle_inputs(sg, topo, s.rows)
+    topo, X = topo[ok], X[ok]
+    # targets 1 to 2 above the FP64 prediction: no gradient block is a
+    # near-cancelling sum of residuals of both signs, whose rounding error
+    # would be amplified by the cancellation
+    yo, _ = mlp.forward(P, X)
+    t = yo + np.random.default_rng(1).uniform(1.0, 2.0, len(topo))
+    fit = (-np.expm1(t)).astype(np.float32)
+    assert s.target_stats() == (0.0, 1.0)  # empty ring: targets unscaled
+    loss, grad = s.grad(_dev(topo), _dev(fit, torch.float32))
+    Lo, Go = mlp.loss_and_grads(P, X, mlp.target(fit.astype(np.float64)))
+    assert abs(loss - Lo) <= 2 * TOL_FWD * Lo
+    G = unpack(grad, D, H)
+    errs = {k: nrel(G[k], Go[k]) for k in ORDER}
+    print("\ngradient normwise relative errors: " + ", ".join(f"{k} {v:.2e}" for k, v in errs.items()))
+    for k, v in errs.items():
+        assert v <= TOL_GRAD, (k, v)
+    # the station block of W1 separately (sparse path)
+    S8 = 8 * sg.n_station
+    assert nrel(G["W1"][:, :S8], Go["W1"][:, :S8]) <= TOL_GRAD
+    assert nrel(G["W1"][:, S8:], Go["W1"][:, S8:]) <= TOL_GRAD
+
+
+def test_adam_steps_follow_formula(g2k):
+    """Two training steps on a ring smaller than the minibatch (every ring
+    entry, in order) equal two Adam updates (oracle formula, FP64) driven by
+    the library's own gradients at P0 and P1."""
+    sg, g = g2k
+    s = _surrogate(g, replay=512, minibatch=512, lr=1e-3)
+    H, D = 512, s.input_dim
+    _params_from_oracle(s, D, H)
+    P0 = s.params()
+    topo = random_topologies(sg, 300, seed=14, min_splits=1)
+    fit = -np.random.default_rng(2).uniform(0.0, 30.0, len(topo)).astype(np.float32)
+    fit[5] = -np.inf  # no target: skipped by the loss
+    td, fd = _dev(topo), _dev(fit, torch.float32)
+    s.add(td, fd)
+    assert s.replay_fill() == 300
+    m, sd = s.target_stats()
+    mo, sdo = mlp.target_stats(mlp.target(fit.astype(np.float64)))
+    assert m == pytest.approx(mo, rel=1e-6) and sd == pytest.approx(sdo, rel=1e-5)
+    _, g1 = s.grad(td, fd)
+    l1 = s.train(1)
+    P1 = s.params()
+    _, g2 = s.grad(td, fd)
+    s.train(1)
+    P2 = s.params()
+    assert np.isfinite(l1) and l1 > 0
+    Pe = {"p": P0.astype(np.float64)}
+    st = {}
+    mlp.adam_step(Pe, {"p": g1.astype(np.float64)}, st, lr=1e-3)
+    np.testing.assert_allclose(P1, Pe["p"], rtol=0, atol=2e-6)
+    mlp.adam_step(Pe, {"p": g2.astype(np.float64)}, st, lr=1e-3)
+    np.testing.assert_allclose(P2, Pe["p"], rtol=0, atol=4e-6)
+    moved = np.abs(P2 - P0) > 1e-4
+    assert moved.mean() > 0.5
+
+
+def _archive_seeded(sg, g, d_split, d_moved, seed):
+    from paper_2605_10128_b300 import Archive, PREC_FP32
+    a = Archive(g, d_split, d_moved)
+    topo = _dev(random_topologies(sg, 64, seed=seed, min_splits=1))
+    out = g.evaluate(topo, precision=PREC_FP32, d_split=d_split, d_moved=d_moved)
+    a.insert(topo, out["fitness"], out["cell"])
+    return a
+
+
+def test_topk_selection_and_scores(g2k):
+    """The screened step evaluates exactly the n_exact proposals of lowest
+    predicted score (ties by proposal index) and reports their scores."""
+    from paper_2605_10128_b300 import DEFAULT_MUTATION
+    sg, g = g2k
+    s = _surrogate(g)
+    seedt = random_topologies(sg, 512, seed=15, min_splits=1)
+    td = _dev(seedt)
+    out = g.evaluate(td)
+    s.add(td, out["fitness"])
+    s.train(3, want_loss=False)
+    a = _archive_seeded(sg, g, 8, 8, 16)
+    for n_prop, n_ex in [(5000, 700), (2048, 2048), (3, 1), (65536, 8192)]:
+        prop = a.propose(77, 5, n_prop, DEFAULT_MUTATION)
+        sc = s.score(prop).cpu().numpy()
+        k = g.k_max
+        topo_out = torch.empty(n_ex, k, dtype=torch.int32, device="cuda")
+        sc_out = torch.empty(n_ex, dtype=torch.float32, device="cuda")
+        a2 = _archive_seeded(sg, g, 8, 8, 16)  # same archive state, fresh copy
+        a2.step_screened(s, 77, 5, n_prop, n_ex, train_steps=0, topo_out=topo_out, score_out=sc_out)
+        order = np.lexsort((np.arange(n_prop), np.where(np.isnan(sc), np.inf, sc)))[:n_ex]
+        assert np.array_equal(topo_out.cpu().numpy(), prop.cpu().numpy()[order]), (n_prop, n_ex)
+        assert np.array_equal(sc_out.cpu().numpy(), sc[order])
+        a2.close()
+
+
+def test_untrained_screen_keeps_first_valid(g30):
+    from paper_2605_10128_b300 import DEFAULT_MUTATION
+    sg, g = g30
+    s = _surrogate(g, n_load=41)
+    a = _archive_seeded(sg, g, 8, 8, 17)
+    prop = a.propose(5, 1, 400, DEFAULT_MUTATION).cpu().numpy()
+    ok = np.array([dcflow.is_connected_uf(*dcflow.post_split_graph(sg, p)[:3]) for p in prop])
+    topo_out = torch.empty(100, g.k_max, dtype=torch.int32, device="cuda")
+    a.step_screened(s, 5, 1, 400, 100, train_steps=0, topo_out=topo_out)
+    keep = np.nonzero(ok)[0][:100]
+    assert np.array_equal(topo_out.cpu().numpy(), prop[keep])
+    assert s.replay_fill() == 100
+
+
+def test_screened_step_deterministic(g2k):
+    from paper_2605_10128_b300 import Archive
+    sg, g = g2k
+    res = []
+    for _ in range(2):
+        s = _surrogate(g, replay=8192, minibatch=1024, seed=9)
+        a = Archive(g, 8, 8)
+        for it in range(4):
+            a.step_screened(s, 21, it, 4096, 512, train_steps=2)
+        res.append((a.export(), s.params()))
+        a.close()
+        s.close()
+    (f0, g0, m0), p0 = res[0]
+    (f1, g1, m1), p1 = res[1]
+    assert np.array_equal(f0, f1) and np.array_equal(g0, g1) and np.array_equal(m0, m1)
+    assert np.array_equal(p0, p1)
+
+
+def _exact(g, topo):
+    out = g.evaluate(topo)
+    return out["fitness"].cpu().numpy().astype(np.float64)
+
+
+def test_training_reduces_loss(g2k):
+    sg, g = g2k
+    s = _surrogate(g, replay=16384, minibatch=4096, lr=1e-3, seed=4)
+    topo = _dev(random_topologies(sg, 8192, seed=18, min_splits=1))
+    fit = g.evaluate(topo)["fitness"]
+    s.add(topo, fit)
+    l0 = s.train(1)
+    l1 = s.train(150)
+    print(f"\ntraining loss {l0:.4f} -> {l1:.4f}")
+    assert l1 < 0.5 * l0
+
+
+def _spearman(a, b):
+    from scipy.stats import spearmanr
+    return float(spearmanr(a, b).statistic)
+
+
+def test_screening_gain_and_rank_correlation(g2k):
+    """Trained on 16384 exact pairs, the network ranks 8192 fresh proposals:
+    the top eighth by score has a better mean exact fitness than the whole
+    set (what random selection of the same size gets on average), and the
+    scores correlate with the exact targets."""
+    sg, g = g2k
+    s = _surrogate(g, replay=16384, minibatch=4096, lr=1e-3, seed=6)
+    train = _dev(random_topologies(sg, 16384, seed=19, min_splits=1))
+    s.add(train, g.evaluate(train)["fitness"])
+    s.train(300, want_loss=False)
+    test = _dev(random_topologies(sg, 8192, seed=20, min_splits=1))
+    fit = _exact(g, test)
+    sc = s.score(test).cpu().numpy().astype(np.float64)
+    ok = np.isfinite(fit) & np.isfinite(sc)
+    rho = _spearman(sc[ok], np.log1p(-fit[ok]))
+    k = ok.sum() // 8
+    top = np.argsort(sc[ok], kind="stable")[:k]
+    f_ok = fit[ok]
+    true_top = np.argsort(-f_ok, kind="stable")[:k]
+    gain = float(f_ok[top].mean() - f_ok.mean())
+    eff = gain / float(f_ok[true_top].mean() - f_ok.mean())
+    print(f"\nSpearman rho {rho:.3f}; top eighth by score: mean fitness {f_ok[top].mean():.2f} vs "
+          f"{f_ok.mean():.2f} for all ({eff:.2f} of the gain of the true top eighth); best "
+          f"{f_ok[top].max():.2f} vs best overall {f_ok.max():.2f}")
+    assert rho > 0.5
+    assert eff > 0.5

@@ -71,3 +71,13 @@ def test_station_features_three_bus():
     x = mlp.features(g, [a], np.array([0, 1]))
     # post-split flows (0, 1, 0) against limits (0.5, 0.9)
     np.testing.assert_allclose(x[8:], [0.0, 1.0 / 0.9], atol=1e-12)
+
+
+def test_target_stats_closed_forms():
+    assert mlp.target_stats([1.0, 3.0]) == (2.0, 1.0)
+    assert mlp.target_stats([1.0, np.nan, 3.0, np.inf, -np.inf]) == (2.0, 1.0)
+    assert mlp.target_stats([5.0, 5.0, 5.0]) == (5.0, 1.0)
+    assert mlp.target_stats([]) == (0.0, 1.0)
+    m, sd = mlp.target_stats([0.0, 0.0, 0.0, 4.0])  # mean 1, squares 1+1+1+9 over 4
+    assert m == 1.0 and sd == pytest.approx(np.sqrt(3.0), rel=1e-15)
+    assert mlp.target([0.0, -np.e + 1.0]) == pytest.approx([0.0, 1.0], rel=1e-15)
