@@ -237,6 +237,109 @@ def run_mixed(args, prec, pk, pk_kind):
     print(json.dumps(line), flush=True)
 
 
+def _best(archive):
+    fit, _, filled = archive.export()
+    return float(fit[filled.astype(bool)].max()) if filled.any() else -np.inf
+
+
+def run_surrogate(args, prec):
+    """Time to target on the 10000-bus workload: surrogate-screened MapElites
+    against plain MapElites (8192 proposals evaluated exactly per iteration),
+    same seeds, same precision.  A screened variant "rank:n" proposes n
+    candidates per iteration, scores them, evaluates the best-ranked 8192
+    exactly (rank "score": by predicted fitness; "gain": by predicted gain over
+    the cell's elite, empty cells first), then runs --train-steps training
+    steps.  The target of a seed is the best fitness its plain run reaches in
+    --iters iterations; each arm's time to target is the wall time of the
+    first iteration whose archive holds a fitness at least as good."""
+    import torch
+    from scipy.stats import spearmanr
+    from paper_2605_10128_b300 import Archive, Surrogate, SCREEN_SCORE, SCREEN_CELL_GAIN
+    cfg = "tto10k"
+    c = CONFIGS[cfg]
+    B = c["batch"]
+    ds, dm = c["archive"]
+    sg, g, _ = make_grid(cfg, 0, seed=0)
+    g.reserve(B)
+    sur_kw = dict(hidden=512, n_load=256, replay=262144, minibatch=8192, lr=1e-3)
+    variants = []
+    for v in args.variants.split(","):
+        mode, n = v.split(":")
+        variants.append((v, {"score": SCREEN_SCORE, "gain": SCREEN_CELL_GAIN}[mode], int(n)))
+    # warm-up: lazily built device data and every kernel of both arms
+    wa = Archive(g, ds, dm)
+    ws = Surrogate(g, seed=1, **sur_kw)
+    for it in range(2):
+        wa.step(1, it, B, precision=prec)
+        wa.step_screened(ws, 1, it, variants[0][2], B, rank_by=variants[0][1], precision=prec, train_steps=1)
+    torch.cuda.synchronize()
+    wa.close()
+    ws.close()
+
+    def run_arm(seed, variant):
+        A = Archive(g, ds, dm)
+        S = Surrogate(g, seed=seed, **sur_kw) if variant else None
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        curve = []
+        for it in range(args.iters):
+            if S is None:
+                A.step(seed, it, B, precision=prec)
+            else:
+                A.step_screened(S, seed, it, variant[2], B, rank_by=variant[1], precision=prec,
+                                train_steps=args.train_steps)
+            curve.append((time.perf_counter() - t0, _best(A)))
+        g.sync_status()
+        rho = None
+        if S is not None:
+            # rank correlation on fresh proposals of the final archive
+            prop = A.propose(seed, args.iters + 1, B)
+            sc = S.score(prop).cpu().numpy().astype(np.float64)
+            fit = g.evaluate(prop, precision=prec, d_split=ds, d_moved=dm)["fitness"].cpu().numpy()
+            ok = np.isfinite(sc) & np.isfinite(fit)
+            rho = float(spearmanr(sc[ok], np.log1p(-fit[ok].astype(np.float64))).statistic)
+            S.close()
+        A.close()
+        return curve, rho
+
+    runs = []
+    for k in range(args.seeds):
+        seed = 2000 + k
+        plain, _ = run_arm(seed, None)
+        target = plain[-1][1]
+        t_plain = next(t for t, b in plain if b >= target)
+        rec = {"seed": seed, "target_fitness": target, "plain_s": t_plain,
+               "plain_s_per_iter": plain[-1][0] / args.iters,
+               "plain_best_by_iter": [round(b, 3) for _, b in plain], "screened": {}}
+        for v in variants:
+            curve, rho = run_arm(seed, v)
+            hit = [t for t, b in curve if b >= target]
+            rec["screened"][v[0]] = {"time_s": hit[0] if hit else None,
+                                     "speedup": (t_plain / hit[0]) if hit else None,
+                                     "final_best": curve[-1][1], "s_per_iter": curve[-1][0] / args.iters,
+                                     "spearman_rho": rho, "best_by_iter": [round(b, 3) for _, b in curve]}
+        runs.append(rec)
+    summary = {}
+    for v in variants:
+        sp = [r["screened"][v[0]]["speedup"] for r in runs]
+        reached = sum(x is not None for x in sp)
+        summary[v[0]] = {"reached": f"{reached}/{len(runs)}",
+                         "median_speedup": float(np.median(sp)) if reached == len(runs) else None,
+                         "final_best_minus_target": [r["screened"][v[0]]["final_best"] - r["target_fitness"]
+                                                     for r in runs]}
+    head = summary[variants[0][0]]["median_speedup"]
+    line = {"metric": "time-to-target best fitness (10k-bus), surrogate-screened vs plain MapElites",
+            "value": head, "unit": "x (plain s / screened s)",
+            "n_gpus": 1, "steps": args.iters, "warmup": 2, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_desc(cfg, B), "precision": args.precision,
+                       "variants": args.variants, "exact_per_iter": B,
+                       "train_steps_per_iter": args.train_steps, "surrogate": sur_kw,
+                       "seeds": args.seeds, "iterations": args.iters},
+            "summary": summary, "runs": runs, "gpu_launches": None}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -248,6 +351,11 @@ def main():
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "fp16x3", "tf32x3", "bf16x3", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-outages", type=int, default=120)
+    ap.add_argument("--iters", type=int, default=60, help="--config surrogate: iterations per arm")
+    ap.add_argument("--seeds", type=int, default=3, help="--config surrogate: seeds")
+    ap.add_argument("--variants", default="score:16384,score:65536",
+                    help="--config surrogate: screened variants rank:proposals (rank = score or gain)")
+    ap.add_argument("--train-steps", type=int, default=8, help="--config surrogate: training steps per iteration")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -270,6 +378,10 @@ def main():
         if rank == 0:
             pk, pk_kind = peaks()
             run_mixed(args, prec, pk, pk_kind)
+        return
+    if args.config == "surrogate":
+        if rank == 0:
+            run_surrogate(args, prec)
         return
     c = CONFIGS[args.config]
     B = args.batch or c["batch"]

@@ -357,18 +357,31 @@ int tto_surrogate_train(tto_surrogate* s, int32_t steps, float* loss, void* stre
 int tto_surrogate_grad(tto_surrogate* s, const int32_t* topo, int32_t B, const float* fitness,
                        float* loss, float* grad, void* stream);
 
+/* Ranking of the screened step (rank_by). */
+#define TTO_SCREEN_SCORE 0     /* by predicted score */
+#define TTO_SCREEN_CELL_GAIN 1 /* empty cells first, then by predicted gain over the cell's elite */
+
 /* One surrogate-screened MapElites iteration: propose n_propose candidates
- * (as tto_mapelites_propose), score them, evaluate exactly the n_exact of
- * lowest predicted score (ties by proposal index; while the replay ring is
- * empty, the first n_exact proposals that do not island the grid), insert them
- * into the archive, append them to the replay ring and run train_steps
- * training steps.  topo_out / fitness_out / score_out (device, optional,
- * [n_exact]) receive the evaluated genomes, their exact fitness and their
- * predicted score.  Asynchronous. */
+ * (as tto_mapelites_propose; n_propose <= 2^30), score them, and evaluate
+ * exactly the n_exact ranked first.  TTO_SCREEN_SCORE ranks by predicted
+ * score; TTO_SCREEN_CELL_GAIN ranks the proposals whose descriptors map to an
+ * empty cell first, by predicted score, then the others by predicted
+ * improvement over their cell's elite, score - log1p(-fitness_elite).  Ties go
+ * by proposal index.  Either way a proposal that islands the grid or equals
+ * its cell's elite slot for slot ranks last, and a proposal whose genome
+ * repeats the one ranked just before it moves behind all others (repeats fill
+ * the batch only when too few others remain).  While the replay ring is empty
+ * every proposal that does not island the grid scores 0.  The evaluated
+ * candidates are inserted into the archive and appended to the replay ring,
+ * then train_steps training steps run.  topo_out / fitness_out / score_out
+ * (device, optional, [n_exact]) receive the evaluated genomes, their exact
+ * fitness and their predicted score (+inf for a skipped elite copy).
+ * Asynchronous. */
 int tto_mapelites_step_screened(tto_archive* a, tto_surrogate* s, uint64_t seed, uint64_t iteration,
-                                int32_t n_propose, int32_t n_exact, const tto_mut_params* mp,
-                                const tto_eval_opts* opts, int32_t train_steps, int32_t* topo_out,
-                                float* fitness_out, float* score_out, void* stream);
+                                int32_t n_propose, int32_t n_exact, int32_t rank_by,
+                                const tto_mut_params* mp, const tto_eval_opts* opts,
+                                int32_t train_steps, int32_t* topo_out, float* fitness_out,
+                                float* score_out, void* stream);
 
 /* Thread-local message of the last failing call ("" if none). */
 const char* tto_last_error(void);

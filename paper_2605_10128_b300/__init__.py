@@ -12,6 +12,7 @@ import numpy as np
 from . import _lib
 from ._lib import (  # noqa: F401
     TTOError, PREC_FP32, PREC_BF16X3, PREC_BF16, PREC_TF32X3, PREC_FP16X3, FIT_WORKLOAD, FIT_F1,
+    SCREEN_SCORE, SCREEN_CELL_GAIN,
 )
 
 DEFAULT_MUTATION = (0.2, 0.2, 0.5, 0.1, 2.0)  # p_add, p_remove, p_change, p_identity, N_mutmean
@@ -161,15 +162,15 @@ class Archive:
         _lib.tto_mapelites_step(self._h, seed, iteration, B, mutation, o, topo_out, fitness_out,
                                 _stream(stream))
 
-    def step_screened(self, surrogate, seed, iteration, n_propose, n_exact,
+    def step_screened(self, surrogate, seed, iteration, n_propose, n_exact, rank_by=SCREEN_SCORE,
                       mutation=DEFAULT_MUTATION, precision=PREC_FP32, fitness_kind=FIT_WORKLOAD,
                       train_steps=1, topo_out=None, fitness_out=None, score_out=None, stream=None):
         """One surrogate-screened iteration: propose n_propose, evaluate the
-        n_exact best-scored exactly, insert, learn from them."""
+        n_exact ranked first exactly, insert, learn from them."""
         o = _lib.EvalOpts(precision, fitness_kind, self.d_split, self.d_moved)
         _lib.tto_mapelites_step_screened(self._h, surrogate.handle, seed, iteration, n_propose,
-                                         n_exact, mutation, o, train_steps, topo_out, fitness_out,
-                                         score_out, _stream(stream))
+                                         n_exact, rank_by, mutation, o, train_steps, topo_out,
+                                         fitness_out, score_out, _stream(stream))
 
 
 class Surrogate:

@@ -56,6 +56,7 @@ class EvalJob(C.Structure):
 
 
 MULTI_SEQUENTIAL, MULTI_STREAMS, MULTI_GRAPH = 0, 1, 2
+SCREEN_SCORE, SCREEN_CELL_GAIN = 0, 1
 
 
 class MutParams(C.Structure):
@@ -108,7 +109,7 @@ _SIGS = {
     "tto_surrogate_add": ([_vp, _vp, C.c_int32, _vp, _vp], C.c_int),
     "tto_surrogate_train": ([_vp, C.c_int32, C.POINTER(C.c_float), _vp], C.c_int),
     "tto_surrogate_grad": ([_vp, _vp, C.c_int32, _vp, C.POINTER(C.c_float), _vp, _vp], C.c_int),
-    "tto_mapelites_step_screened": ([_vp, _vp, C.c_uint64, C.c_uint64, C.c_int32, C.c_int32,
+    "tto_mapelites_step_screened": ([_vp, _vp, C.c_uint64, C.c_uint64, C.c_int32, C.c_int32, C.c_int32,
                                      C.POINTER(MutParams), C.POINTER(EvalOpts), C.c_int32, _vp, _vp,
                                      _vp, _vp], C.c_int),
     "tto_last_error": ([], C.c_char_p),
@@ -422,11 +423,11 @@ def tto_surrogate_grad(h, topo, B, fitness, n_params, stream):
     return loss.value, grad
 
 
-def tto_mapelites_step_screened(a, s, seed, iteration, n_propose, n_exact, mut, opts, train_steps,
-                                topo_out, fitness_out, score_out, stream):
+def tto_mapelites_step_screened(a, s, seed, iteration, n_propose, n_exact, rank_by, mut, opts,
+                                train_steps, topo_out, fitness_out, score_out, stream):
     m = _mut(mut)
     return check(lib().tto_mapelites_step_screened(a, s, int(seed), int(iteration), int(n_propose),
-                                                   int(n_exact), C.byref(m), C.byref(opts),
+                                                   int(n_exact), int(rank_by), C.byref(m), C.byref(opts),
                                                    int(train_steps), _dp(topo_out), _dp(fitness_out),
                                                    _dp(score_out), _vp(stream)))
 

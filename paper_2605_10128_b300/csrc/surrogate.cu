@@ -46,6 +46,7 @@ struct tto_surrogate {
   float* Am = nullptr;    // Adam first moment
   float* Av = nullptr;    // Adam second moment
   float* W1sT = nullptr;  // [8S][H] station block of W1, transposed (refreshed after every update)
+  float* wsk = nullptr;   // split-K partials of the weight gradients
   int* rows = nullptr;    // [R] branch ids of the loading features
   double* row_lim = nullptr;  // [R] their thermal limits
   double* Nsr = nullptr;  // [n_sw][R] N[rows[r]][movable branch] (the movable columns at those rows)
@@ -56,6 +57,7 @@ struct tto_surrogate {
   float* SF = nullptr;    // [bcap][k][8] that station's eight values
   float* XD = nullptr;    // [bcap][R] loadings
   int* valid = nullptr;   // [bcap] 0 = the split islands the grid (or the genome is invalid)
+  int2* nsm = nullptr;    // [bcap] descriptors: split stations, moved assets
   float *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *Y = nullptr;
   float *dH1 = nullptr, *dH2 = nullptr, *dH3 = nullptr, *dY = nullptr, *T = nullptr;
   int32_t* mb_topo = nullptr;  // [bcap][k] genomes of a training minibatch
@@ -71,6 +73,7 @@ struct tto_surrogate {
   int32_t* prop = nullptr;              // [pcap][k] proposals
   unsigned long long* keys = nullptr;   // [keys_n] (score, index) sort keys
   int keys_n = 0;
+  int32_t* sel = nullptr;               // [pcap] proposals chosen for exact evaluation
 };
 
 namespace tto {
@@ -88,12 +91,15 @@ __device__ __forceinline__ float bf(float x) { return __bfloat162float(__float2b
 // opA(m, k) = TA ? A[k lda + m] : A[m lda + k];
 // opB(k, n) = TB ? B[n ldb + k] : B[k ldb + n].
 // 64x64 output tile per 128-thread CTA (2x2 warps of 32x32), K in steps of 32;
-// operands are rounded to BF16 when staged in shared memory.
+// operands are rounded to BF16 when staged in shared memory.  Split K:
+// blockIdx.z covers k in [z kc, z kc + kc) and writes its partial product to
+// C + z c_split (bias, mask and relu only without a split).
 template <bool TA, bool TB>
 __global__ void __launch_bounds__(128) gemm_bf16_kernel(int M, int N, int K, const float* __restrict__ A,
                                                         int lda, const float* __restrict__ B, int ldb,
                                                         float* C, int ldc, const float* __restrict__ bias,
-                                                        const float* __restrict__ mask, int relu) {
+                                                        const float* __restrict__ mask, int relu, int kc,
+                                                        size_t c_split) {
   __shared__ __align__(16) __nv_bfloat16 As[kBM][kPadK];
   __shared__ __align__(16) __nv_bfloat16 Bs[kBN][kPadK];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, q = lane & 3;
@@ -106,20 +112,22 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(int M, int N, int K, con
     for (int j = 0; j < 4; ++j)
 #pragma unroll
       for (int r = 0; r < 4; ++r) d[i][j][r] = 0.f;
-  for (int k0 = 0; k0 < K; k0 += kBK) {
+  const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
+  C += blockIdx.z * c_split;
+  for (int k0 = kb; k0 < ke; k0 += kBK) {
     // consecutive threads read consecutive global addresses in both layouts
     for (int e = tid; e < kBM * kBK; e += 128) {
       const int r = TA ? e % kBM : e / kBK, c = TA ? e / kBM : e % kBK;
       const int m = m0 + r, kk = k0 + c;
       float v = 0.f;
-      if (m < M && kk < K) v = TA ? A[(size_t)kk * lda + m] : A[(size_t)m * lda + kk];
+      if (m < M && kk < ke) v = TA ? A[(size_t)kk * lda + m] : A[(size_t)m * lda + kk];
       As[r][c] = __float2bfloat16_rn(v);
     }
     for (int e = tid; e < kBN * kBK; e += 128) {
       const int r = TB ? e / kBK : e % kBN, c = TB ? e % kBK : e / kBN;
       const int n = n0 + r, kk = k0 + c;
       float v = 0.f;
-      if (n < N && kk < K) v = TB ? B[(size_t)n * ldb + kk] : B[(size_t)kk * ldb + n];
+      if (n < N && kk < ke) v = TB ? B[(size_t)n * ldb + kk] : B[(size_t)kk * ldb + n];
       Bs[r][c] = __float2bfloat16_rn(v);
     }
     __syncthreads();
@@ -176,7 +184,39 @@ int gemm(int M, int N, int K, const float* A, int lda, const float* B, int ldb, 
   if (M <= 0 || N <= 0) return TTO_OK;
   const dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM);
   if (grid.y > 65535) return set_error(TTO_E_ARG, "surrogate batch too large for one product");
-  gemm_bf16_kernel<TA, TB><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, mask, relu ? 1 : 0);
+  gemm_bf16_kernel<TA, TB><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, mask, relu ? 1 : 0, K, 0);
+  TTO_CUDA_TRY(cudaGetLastError());
+  return TTO_OK;
+}
+
+// out[m][n] (ldo) = sum over z in order of part[z][m][n]
+__global__ void splitk_reduce_kernel(int M, int N, int splits, const float* part, float* out, int ldo) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)M * N) return;
+  float v = 0.f;
+  for (int z = 0; z < splits; ++z) v += part[(size_t)z * M * N + i];
+  out[(i / N) * ldo + i % N] = v;
+}
+
+constexpr int kMaxSplitK = 16;
+
+// Weight gradient C[M][N] (ldc) = A^T B over K batch rows (A [K][M], B [K][N]):
+// few output tiles and a long K, so K is split over up to 16 CTAs per tile
+// whose partials (in ws, kMaxSplitK * M * N floats) are summed in a fixed order.
+int gemm_wgrad(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc, float* ws,
+               cudaStream_t s) {
+  if (M <= 0 || N <= 0) return TTO_OK;
+  const int tiles = ((N + kBN - 1) / kBN) * ((M + kBM - 1) / kBM);
+  int splits = std::max(1, std::min(kMaxSplitK, (4 * 148 + tiles - 1) / tiles));
+  splits = std::max(1, std::min(splits, (K + 255) / 256));
+  const int kc = ((K + splits - 1) / splits + kBK - 1) / kBK * kBK;
+  splits = (K + kc - 1) / kc;
+  if (splits <= 1) return gemm<true, false>(M, N, K, A, lda, B, ldb, C, ldc, nullptr, nullptr, false, s);
+  const dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM, splits);
+  gemm_bf16_kernel<true, false><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, ws, N, nullptr, nullptr, 0, kc,
+                                                     (size_t)M * N);
+  const size_t n = (size_t)M * N;
+  splitk_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(M, N, splits, ws, C, ldc);
   TTO_CUDA_TRY(cudaGetLastError());
   return TTO_OK;
 }
@@ -205,6 +245,7 @@ struct FeatArgs {
   float* SF;
   float* XD;
   int* valid;
+  int2* nsm;
 };
 
 // One CTA per genome.  Decodes the genome as the evaluation does (an
@@ -215,14 +256,14 @@ struct FeatArgs {
 // loading rows.
 __global__ void __launch_bounds__(128) features_kernel(FeatArgs a) {
   const int bi = blockIdx.x, tid = threadIdx.x;
-  __shared__ int s_k, s_isl;
+  __shared__ int s_k, s_isl, s_nm;
   __shared__ int s_slot[TTO_MAX_K + 1];
   __shared__ int s_e[kMaxMoved], s_sw[kMaxMoved];
   __shared__ double s_sign[kMaxMoved], s_coef[kMaxMoved];
   __shared__ int s_injbus[TTO_MAX_K];
   __shared__ double s_K[TTO_MAX_K][TTO_MAX_K], s_rhs[TTO_MAX_K], s_psi[TTO_MAX_K], s_sb[TTO_MAX_K];
   if (tid == 0) {
-    int k = 0, ne = 0, bad = 0;
+    int k = 0, ne = 0, bad = 0, nm = 0;
     int seen[TTO_MAX_K];
     s_slot[0] = 0;
     for (int j = 0; j < a.k; ++j) {
@@ -245,6 +286,7 @@ __global__ void __launch_bounds__(128) features_kernel(FeatArgs a) {
       const uint32_t mask = a.act_mask[act];
       const int bus = a.station_bus[st], a0 = a.asset_off[st], m = a.asset_off[st + 1] - a0;
       const int nb = __popc(mask);
+      nm += min(nb, m - nb);
       double b_all = 0.0, b_b = 0.0, pb = 0.0;
       int br = 0, br_b = 0;
       s_injbus[k] = -1;
@@ -285,8 +327,10 @@ __global__ void __launch_bounds__(128) features_kernel(FeatArgs a) {
       for (int j = 0; j < a.k; ++j) a.SI[(size_t)bi * a.k + j] = -1;
     s_k = bad ? 0 : k;
     s_isl = bad;
+    s_nm = nm;
   }
   __syncthreads();
+  if (tid == 0) a.nsm[bi] = make_int2(s_k, s_nm);
   if (!a.with_loads) {
     if (tid == 0) a.valid[bi] = s_isl ? 0 : 1;
     return;
@@ -496,40 +540,58 @@ __global__ void __launch_bounds__(1024) colsum_kernel(int M, int N, const float*
 }
 
 // Gradient of the station block of W1: one CTA per station s,
-// G1[h][8 s + c] = sum over genome slots holding s (in row order) of
-// dH1[row][h] f_c.  The slots of s are compacted in order, 256 at a time.
+// G1[h][8 s + c] = sum over genome slots holding s (in slot order) of
+// dH1[row][h] f_c.  Each thread counts the hits in its contiguous share of
+// the slots; an exclusive scan of the counts gives every hit its position in
+// slot order; the hits are then staged in shared memory 1024 at a time and
+// accumulated by all threads, two hidden units each (H <= 1024: four).
+constexpr int kGradList = 1024;
 __global__ void __launch_bounds__(256) station_grad_kernel(int M, int H, int D, int k, const int* SI,
                                                            const float* SF, const float* dH1, float* G1) {
-  const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  __shared__ int s_row[256];
-  __shared__ float s_f[256][8];
-  __shared__ int s_wcnt[8];
+  const int s = blockIdx.x, tid = threadIdx.x;
+  __shared__ int s_row[kGradList];
+  __shared__ float s_f[kGradList][8];
+  __shared__ int s_cnt[256];
+  __shared__ int s_total;
+  const int n_ent = M * k;
+  const int per = (n_ent + 255) / 256;
+  const int e0 = min(n_ent, tid * per), e1 = min(n_ent, e0 + per);
+  int cnt = 0;
+  for (int e = e0; e < e1; ++e) cnt += SI[e] == s ? 1 : 0;
+  s_cnt[tid] = cnt;
+  __syncthreads();
+  if (tid == 0) {
+    int run = 0;
+    for (int i = 0; i < 256; ++i) {
+      const int c = s_cnt[i];
+      s_cnt[i] = run;
+      run += c;
+    }
+    s_total = run;
+  }
+  __syncthreads();
+  const int total = s_total, off = s_cnt[tid];
   float acc[kMaxHidden / 256][8];
 #pragma unroll
   for (int u = 0; u < kMaxHidden / 256; ++u)
 #pragma unroll
     for (int c = 0; c < 8; ++c) acc[u][c] = 0.f;
-  const int n_ent = M * k;
-  for (int base = 0; base < n_ent; base += 256) {
-    const int e = base + tid;
-    const bool hit = e < n_ent && SI[e] == s;
-    const unsigned bal = __ballot_sync(0xffffffffu, hit);
-    if (lane == 0) s_wcnt[warp] = __popc(bal);
-    __syncthreads();
-    int off = 0, tot = 0;
+  for (int base = 0; base < total; base += kGradList) {
+    if (cnt > 0 && off < base + kGradList && off + cnt > base) {
+      int pos = off;
+      for (int e = e0; e < e1 && pos < base + kGradList; ++e) {
+        if (SI[e] != s) continue;
+        if (pos >= base) {
+          s_row[pos - base] = e / k;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) {
-      off += w < warp ? s_wcnt[w] : 0;
-      tot += s_wcnt[w];
-    }
-    if (hit) {
-      const int pos = off + __popc(bal & ((1u << lane) - 1u));
-      s_row[pos] = e / k;
-#pragma unroll
-      for (int c = 0; c < 8; ++c) s_f[pos][c] = bf(SF[(size_t)e * 8 + c]);
+          for (int c = 0; c < 8; ++c) s_f[pos - base][c] = bf(SF[(size_t)e * 8 + c]);
+        }
+        ++pos;
+      }
     }
     __syncthreads();
-    for (int i = 0; i < tot; ++i) {
+    const int nl = min(kGradList, total - base);
+    for (int i = 0; i < nl; ++i) {
       const float* dr = dH1 + (size_t)s_row[i] * H;
 #pragma unroll
       for (int u = 0; u < kMaxHidden / 256; ++u) {
@@ -566,18 +628,54 @@ __global__ void adam_kernel(size_t n, float* P, const float* G, float* m, float*
 }
 
 // ------------------------------------------------------------------ top-k
-// Sort keys (orderable score bits << 32 | proposal index), ascending: the best
-// predicted scores first, ties by index; NaN scores rank as +inf.
+// Unsigned integer with the order of the float (after -0 -> +0).
 __device__ __forceinline__ uint32_t orderable(float f) {
   const uint32_t u = __float_as_uint(f + 0.0f);  // -0 -> +0
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-__global__ void keys_kernel(int n, int npad, const float* Y, unsigned long long* keys) {
+// Screening keys (ascending = evaluated first), 64 bits: a flag, the
+// orderable bits of a float, and the proposal index (31 bits).
+// by_gain = 0: flag 0 and the predicted log1p(-fitness);
+// by_gain = 1: flag 0 and the predicted log1p(-fitness) for a proposal whose
+// descriptors map to an empty archive cell, flag 1 and the predicted
+// improvement over the cell's elite, y - log1p(-fitness_elite) (FP64, then
+// rounded), for a filled one.
+// Either way +inf with flag 1 for a proposal that islands the grid or equals
+// its cell's elite slot for slot (evaluated already; its score is reported as
+// +inf).  Padding entries are all ones.
+__global__ void screen_keys_kernel(int n, int npad, int k, int by_gain, const int32_t* prop, const int2* nsm,
+                                   int d_split, int d_moved, const int32_t* elite, const float* elite_fit,
+                                   const uint8_t* filled, float* Y, unsigned long long* keys) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= npad) return;
-  keys[i] = i < n ? (((unsigned long long)orderable(isnan(Y[i]) ? INFINITY : Y[i]) << 32) | (uint32_t)i)
-                  : ~0ull;
+  if (i >= n) {
+    keys[i] = ~0ull;
+    return;
+  }
+  float y = Y[i];
+  unsigned long long flag = 1;
+  float key = INFINITY;
+  if (!isnan(y) && isfinite(y)) {
+    const int2 d = nsm[i];
+    const int cell = min(d.x, d_split - 1) * d_moved + min(d.y, d_moved - 1);
+    if (!filled[cell]) {
+      flag = 0;
+      key = y;
+    } else {
+      bool same = true;
+      for (int j = 0; j < k && same; ++j) same = prop[(size_t)i * k + j] == elite[(size_t)cell * k + j];
+      if (same) {
+        Y[i] = INFINITY;
+      } else if (by_gain) {
+        key = (float)((double)y - log1p(-(double)elite_fit[cell]));
+      } else {
+        flag = 0;
+        key = y;
+      }
+    }
+  }
+  keys[i] = (flag << 63) | ((unsigned long long)orderable(key) << 31) | (unsigned long long)(uint32_t)i;
 }
 
 // One compare-exchange stage (kk, jj) of the bitonic network over the array.
@@ -618,16 +716,57 @@ __global__ void __launch_bounds__(1024) bitonic_shared_kernel(int kk_from, unsig
   keys[base + t + 1024] = s[t + 1024];
 }
 
-__global__ void gather_topo_kernel(int n, int k, const unsigned long long* keys, const int32_t* src, int32_t* dst) {
+__global__ void gather_topo_kernel(int n, int k, const int32_t* sel, const int32_t* src, int32_t* dst) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const size_t j = (size_t)(keys[i] & 0xffffffffu);
+  const size_t j = (size_t)sel[i];
   for (int c = 0; c < k; ++c) dst[(size_t)i * k + c] = src[j * k + c];
 }
 
-__global__ void gather_score_kernel(int n, const unsigned long long* keys, const float* Y, float* out) {
+__global__ void gather_score_kernel(int n, const int32_t* sel, const float* Y, float* out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = Y[keys[i] & 0xffffffffu];
+  if (i < n) out[i] = Y[sel[i]];
+}
+
+__device__ __forceinline__ uint32_t key_index(unsigned long long key) { return (uint32_t)(key & 0x7fffffffull); }
+
+__device__ __forceinline__ bool same_genome(const int32_t* prop, int k, uint32_t x, uint32_t y) {
+  for (int j = 0; j < k; ++j)
+    if (prop[(size_t)x * k + j] != prop[(size_t)y * k + j]) return false;
+  return true;
+}
+
+// One CTA: walks the sorted keys and writes to sel the proposal indices of the
+// first n_keep entries of the stable partition [entries whose genome differs
+// from their predecessor's | the repeats].  Equal genomes have equal keys
+// (apart from the index), so repeats are adjacent in the sorted order.
+__global__ void __launch_bounds__(1024) select_kernel(int n, int n_keep, int k, const unsigned long long* keys,
+                                                      const int32_t* prop, int32_t* sel) {
+  __shared__ int s_cnt[1024];
+  __shared__ int s_total;
+  const int t = threadIdx.x, per = (n + 1023) / 1024;
+  const int p0 = min(n, t * per), p1 = min(n, p0 + per);
+  int uniq = 0;
+  for (int p = p0; p < p1; ++p)
+    uniq += (p == 0 || !same_genome(prop, k, key_index(keys[p]), key_index(keys[p - 1]))) ? 1 : 0;
+  s_cnt[t] = uniq;
+  __syncthreads();
+  if (t == 0) {
+    int run = 0;
+    for (int i = 0; i < 1024; ++i) {
+      const int c = s_cnt[i];
+      s_cnt[i] = run;
+      run += c;
+    }
+    s_total = run;
+  }
+  __syncthreads();
+  int u = s_cnt[t], r = s_total + (p0 - s_cnt[t]);  // repeats before p0 = p0 - uniques before p0
+  for (int p = p0; p < p1; ++p) {
+    const bool first = p == 0 || !same_genome(prop, k, key_index(keys[p]), key_index(keys[p - 1]));
+    const int dst = first ? u++ : r++;
+    if (dst < n_keep) sel[dst] = (int32_t)key_index(keys[p]);
+  }
 }
 
 // ------------------------------------------------------------------ replay
@@ -702,14 +841,14 @@ __global__ void targets_kernel(int n, const float* fit, const float* stats, floa
 }
 
 // Append n pairs at the ring head: genome i, the loadings of batch row
-// (keys ? the index in keys[i] : i), target log1p(-fitness) or NaN.
+// (idx ? idx[i] : i), target log1p(-fitness) or NaN.
 __global__ void replay_append_kernel(int n, int k, int R, int cap, int head, const int32_t* topo,
-                                     const unsigned long long* keys, const float* XD, const float* fit,
+                                     const int32_t* idx, const float* XD, const float* fit,
                                      int32_t* rg, float* rx, float* rt) {
   const int i = blockIdx.x;
   if (i >= n) return;
   const size_t slot = (size_t)((head + i) % cap);
-  const size_t src = keys ? (size_t)(keys[i] & 0xffffffffu) : (size_t)i;
+  const size_t src = idx ? (size_t)idx[i] : (size_t)i;
   for (int r = threadIdx.x; r < R; r += blockDim.x) rx[slot * R + r] = XD[src * R + r];
   if (threadIdx.x < k) rg[slot * k + threadIdx.x] = topo[(size_t)i * k + threadIdx.x];
   if (threadIdx.x == 0) rt[slot] = raw_target(fit[i]);
@@ -736,13 +875,14 @@ __global__ void sample_kernel(int M, int n_rep, int k, int R, uint2 key, uint32_
 // ------------------------------------------------------------------ host side
 int alloc_batch(tto_surrogate* s, int B) {
   if (B <= s->bcap) return TTO_OK;
-  void* old[] = {s->SI, s->SF, s->XD, s->valid, s->H1, s->H2, s->H3, s->Y, s->dH1, s->dH2, s->dH3, s->dY, s->T,
-                 s->mb_topo};
+  void* old[] = {s->SI, s->SF, s->XD, s->valid, s->nsm, s->H1, s->H2, s->H3, s->Y, s->dH1, s->dH2, s->dH3, s->dY,
+                 s->T, s->mb_topo};
   for (void* p : old)
     if (p) cudaFree(p);
   s->SI = nullptr;
   s->SF = s->XD = s->H1 = s->H2 = s->H3 = s->Y = s->dH1 = s->dH2 = s->dH3 = s->dY = s->T = nullptr;
   s->valid = nullptr;
+  s->nsm = nullptr;
   s->mb_topo = nullptr;
   s->bcap = 0;
   const size_t b = B, H = s->H;
@@ -750,6 +890,7 @@ int alloc_batch(tto_surrogate* s, int B) {
   TTO_CUDA_TRY(cudaMalloc(&s->SF, b * s->k * 8 * sizeof(float)));
   TTO_CUDA_TRY(cudaMalloc(&s->XD, b * s->R * sizeof(float)));
   TTO_CUDA_TRY(cudaMalloc(&s->valid, b * sizeof(int)));
+  TTO_CUDA_TRY(cudaMalloc(&s->nsm, b * sizeof(int2)));
   TTO_CUDA_TRY(cudaMalloc(&s->H1, b * H * sizeof(float)));
   TTO_CUDA_TRY(cudaMalloc(&s->H2, b * H * sizeof(float)));
   TTO_CUDA_TRY(cudaMalloc(&s->H3, b * H * sizeof(float)));
@@ -792,6 +933,7 @@ FeatArgs feat_args(const tto_surrogate* s, const int32_t* topo, int with_loads) 
   a.SF = s->SF;
   a.XD = s->XD;
   a.valid = s->valid;
+  a.nsm = s->nsm;
   return a;
 }
 
@@ -843,15 +985,13 @@ int backward(tto_surrogate* s, int M, cudaStream_t st) {
   out_back_kernel<<<nb, 256, 0, st>>>(M, H, s->dY, P + s->ow4, s->H3, s->dH3);
   TTO_CUDA_TRY(cudaGetLastError());
   int rc;
-  if ((rc = gemm<true, false>(H, H, M, s->dH3, H, s->H2, H, G + s->oW3, H, nullptr, nullptr, false, st))) return rc;
+  if ((rc = gemm_wgrad(H, H, M, s->dH3, H, s->H2, H, G + s->oW3, H, s->wsk, st))) return rc;
   colsum_kernel<<<ncs, cs, 0, st>>>(M, H, s->dH3, nullptr, G + s->ob3);
   if ((rc = gemm<false, false>(M, H, H, s->dH3, H, P + s->oW3, H, s->dH2, H, nullptr, s->H2, false, st))) return rc;
-  if ((rc = gemm<true, false>(H, H, M, s->dH2, H, s->H1, H, G + s->oW2, H, nullptr, nullptr, false, st))) return rc;
+  if ((rc = gemm_wgrad(H, H, M, s->dH2, H, s->H1, H, G + s->oW2, H, s->wsk, st))) return rc;
   colsum_kernel<<<ncs, cs, 0, st>>>(M, H, s->dH2, nullptr, G + s->ob2);
   if ((rc = gemm<false, false>(M, H, H, s->dH2, H, P + s->oW2, H, s->dH1, H, nullptr, s->H1, false, st))) return rc;
-  if ((rc = gemm<true, false>(H, R, M, s->dH1, H, s->XD, R, G + s->oW1 + 8 * (size_t)s->S, D, nullptr, nullptr,
-                              false, st)))
-    return rc;
+  if ((rc = gemm_wgrad(H, R, M, s->dH1, H, s->XD, R, G + s->oW1 + 8 * (size_t)s->S, D, s->wsk, st))) return rc;
   colsum_kernel<<<ncs, cs, 0, st>>>(M, H, s->dH1, nullptr, G + s->ob1);
   station_grad_kernel<<<s->S, 256, 0, st>>>(M, H, D, s->k, s->SI, s->SF, s->dH1, G + s->oW1);
   TTO_CUDA_TRY(cudaGetLastError());
@@ -900,10 +1040,14 @@ int train(tto_surrogate* s, int steps, float* loss_host, cudaStream_t st) {
   return TTO_OK;
 }
 
-// Sort the keys of the first n scores in s->Y (ascending).
-int rank(tto_surrogate* s, int n, cudaStream_t st) {
+int sort_pad(int n) {
   int npad = kSortChunk;
   while (npad < n) npad <<= 1;
+  return npad;
+}
+
+int ensure_keys(tto_surrogate* s, int n) {
+  const int npad = sort_pad(n);
   if (npad > s->keys_n) {
     if (s->keys) cudaFree(s->keys);
     s->keys = nullptr;
@@ -911,7 +1055,12 @@ int rank(tto_surrogate* s, int n, cudaStream_t st) {
     TTO_CUDA_TRY(cudaMalloc(&s->keys, (size_t)npad * sizeof(unsigned long long)));
     s->keys_n = npad;
   }
-  keys_kernel<<<(npad + 255) / 256, 256, 0, st>>>(n, npad, s->Y, s->keys);
+  return TTO_OK;
+}
+
+// Sort the first sort_pad(n) keys in s->keys (ascending).
+int sort_keys(tto_surrogate* s, int n, cudaStream_t st) {
+  const int npad = sort_pad(n);
   const int chunks = npad / kSortChunk;
   bitonic_shared_kernel<<<chunks, 1024, 0, st>>>(0, s->keys);
   for (int kk = 2 * kSortChunk; kk <= npad; kk <<= 1) {
@@ -924,12 +1073,12 @@ int rank(tto_surrogate* s, int n, cudaStream_t st) {
 }
 
 // Append n pairs (genomes topo [n][k], fitness fit [n]) whose loadings are
-// batch rows keys[i] (or i) of s->XD.
-int append(tto_surrogate* s, const int32_t* topo, int n, const unsigned long long* keys, const float* XD,
-           const float* fit, cudaStream_t st) {
+// batch rows idx[i] (or i) of XD.
+int append(tto_surrogate* s, const int32_t* topo, int n, const int32_t* idx, const float* XD, const float* fit,
+           cudaStream_t st) {
   n = std::min(n, s->cap);
   if (n <= 0) return TTO_OK;
-  replay_append_kernel<<<n, 128, 0, st>>>(n, s->k, s->R, s->cap, s->rep_head, topo, keys, XD, fit, s->rep_genome,
+  replay_append_kernel<<<n, 128, 0, st>>>(n, s->k, s->R, s->cap, s->rep_head, topo, idx, XD, fit, s->rep_genome,
                                           s->rep_xd, s->rep_t);
   TTO_CUDA_TRY(cudaGetLastError());
   s->rep_head = (s->rep_head + n) % s->cap;
@@ -940,9 +1089,9 @@ int append(tto_surrogate* s, const int32_t* topo, int n, const unsigned long lon
 }
 
 void release(tto_surrogate* s) {
-  void* ptrs[] = {s->P,  s->G,     s->Am, s->Av, s->W1sT, s->rows, s->row_lim, s->Nsr, s->SI,  s->SF,
-                  s->XD, s->valid, s->H1, s->H2, s->H3,   s->Y,    s->dH1,     s->dH2, s->dH3, s->dY,
-                  s->T,  s->mb_topo, s->loss, s->stats, s->rep_genome, s->rep_xd, s->rep_t, s->prop, s->keys};
+  void* ptrs[] = {s->P,  s->G,     s->Am, s->Av, s->W1sT, s->wsk, s->rows, s->row_lim, s->Nsr, s->SI,  s->SF,
+                  s->XD, s->valid, s->nsm, s->H1, s->H2, s->H3, s->Y,    s->dH1,     s->dH2, s->dH3, s->dY,
+                  s->T,  s->mb_topo, s->loss, s->stats, s->rep_genome, s->rep_xd, s->rep_t, s->prop, s->keys, s->sel};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete s;
@@ -1033,6 +1182,7 @@ int tto_surrogate_create(tto_grid* g, const tto_surrogate_cfg* cfg, tto_surrogat
   A((void**)&s->Am, s->n_params * 4);
   A((void**)&s->Av, s->n_params * 4);
   A((void**)&s->W1sT, (size_t)8 * s->S * H * 4);
+  A((void**)&s->wsk, (size_t)kMaxSplitK * H * std::max(H, (size_t)s->R) * 4);
   A((void**)&s->rows, s->R * sizeof(int));
   A((void**)&s->row_lim, s->R * sizeof(double));
   A((void**)&s->Nsr, (size_t)std::max(g->n_sw, 1) * s->R * sizeof(double));
@@ -1175,12 +1325,14 @@ int tto_surrogate_grad(tto_surrogate* s, const int32_t* topo, int32_t B, const f
 }
 
 int tto_mapelites_step_screened(tto_archive* a, tto_surrogate* s, uint64_t seed, uint64_t iteration,
-                                int32_t n_propose, int32_t n_exact, const tto_mut_params* mp,
+                                int32_t n_propose, int32_t n_exact, int32_t rank_by, const tto_mut_params* mp,
                                 const tto_eval_opts* opts, int32_t train_steps, int32_t* topo_out,
                                 float* fitness_out, float* score_out, void* stream) {
   if (!a || !s || !mp || !opts || a->g != s->g) return set_error(TTO_E_ARG, "bad screened-step arguments");
   if (n_exact < 1 || n_propose < n_exact) return set_error(TTO_E_ARG, "need 1 <= n_exact <= n_propose");
+  if (n_propose > (1 << 30)) return set_error(TTO_E_ARG, "n_propose must be at most 2^30");
   if (train_steps < 0) return set_error(TTO_E_ARG, "train_steps must be >= 0");
+  if (rank_by != TTO_SCREEN_SCORE && rank_by != TTO_SCREEN_CELL_GAIN) return set_error(TTO_E_ARG, "unknown rank_by");
   if (opts->d_split != a->d_split || opts->d_moved != a->d_moved)
     return set_error(TTO_E_ARG, "evaluation cell extents differ from the archive's");
   tto_grid* g = a->g;
@@ -1191,9 +1343,12 @@ int tto_mapelites_step_screened(tto_archive* a, tto_surrogate* s, uint64_t seed,
   if (rc) return rc;
   if (n_propose > s->pcap) {
     if (s->prop) cudaFree(s->prop);
+    if (s->sel) cudaFree(s->sel);
     s->prop = nullptr;
+    s->sel = nullptr;
     s->pcap = 0;
     TTO_CUDA_TRY(cudaMalloc(&s->prop, (size_t)n_propose * g->k_max * sizeof(int32_t)));
+    TTO_CUDA_TRY(cudaMalloc(&s->sel, (size_t)n_propose * sizeof(int32_t)));
     s->pcap = n_propose;
   }
   // one allocation for scoring and training, so neither invalidates the other
@@ -1207,14 +1362,21 @@ int tto_mapelites_step_screened(tto_archive* a, tto_surrogate* s, uint64_t seed,
     valid_only_kernel<<<(n_propose + 255) / 256, 256, 0, st>>>(n_propose, s->valid, s->Y);
     TTO_CUDA_TRY(cudaGetLastError());
   }
-  if ((rc = rank(s, n_propose, st))) return rc;
-  gather_topo_kernel<<<(n_exact + 255) / 256, 256, 0, st>>>(n_exact, g->k_max, s->keys, s->prop, w.topo);
-  if (score_out) gather_score_kernel<<<(n_exact + 255) / 256, 256, 0, st>>>(n_exact, s->keys, s->Y, score_out);
+  if ((rc = ensure_keys(s, n_propose))) return rc;
+  const int npad = sort_pad(n_propose);
+  screen_keys_kernel<<<(npad + 255) / 256, 256, 0, st>>>(n_propose, npad, g->k_max, rank_by, s->prop, s->nsm,
+                                                         a->d_split, a->d_moved, a->d_genome, a->d_fit,
+                                                         a->d_filled, s->Y, s->keys);
+  TTO_CUDA_TRY(cudaGetLastError());
+  if ((rc = sort_keys(s, n_propose, st))) return rc;
+  select_kernel<<<1, 1024, 0, st>>>(n_propose, n_exact, g->k_max, s->keys, s->prop, s->sel);
+  gather_topo_kernel<<<(n_exact + 255) / 256, 256, 0, st>>>(n_exact, g->k_max, s->sel, s->prop, w.topo);
+  if (score_out) gather_score_kernel<<<(n_exact + 255) / 256, 256, 0, st>>>(n_exact, s->sel, s->Y, score_out);
   TTO_CUDA_TRY(cudaGetLastError());
   rc = evaluate_impl(g, w.topo, n_exact, nullptr, g->T, opts, w.fit, w.desc, w.cell, w.island, nullptr, nullptr, st);
   if (rc) return rc;
   if ((rc = insert_impl(a, w.topo, n_exact, w.fit, w.cell, st))) return rc;
-  if ((rc = append(s, w.topo, n_exact, s->keys, s->XD, w.fit, st))) return rc;
+  if ((rc = append(s, w.topo, n_exact, s->sel, s->XD, w.fit, st))) return rc;
   if (train_steps > 0 && (rc = train(s, train_steps, nullptr, st))) return rc;
   if (topo_out)
     TTO_CUDA_TRY(cudaMemcpyAsync(topo_out, w.topo, (size_t)n_exact * g->k_max * sizeof(int32_t),

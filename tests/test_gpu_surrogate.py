@@ -234,9 +234,40 @@ def _archive_seeded(sg, g, d_split, d_moved, seed):
     return a
 
 
+def _expected_selection(sg, archive, prop, sc, n_ex, by_gain=True, d_split=8, d_moved=8):
+    """Reference of the screened step's choice.  by_gain: empty-cell
+    proposals first by score, then the rest by predicted improvement over
+    their cell's elite; else all by score.  Ties by index; elite copies and
+    islanding proposals last; then the stable partition [genome differs from
+    its predecessor's | repeats]."""
+    efit, gen, filled = archive.export()
+    sc = np.where(np.isnan(sc), np.inf, sc).astype(np.float32)
+    flag = np.ones(len(prop), dtype=np.int64)
+    key = np.full(len(prop), np.inf, dtype=np.float32)
+    for i, p in enumerate(prop):
+        if not np.isfinite(sc[i]):
+            continue
+        _, _, cell = dcflow.descriptors(sg, p, d_split, d_moved)
+        if not filled[cell]:
+            flag[i], key[i] = 0, sc[i]
+        elif np.array_equal(gen[cell], p):
+            sc[i] = np.inf
+        elif by_gain:
+            key[i] = np.float32(np.float64(sc[i]) - np.log1p(-np.float64(efit[cell])))
+        else:
+            flag[i], key[i] = 0, sc[i]
+    order = np.lexsort((np.arange(len(prop)), key, flag))
+    first = [order[0]] + [order[j] for j in range(1, len(order))
+                          if not np.array_equal(prop[order[j]], prop[order[j - 1]])]
+    fs = set(first)
+    rest = [o for o in order if o not in fs]
+    return np.array((first + rest)[:n_ex]), sc
+
+
 def test_topk_selection_and_scores(g2k):
-    """The screened step evaluates exactly the n_exact proposals of lowest
-    predicted score (ties by proposal index) and reports their scores."""
+    """The screened step evaluates the n_exact proposals of lowest predicted
+    score (ties by proposal index), elite copies last and repeats after the
+    others, and reports their scores."""
     from paper_2605_10128_b300 import DEFAULT_MUTATION
     sg, g = g2k
     s = _surrogate(g)
@@ -246,17 +277,24 @@ def test_topk_selection_and_scores(g2k):
     s.add(td, out["fitness"])
     s.train(3, want_loss=False)
     a = _archive_seeded(sg, g, 8, 8, 16)
-    for n_prop, n_ex in [(5000, 700), (2048, 2048), (3, 1), (65536, 8192)]:
+    from paper_2605_10128_b300 import SCREEN_SCORE, SCREEN_CELL_GAIN
+    for n_prop, n_ex, mode in [(5000, 700, SCREEN_CELL_GAIN), (2048, 2048, SCREEN_SCORE), (3, 1, SCREEN_CELL_GAIN),
+                               (65536, 8192, SCREEN_SCORE), (65536, 8192, SCREEN_CELL_GAIN)]:
         prop = a.propose(77, 5, n_prop, DEFAULT_MUTATION)
         sc = s.score(prop).cpu().numpy()
         k = g.k_max
         topo_out = torch.empty(n_ex, k, dtype=torch.int32, device="cuda")
         sc_out = torch.empty(n_ex, dtype=torch.float32, device="cuda")
         a2 = _archive_seeded(sg, g, 8, 8, 16)  # same archive state, fresh copy
-        a2.step_screened(s, 77, 5, n_prop, n_ex, train_steps=0, topo_out=topo_out, score_out=sc_out)
-        order = np.lexsort((np.arange(n_prop), np.where(np.isnan(sc), np.inf, sc)))[:n_ex]
-        assert np.array_equal(topo_out.cpu().numpy(), prop.cpu().numpy()[order]), (n_prop, n_ex)
-        assert np.array_equal(sc_out.cpu().numpy(), sc[order])
+        pn = prop.cpu().numpy()
+        sel, sc_x = _expected_selection(sg, a2, pn, sc, n_ex, by_gain=mode == SCREEN_CELL_GAIN)
+        a2.step_screened(s, 77, 5, n_prop, n_ex, rank_by=mode, train_steps=0, topo_out=topo_out,
+                         score_out=sc_out)
+        assert np.array_equal(topo_out.cpu().numpy(), pn[sel]), (n_prop, n_ex)
+        assert np.array_equal(sc_out.cpu().numpy(), sc_x[sel])  # elite copies report +inf
+        n_copies = int(np.sum(np.isinf(sc_x) & np.isfinite(sc)))
+        print(f"\n{n_prop} proposals: {n_copies} elite copies, "
+              f"{n_prop - len(set(map(tuple, pn)))} repeated genomes")
         a2.close()
 
 
@@ -267,10 +305,11 @@ def test_untrained_screen_keeps_first_valid(g30):
     a = _archive_seeded(sg, g, 8, 8, 17)
     prop = a.propose(5, 1, 400, DEFAULT_MUTATION).cpu().numpy()
     ok = np.array([dcflow.is_connected_uf(*dcflow.post_split_graph(sg, p)[:3]) for p in prop])
+    sc = np.where(ok, 0.0, np.inf).astype(np.float32)
+    sel, _ = _expected_selection(sg, a, prop, sc, 100, by_gain=False)
     topo_out = torch.empty(100, g.k_max, dtype=torch.int32, device="cuda")
     a.step_screened(s, 5, 1, 400, 100, train_steps=0, topo_out=topo_out)
-    keep = np.nonzero(ok)[0][:100]
-    assert np.array_equal(topo_out.cpu().numpy(), prop[keep])
+    assert np.array_equal(topo_out.cpu().numpy(), prop[sel])
     assert s.replay_fill() == 100
 
 
