@@ -157,8 +157,9 @@ int tto_evaluate_batch(tto_grid* g, const int32_t* topo, int32_t B, const int32_
  * sweep has no data-dependent work, so the timing holds for any batch of that
  * size) and keep the fastest for later calls on this grid with that
  * precision.  *shape_out receives the chosen variant, ms_out (host, may be
- * NULL) the milliseconds of one evaluation per variant (2 variants for
- * TTO_PREC_FP32, 3 for the tensor-core modes).  Synchronises the stream.
+ * NULL, room for 8) the milliseconds of one evaluation per variant: 2 variants
+ * for TTO_PREC_FP32, 4 for the mma.sync tensor-core modes, and for
+ * TTO_PREC_TF32X3 a fifth, the tcgen05 sweep.  Synchronises the stream.
  * Call it outside stream capture (it may allocate workspace). */
 int tto_grid_autotune(tto_grid* g, int32_t B, int32_t n_t, int32_t precision, int32_t* shape_out,
                       float* ms_out, void* stream);

@@ -252,9 +252,14 @@ def tto_evaluate_batch_static(h, topo, B, timesteps, opts, fitness, desc, cell, 
 
 def tto_grid_autotune(h, B, n_t, precision, stream):
     shape = C.c_int32()
-    ms = (C.c_float * 4)()
+    ms = (C.c_float * 8)()
     check(lib().tto_grid_autotune(h, int(B), int(n_t), int(precision), C.byref(shape), ms, _vp(stream)))
-    return shape.value, list(ms)
+    return shape.value, list(ms)[:_n_shapes(precision)]
+
+
+def _n_shapes(precision):
+    """Sweep tile variants per precision mode (see tto_grid_autotune)."""
+    return 2 if precision == PREC_FP32 else (5 if precision == PREC_TF32X3 else 4)
 
 
 def tto_grid_set_sweep_shape(h, precision, shape):

@@ -175,7 +175,9 @@ int launch_sweep_fp32(const EvalArgs& a, cudaStream_t s) {
   return set_error(TTO_E_ARG, "unsupported padded rank %d", a.KP);
 }
 
-int sweep_shapes(int precision) { return precision == TTO_PREC_FP32 ? 2 : 3; }
+int sweep_shapes(int precision) {
+  return precision == TTO_PREC_FP32 ? 2 : (precision == TTO_PREC_TF32X3 ? kUmmaShape + 1 : 4);
+}
 
 int launch_sweep(EvalArgs& a, cudaStream_t s) {
   if (a.shape < 0 || a.shape >= sweep_shapes(a.precision)) return set_error(TTO_E_ARG, "unknown sweep shape %d", a.shape);

@@ -40,16 +40,18 @@
 namespace tto {
 
 // CTA shapes: TOPO topologies x HALVES row groups of 16*MW rows, one warp
-// each, SLOTS pipeline slots, two CTAs per SM.  The autotuner picks one per grid.
-template <int TOPO, int HALVES, int SLOTS>
+// each, SLOTS pipeline slots, CTAS resident CTAs per SM (the register budget
+// per thread follows: 128 at two, 80 at three).  The autotuner picks one per
+// grid.
+template <int TOPO, int HALVES, int SLOTS, int CTAS>
 struct CtaShape {
-  static constexpr int kTopo = TOPO, kHalves = HALVES, kWarps = TOPO * HALVES, kSlots = SLOTS;
+  static constexpr int kTopo = TOPO, kHalves = HALVES, kWarps = TOPO * HALVES, kSlots = SLOTS, kCtas = CTAS;
 };
-using Shape0 = CtaShape<4, 2, 3>;  // default: 64 rows x 4 topologies
-using Shape1 = CtaShape<8, 1, 2>;  // 32 rows x 8 topologies
-using Shape2 = CtaShape<2, 4, 2>;  // 128 rows x 2 topologies
-constexpr int kNumShapes = 3;
-constexpr int kCtasPerSM = 2;
+using Shape0 = CtaShape<4, 2, 3, 2>;  // default: 64 rows x 4 topologies
+using Shape1 = CtaShape<8, 1, 2, 2>;  // 32 rows x 8 topologies
+using Shape2 = CtaShape<2, 4, 2, 2>;  // 128 rows x 2 topologies
+using Shape3 = CtaShape<4, 2, 2, 3>;  // as Shape0, three CTAs (24 warps) per SM
+constexpr int kNumShapes = 4;
 constexpr int kSwB = 16, kSwG = 16;   // launch-order tile: row bands x topology groups
 constexpr int kMaxTChunk = 8;         // timesteps per sweep pass
 constexpr int kSN = 8;                // outage tiles (8 columns each) per pipeline stage
@@ -144,7 +146,7 @@ struct Slot {
 };
 
 template <int TC, int MW, int MODE, class SH>
-__global__ void __launch_bounds__(SH::kWarps * 32, kCtasPerSM)
+__global__ void __launch_bounds__(SH::kWarps * 32, SH::kCtas)
     sweep_tc_kernel(EvalArgs a, int tci, int n_bands, int n_groups) {
   using S = Slot<MW, MODE, TC, SH>;
   constexpr int AW = TCMode<MODE>::AW, BW = TCMode<MODE>::BW;
@@ -515,6 +517,10 @@ __global__ void fragment_N_kernel(const float* __restrict__ Nmo, float4* __restr
 }
 
 int ensure_fragment_N(tto_grid* g, cudaStream_t s) {
+  if (!g->d_Nq) {
+    const int rc = ensure_quad_N(g, s);
+    if (rc) return rc;
+  }
   if (g->d_Nf) return TTO_OK;
   const size_t n = (size_t)g->E_mon_pad * g->O_pad;
   TTO_CUDA_TRY(cudaMalloc(&g->d_Nf, n * sizeof(float)));
@@ -570,6 +576,7 @@ static int launch_tc_shape(EvalArgs& a, int tci, cudaStream_t s) {
   switch (a.shape) {
     case 1: return launch_tc_chunk<MODE, Shape1>(a, tci, s);
     case 2: return launch_tc_chunk<MODE, Shape2>(a, tci, s);
+    case 3: return launch_tc_chunk<MODE, Shape3>(a, tci, s);
     default: return launch_tc_chunk<MODE, Shape0>(a, tci, s);
   }
 }
@@ -584,6 +591,7 @@ static int tc_mode(int precision) {
 }
 
 int launch_sweep_tc(EvalArgs& a, cudaStream_t s) {
+  if (a.shape == kUmmaShape) return launch_sweep_umma(a, s);
   if ((a.O_pad >> 3) % kSN != 0) return set_error(TTO_E_ARG, "outage padding is not a multiple of the stage width");
   if ((a.E_mon_pad >> 4) % 8 != 0) return set_error(TTO_E_ARG, "monitored padding is not a multiple of the band");
   if (a.shape < 0 || a.shape >= kNumShapes) return set_error(TTO_E_ARG, "unknown sweep shape %d", a.shape);

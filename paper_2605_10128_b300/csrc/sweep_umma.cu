@@ -1,0 +1,503 @@
+// Fused N-1 sweep on the fifth-generation tensor cores (tcgen05, sm_100 family).
+//
+// Same arithmetic as the mma.sync sweep (sweep_tc.cu): for every monitored row
+// l, outage c and timestep t,
+//     F_lc[t] = f'_l[t] + (U_l . V_c - N_lc) g_c[t],   fmax_l[t] = max_c |F_lc[t]|,
+// with the rank-k product split into TF32 parts, U V^T = U_hi V_hi + U_lo V_hi +
+// U_hi V_lo (about 2^-21 relative error), and F never stored.
+//
+// CTA = one band of 128 monitored rows x 4 topologies, all outage columns in
+// chunks of 64.  Roles:
+//   warp 0 (one lane)   streams each chunk's operands into a 3-slot shared-memory
+//                       ring with bulk copies (cp.async.bulk, completion counted
+//                       on an mbarrier): the -N tile of the band (shared by the
+//                       four topologies) and per topology the V_hi / V_lo tiles
+//                       and the g values;
+//   warp 1 (one lane)   issues, per chunk and topology, three tcgen05.mma
+//                       (M = 128, N = 64, K = 8, kind::tf32) into that
+//                       topology's accumulator in tensor memory (two 64-column
+//                       buffers per topology, 512 columns in all) and commits
+//                       them to an mbarrier;
+//   warps 2..17         four epilogue warpgroups, one per topology: each warp
+//                       reads its 32 accumulator lanes (= rows) with
+//                       tcgen05.ld.32x32b, adds -N, and keeps the running
+//                       maxima of every timestep in registers.
+// The U tiles of the four topologies stay in shared memory for the whole
+// sweep.  Operand tiles use the canonical K-major layout without swizzle:
+// core matrices of 8 rows x 16 bytes, 128 bytes apart along K and 256 bytes
+// apart along M/N.  Every wait is bounded (about a second): a wait that gives
+// up raises a CTA-wide abort flag and sets the status word to TTO_E_TIMEOUT;
+// before the CTA exits, the copies and MMAs it issued are waited for (again
+// bounded) and the tensor memory is released.
+#include <stdint.h>
+
+#include "sweep.cuh"
+
+namespace tto {
+
+namespace {
+
+constexpr int kUTopo = 4;                 // topologies per CTA (one epilogue warpgroup each)
+constexpr int kUNC = 64;                  // outage columns per chunk (MMA N)
+constexpr int kUStages = 3;               // shared-memory ring slots
+constexpr int kUEpiWarps = 4 * kUTopo;    // 16 epilogue warps
+constexpr int kUThreads = 32 * (2 + kUEpiWarps);
+constexpr uint32_t kUTmemCols = 512;      // 4 topologies x 2 buffers x 64 columns
+constexpr uint32_t kUA = 2 * 128 * 8 * 4;        // U_hi + U_lo tiles of one topology (8 KB)
+constexpr uint32_t kUN = 128 * kUNC * 4;         // -N tile of a chunk (32 KB)
+constexpr uint32_t kUV = 2 * kUNC * 8 * 4;       // V_hi + V_lo tiles of a chunk (4 KB)
+constexpr long long kUWaitCycles = 1ll << 31;    // ~1 s at 2 GHz
+
+template <int TC>
+struct UCfg {
+  static constexpr uint32_t kG = kUNC * TC * 4;           // g values of a chunk
+  static constexpr uint32_t kTopoBytes = kUV + kG;
+  static constexpr uint32_t kStage = kUN + kUTopo * kTopoBytes;
+  static constexpr uint32_t kSmem = kUTopo * kUA + kUStages * kStage + 1024;  // + alignment slack
+};
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool bar_test(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; false when it gave up or another role raised the abort flag.
+__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+  if (bar_test(b, parity)) return true;
+  const long long t0 = clock64();
+  for (;;) {
+    __nanosleep(32);
+    if (bar_test(b, parity)) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kUWaitCycles) return false;
+  }
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(su32(dst)),
+      "l"(src), "r"(bytes), "r"(su32(b))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, canonical K-major layout without swizzle:
+// start address, leading (K) byte offset, stride (M/N) byte offset, the fixed
+// descriptor version 1 at bit 46, base offset 0, swizzle mode 0.
+__device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t lbo, uint32_t sbo) {
+  const uint32_t a = su32(p);
+  return (uint64_t)((a >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor, kind::tf32: F32 accumulator (bits 4-5 = 1), A and B
+// TF32 (bits 7-9, 10-12 = 2), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t kIdescTF32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kUNC >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(kIdescTF32), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* b) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
+               : "memory");
+}
+
+// 32 lanes x 16 columns of 32-bit accumulators: thread i gets lane (base + i),
+// columns col .. col+15 in r[0..15].
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+// Wait for the thread's outstanding tcgen05.ld; the registers are tied to the
+// wait so that no use of them moves above it.
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15])
+               :
+               : "memory");
+}
+
+template <int TC>
+__device__ __forceinline__ void epilogue16(const uint32_t (&P)[16], const float4* nq, const float* gs, int c0,
+                                           const float (&f)[TC], float (&m)[TC]) {
+#pragma unroll
+  for (int cq = 0; cq < 4; ++cq) {
+    const float4 nv = nq[(c0 / 4 + cq) * 128];
+    const float n4[4] = {nv.x, nv.y, nv.z, nv.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int c = c0 + 4 * cq + i;
+      const float D = __uint_as_float(P[4 * cq + i]) + n4[i];
+      float g[TC];
+      if constexpr (TC >= 4) {
+#pragma unroll
+        for (int x = 0; x < TC / 4; ++x) {
+          const float4 v = *reinterpret_cast<const float4*>(gs + c * TC + 4 * x);
+          g[4 * x] = v.x;
+          g[4 * x + 1] = v.y;
+          g[4 * x + 2] = v.z;
+          g[4 * x + 3] = v.w;
+        }
+      } else if constexpr (TC == 2) {
+        const float2 v = *reinterpret_cast<const float2*>(gs + c * 2);
+        g[0] = v.x;
+        g[1] = v.y;
+      } else {
+        g[0] = gs[c];
+      }
+#pragma unroll
+      for (int t = 0; t < TC; ++t) m[t] = fmaxf(m[t], fabsf(fmaf(D, g[t], f[t])));
+    }
+  }
+}
+
+template <int TC>
+__global__ void __launch_bounds__(kUThreads, 1)
+    sweep_umma_kernel(EvalArgs a, int tci, int n_bands, int n_groups) {
+  using C = UCfg<TC>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t bar_a, full[kUStages], empty[kUStages], tfull[kUTopo][2], tempty[kUTopo][2],
+      mma_done;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  volatile int* abort_flag = &s_abort;
+  auto give_up = [&]() {
+    atomicExch(a.status, TTO_E_TIMEOUT);
+    *abort_flag = 1;
+  };
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles_b = (n_bands + 15) / 16;
+  const int tile = blockIdx.x / 256, within = blockIdx.x % 256;
+  const int band = (tile % tiles_b) * 16 + within % 16;
+  const int grp = (tile / tiles_b) * 16 + within / 16;
+  if (band >= n_bands || grp >= n_groups) return;  // CTA-uniform, before any barrier or allocation
+  const int n_topo = min(kUTopo, a.B - grp * kUTopo);
+  const int n_chunks = a.O_pad / kUNC;
+  unsigned char* smA = smem;                          // [topo][hi, lo][128 x 8]
+  unsigned char* smS = smem + kUTopo * kUA;           // ring slots
+
+  if (threadIdx.x == 0) {
+    bar_init(&bar_a, 1);
+    for (int s = 0; s < kUStages; ++s) {
+      bar_init(&full[s], 1);
+      bar_init(&empty[s], 4 * n_topo);
+    }
+    for (int b = 0; b < kUTopo; ++b)
+      for (int x = 0; x < 2; ++x) {
+        bar_init(&tfull[b][x], 1);
+        bar_init(&tempty[b][x], 4);
+      }
+    bar_init(&mma_done, 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&s_tmem)),
+                 "r"(kUTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    tc_fence_before();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+
+  int issued = 0;  // producer: stages issued
+  if (warp == 0 && lane == 0) {
+    // U tiles of the group's topologies, then the ring
+    bar_expect_tx(&bar_a, n_topo * kUA);
+    for (int b = 0; b < n_topo; ++b)
+      bulk_g2s(smA + b * kUA, a.Ua + (((size_t)(grp * kUTopo + b) * n_bands + band) * (kUA / 4)), kUA, &bar_a);
+    for (int s = 0; s < n_chunks; ++s) {
+      const int slot = s % kUStages;
+      if (s >= kUStages && !bar_wait(&empty[slot], (uint32_t)((s / kUStages) - 1) & 1u, abort_flag)) {
+        give_up();
+        break;
+      }
+      unsigned char* st = smS + (size_t)slot * C::kStage;
+      bar_expect_tx(&full[slot], kUN + n_topo * C::kTopoBytes);
+      bulk_g2s(st, a.Nq + ((size_t)band * (a.O_pad / 4) + (size_t)s * (kUNC / 4)) * 128, kUN, &full[slot]);
+      for (int b = 0; b < n_topo; ++b) {
+        const size_t bt = (size_t)grp * kUTopo + b;
+        unsigned char* tb = st + kUN + b * C::kTopoBytes;
+        bulk_g2s(tb, a.Vb + (bt * n_chunks + s) * (kUV / 4), kUV, &full[slot]);
+        bulk_g2s(tb + kUV, a.gq + ((bt * a.n_tch + tci) * a.O_pad + (size_t)s * kUNC) * TC, C::kG, &full[slot]);
+      }
+      issued = s + 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    if (!bar_wait(&bar_a, 0, abort_flag)) {
+      give_up();
+    } else {
+      for (int s = 0; s < n_chunks; ++s) {
+        const int slot = s % kUStages, buf = s & 1;
+        if (!bar_wait(&full[slot], (uint32_t)(s / kUStages) & 1u, abort_flag)) {
+          give_up();
+          break;
+        }
+        const unsigned char* st = smS + (size_t)slot * C::kStage;
+        bool ok = true;
+        for (int b = 0; b < n_topo; ++b) {
+          if (s >= 2 && !bar_wait(&tempty[b][buf], (uint32_t)((s >> 1) - 1) & 1u, abort_flag)) {
+            give_up();
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const unsigned char* A = smA + b * kUA;
+          const unsigned char* V = st + kUN + b * C::kTopoBytes;
+          const uint64_t a_hi = smem_desc(A, 128, 256), a_lo = smem_desc(A + kUA / 2, 128, 256);
+          const uint64_t v_hi = smem_desc(V, 128, 256), v_lo = smem_desc(V + kUV / 2, 128, 256);
+          const uint32_t d = tmem + (uint32_t)(b * 2 * kUNC + buf * kUNC);
+          umma_tf32(d, a_hi, v_hi, 0u);
+          umma_tf32(d, a_lo, v_hi, 1u);
+          umma_tf32(d, a_hi, v_lo, 1u);
+          umma_commit(&tfull[b][buf]);
+        }
+        if (!ok) break;
+      }
+    }
+  } else if (warp >= 2) {
+    const int e = warp - 2, b = e >> 2, q = warp & 3;  // q: this warp's tensor-memory lane quarter
+    if (b < n_topo) {
+      const size_t bt = (size_t)grp * kUTopo + b;
+      const int rib = 32 * q + lane, row = band * 128 + rib;
+      const int t0 = tci * TC;
+      float f[TC], m[TC];
+#pragma unroll
+      for (int t = 0; t < TC; ++t) {
+        f[t] = a.fp[(bt * a.TT + t0 + t) * (size_t)a.E_mon_pad + row];
+        m[t] = 0.f;
+      }
+      bool ok = true;
+      for (int s = 0; s < n_chunks && ok; ++s) {
+        const int slot = s % kUStages, buf = s & 1;
+        ok = __all_sync(0xffffffffu, bar_wait(&full[slot], (uint32_t)(s / kUStages) & 1u, abort_flag) &&
+                                         bar_wait(&tfull[b][buf], (uint32_t)(s >> 1) & 1u, abort_flag));
+        if (!ok) break;
+        tc_fence_after();
+        const unsigned char* st = smS + (size_t)slot * C::kStage;
+        const float4* nq = reinterpret_cast<const float4*>(st) + rib;
+        const float* gs = reinterpret_cast<const float*>(st + kUN + b * C::kTopoBytes + kUV);
+        const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 2 * kUNC + buf * kUNC);
+        uint32_t P0[16], P1[16];
+        tmem_ld16(taddr, P0);
+        tmem_wait_ld(P0);
+        tmem_ld16(taddr + 16, P1);
+        epilogue16<TC>(P0, nq, gs, 0, f, m);
+        tmem_wait_ld(P1);
+        tmem_ld16(taddr + 32, P0);
+        epilogue16<TC>(P1, nq, gs, 16, f, m);
+        tmem_wait_ld(P0);
+        tmem_ld16(taddr + 48, P1);
+        epilogue16<TC>(P0, nq, gs, 32, f, m);
+        tmem_wait_ld(P1);
+        epilogue16<TC>(P1, nq, gs, 48, f, m);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          bar_arrive(&tempty[b][buf]);
+          bar_arrive(&empty[slot]);
+        }
+      }
+      if (!ok) {
+        give_up();
+      } else {
+        // per-row metrics of this warp's 32 rows, then one partial record
+        float over = 0.f, cnt = 0.f, ml = 0.f;
+        if (row < a.E_mon) {
+          const float lim = a.lim[row];
+#pragma unroll
+          for (int t = 0; t < TC; ++t) {
+            const int tt = t0 + t;
+            if (tt < a.n_t) {
+              over += fmaxf(m[t] - lim, 0.f);
+              cnt += m[t] > lim ? 1.f : 0.f;
+              ml = fmaxf(ml, fmaxf(fabsf(f[t]), m[t]) / lim);
+              if (a.fmax) a.fmax[(bt * a.n_t + tt) * a.E_mon + row] = m[t];
+            }
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          over += __shfl_xor_sync(0xffffffffu, over, o);
+          cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+          ml = fmaxf(ml, __shfl_xor_sync(0xffffffffu, ml, o));
+        }
+        if (lane == 0) {
+          float* pp = a.part + (bt * a.n_parts + (size_t)(band * 4 + q) * a.n_tch + tci) * 4;
+          pp[0] = over;
+          pp[1] = cnt;
+          pp[2] = ml;
+          pp[3] = 0.f;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // drain: no copy or MMA of this CTA may still be in flight when it exits
+  if (warp == 0 && lane == 0) {
+    for (int s = issued > kUStages ? issued - kUStages : 0; s < issued; ++s) {
+      int dummy = 0;
+      bar_wait(&full[s % kUStages], (uint32_t)(s / kUStages) & 1u, &dummy);
+    }
+  } else if (warp == 1 && lane == 0) {
+    int dummy = 0;
+    umma_commit(&mma_done);
+    bar_wait(&mma_done, 0, &dummy);
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kUTmemCols) : "memory");
+  }
+}
+
+// -N in row-quad order per band of 128 rows: Nq[band][c / 4][r][c % 4] =
+// -N[128 band + r][c].
+__global__ void quad_N_kernel(const float* __restrict__ Nmo, float4* __restrict__ Nq, int n_bands, int O_pad) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t nq = (size_t)O_pad / 4;
+  if (i >= (size_t)n_bands * nq * 128) return;
+  const int r = (int)(i % 128);
+  const size_t cq = (i / 128) % nq, band = i / (128 * nq);
+  const float* src = Nmo + ((size_t)band * 128 + r) * O_pad + 4 * cq;
+  Nq[i] = make_float4(-src[0], -src[1], -src[2], -src[3]);
+}
+
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// Canonical K-major no-swizzle position of element (row, k) in a tile of
+// 8-column rows: core matrix (row / 8, k / 4) at 256 (row / 8) + 128 (k / 4)
+// bytes, 16 bytes per core-matrix row.
+__device__ __forceinline__ int canon(int row, int k) { return (row >> 3) * 64 + (k >> 2) * 32 + (row & 7) * 4 + (k & 3); }
+
+// U rows -> [B][band][hi, lo][128 x 8]; V columns -> [B][chunk][hi, lo][64 x 8];
+// g -> [B][t-chunk][O_pad][TC] (zero beyond the padded timesteps).
+__global__ void pack_umma_kernel(EvalArgs a) {
+  const int rows = a.E_mon_pad, cols = a.O_pad;
+  const size_t per = (size_t)rows + cols;
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= per * a.B) return;
+  const int b = (int)(i / per);
+  const int x = (int)(i % per);
+  if (x < rows) {
+    const int l = x, band = l >> 7, r = l & 127;
+    const float4* ur = reinterpret_cast<const float4*>(a.U + ((size_t)b * rows + l) * 8);
+    const float4 u0 = ur[0], u1 = ur[1];
+    const float u[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+    uint32_t* base = a.Ua + ((size_t)b * (rows >> 7) + band) * 2048;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t hi = tf32_bits(u[k]);
+      base[canon(r, k)] = hi;
+      base[1024 + canon(r, k)] = tf32_bits(u[k] - __uint_as_float(hi));
+    }
+  } else {
+    const int c = x - rows, chunk = c / kUNC, n = c % kUNC;
+    const float4* vr = reinterpret_cast<const float4*>(a.V + ((size_t)b * cols + c) * 8);
+    const float4 v0 = vr[0], v1 = vr[1];
+    const float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+    uint32_t* base = a.Vb + ((size_t)b * (cols / kUNC) + chunk) * 1024;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t hi = tf32_bits(v[k]);
+      base[canon(n, k)] = hi;
+      base[512 + canon(n, k)] = tf32_bits(v[k] - __uint_as_float(hi));
+    }
+    for (int ci = 0; ci < a.n_tch; ++ci)
+      for (int t = 0; t < a.TC; ++t) {
+        const int tt = ci * a.TC + t;
+        a.gq[(((size_t)b * a.n_tch + ci) * cols + c) * a.TC + t] =
+            tt < a.TT ? a.gg[((size_t)b * cols + c) * a.TT + tt] : 0.f;
+      }
+  }
+}
+
+template <int TC>
+int launch_umma_tc(EvalArgs& a, int tci, cudaStream_t s) {
+  using C = UCfg<TC>;
+  static bool attr_set[64] = {};
+  int dev = 0;
+  TTO_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return set_error(TTO_E_ARG, "device %d out of range", dev);
+  if (!attr_set[dev]) {
+    TTO_CUDA_TRY(cudaFuncSetAttribute(sweep_umma_kernel<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmem));
+    attr_set[dev] = true;
+  }
+  const int n_bands = a.E_mon_pad / 128;
+  const int n_groups = (a.B + kUTopo - 1) / kUTopo;
+  const int tiles_b = (n_bands + 15) / 16, tiles_g = (n_groups + 15) / 16;
+  const size_t blocks = (size_t)tiles_b * tiles_g * 256;
+  if (blocks > 0x7fffffffu) return set_error(TTO_E_ARG, "batch too large for one sweep launch");
+  sweep_umma_kernel<TC><<<(unsigned)blocks, kUThreads, C::kSmem, s>>>(a, tci, n_bands, n_groups);
+  TTO_CUDA_TRY(cudaGetLastError());
+  return TTO_OK;
+}
+
+}  // namespace
+
+int ensure_quad_N(tto_grid* g, cudaStream_t s) {
+  if (g->d_Nq) return TTO_OK;
+  const int n_bands = g->E_mon_pad / 128;
+  const size_t n4 = (size_t)n_bands * (g->O_pad / 4) * 128;
+  TTO_CUDA_TRY(cudaMalloc(&g->d_Nq, n4 * sizeof(float4)));
+  quad_N_kernel<<<(unsigned)((n4 + 255) / 256), 256, 0, s>>>(g->d_Nmo, g->d_Nq, n_bands, g->O_pad);
+  TTO_CUDA_TRY(cudaGetLastError());
+  return TTO_OK;
+}
+
+int launch_sweep_umma(EvalArgs& a, cudaStream_t s) {
+  if (a.precision != TTO_PREC_TF32X3) return set_error(TTO_E_ARG, "the tcgen05 sweep runs in TF32X3 only");
+  if (a.E_mon_pad % 128 != 0 || a.O_pad % kUNC != 0) return set_error(TTO_E_ARG, "padding does not fit the tcgen05 tiles");
+  if (!a.Nq) return set_error(TTO_E_ARG, "quad-ordered -N missing");
+  const size_t threads = ((size_t)a.E_mon_pad + a.O_pad) * a.B;
+  pack_umma_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
+  TTO_CUDA_TRY(cudaGetLastError());
+  a.n_parts = (a.E_mon_pad / 32) * a.n_tch;
+  for (int ci = 0; ci < a.n_tch; ++ci) {
+    int rc;
+    switch (a.TC) {
+      case 1: rc = launch_umma_tc<1>(a, ci, s); break;
+      case 2: rc = launch_umma_tc<2>(a, ci, s); break;
+      case 4: rc = launch_umma_tc<4>(a, ci, s); break;
+      case 8: rc = launch_umma_tc<8>(a, ci, s); break;
+      default: return set_error(TTO_E_ARG, "unsupported timestep chunk %d", a.TC);
+    }
+    if (rc) return rc;
+  }
+  return TTO_OK;
+}
+
+}  // namespace tto
