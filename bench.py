@@ -351,6 +351,8 @@ def main():
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "fp16x3", "tf32x3", "bf16x3", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-outages", type=int, default=120)
+    ap.add_argument("--sweep-variant", type=int, default=-1,
+                    help="fix the sweep tile variant instead of autotuning (4 = tcgen05, TF32X3 only)")
     ap.add_argument("--iters", type=int, default=60, help="--config surrogate: iterations per arm")
     ap.add_argument("--seeds", type=int, default=3, help="--config surrogate: seeds")
     ap.add_argument("--variants", default="score:16384,score:65536",
@@ -388,6 +390,13 @@ def main():
     ds, dm = c["archive"]
     sg, g, create_s = make_grid(args.config, local, seed=0)
     g.reserve(B)
+    # sweep tile variant chosen by the library's autotuner (timed on 512
+    # topologies), unless --sweep-variant fixes it
+    if args.sweep_variant >= 0:
+        g.set_sweep_shape(prec, args.sweep_variant)
+        tuned_shape, tuned_ms = args.sweep_variant, None
+    else:
+        tuned_shape, tuned_ms = g.autotune(min(B, 512), precision=prec)
     A = Archive(g, ds, dm)
     seed = 1000 + rank
     stream = torch.cuda.current_stream()
@@ -476,7 +485,8 @@ def main():
                        "precision": args.precision, "parallelism": f"independent searches x{world}",
                        "l2": "inputs larger than L2 (N tile 305 MB + per-batch workspace ~8 GB)",
                        "step": "one MapElites iteration: propose, exact N-1 evaluation, insert",
-                       "grid_create_s": round(create_s, 2)},
+                       "grid_create_s": round(create_s, 2),
+                       "sweep_variant": {"chosen": tuned_shape, "ms_per_variant_at_B512": tuned_ms}},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "N-1 sweep", "sweep_ms_per_launch": sweep_ms,

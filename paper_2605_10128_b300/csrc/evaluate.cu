@@ -479,7 +479,6 @@ int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, 
     rc = ensure_fragment_N(g, s);
     if (rc) return rc;
     a.Nf = g->d_Nf;
-    a.Nq = g->d_Nq;
   }
   rc = launch_sweep(a, s);
   if (rc) return rc;

@@ -407,7 +407,7 @@ static void release(tto_grid* g) {
   cudaSetDevice(g->device);
   forget_grid_graphs(g);
   free_workspace(g);
-  void* ptrs[] = {g->d_from, g->d_Nf, g->d_Nq, g->d_Nmo, g->d_Nsw, g->d_swcol, g->d_f0, g->d_p, g->d_b, g->d_lim,
+  void* ptrs[] = {g->d_from, g->d_Nf, g->d_Nmo, g->d_Nsw, g->d_swcol, g->d_f0, g->d_p, g->d_b, g->d_lim,
                   g->d_mon, g->d_out, g->d_Ncc, g->d_station_bus, g->d_asset_off,
                   g->d_asset_br, g->d_act_st, g->d_act_off, g->d_act_mask, g->d_status};
   for (void* p : ptrs)

@@ -11,7 +11,6 @@ struct EvalArgs {
   // grid (device)
   const float* Nmo;
   const float4* Nf;  // -N in mma C-fragment order (tensor-core sweep)
-  const float4* Nq;  // -N in row-quad order per 128-row band (tcgen05 sweep)
   const double* Nsw;
   const int* swcol;
   const double* f0;
@@ -70,8 +69,6 @@ int sweep_shapes(int precision);
 size_t max_parts(const tto_grid* g);
 // Build the fragment-ordered copy of -N used by the tensor-core sweep (once).
 int ensure_fragment_N(tto_grid* g, cudaStream_t s);
-// Build the row-quad copy of -N used by the tcgen05 sweep (once).
-int ensure_quad_N(tto_grid* g, cudaStream_t s);
 // The tcgen05 sweep (TF32X3 only); sets a.n_parts.
 int launch_sweep_umma(EvalArgs& a, cudaStream_t s);
 // Sweep tile variant of TF32X3 that runs the tcgen05 kernel.

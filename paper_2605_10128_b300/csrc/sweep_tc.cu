@@ -517,10 +517,6 @@ __global__ void fragment_N_kernel(const float* __restrict__ Nmo, float4* __restr
 }
 
 int ensure_fragment_N(tto_grid* g, cudaStream_t s) {
-  if (!g->d_Nq) {
-    const int rc = ensure_quad_N(g, s);
-    if (rc) return rc;
-  }
   if (g->d_Nf) return TTO_OK;
   const size_t n = (size_t)g->E_mon_pad * g->O_pad;
   TTO_CUDA_TRY(cudaMalloc(&g->d_Nf, n * sizeof(float)));

@@ -10,22 +10,29 @@
 // chunks of 64.  Roles:
 //   warp 0 (one lane)   streams each chunk's operands into a 3-slot shared-memory
 //                       ring with bulk copies (cp.async.bulk, completion counted
-//                       on an mbarrier): the -N tile of the band (shared by the
-//                       four topologies) and per topology the V_hi / V_lo tiles
-//                       and the g values;
-//   warp 1 (one lane)   issues, per chunk and topology, three tcgen05.mma
-//                       (M = 128, N = 64, K = 8, kind::tf32) into that
-//                       topology's accumulator in tensor memory (two 64-column
-//                       buffers per topology, 512 columns in all) and commits
-//                       them to an mbarrier;
+//                       on an mbarrier): the -N tile of the band in mma
+//                       C-fragment order (shared by the four topologies) and
+//                       per topology the V_hi / V_lo tiles and the g values;
+//   warp 1 (one lane)   per chunk and topology, issues three tcgen05.mma
+//                       (M = 128, N = 64, K = 8, kind::tf32) computing U V^T
+//                       into that topology's accumulator in tensor memory (two
+//                       64-column buffers per topology, 512 columns in all) and
+//                       commits them to an mbarrier;
 //   warps 2..17         four epilogue warpgroups, one per topology: each warp
-//                       reads its 32 accumulator lanes (= rows) with
-//                       tcgen05.ld.32x32b, adds -N, and keeps the running
-//                       maxima of every timestep in registers.
+//                       reads its 32 accumulator lanes with tcgen05.ld.16x256b,
+//                       whose register layout is the mma C fragment (a thread
+//                       holds 4 rows x 2 columns of every 8-column block, so
+//                       one g value serves 4 rows and one 16-byte load brings
+//                       the matching -N values), adds -N, and keeps the running
+//                       maxima of every timestep in registers; the 4 lanes that
+//                       share rows combine theirs at the end.
+// (Copying -N into each accumulator with tcgen05.cp instead measured slower:
+// the copies of four topologies' accumulators per chunk became the critical
+// path.)
 // The U tiles of the four topologies stay in shared memory for the whole
-// sweep.  Operand tiles use the canonical K-major layout without swizzle:
-// core matrices of 8 rows x 16 bytes, 128 bytes apart along K and 256 bytes
-// apart along M/N.  Every wait is bounded (about a second): a wait that gives
+// sweep.  Operand tiles use the canonical K-major layout without swizzle: core
+// matrices of 8 rows x 16 bytes, 128 bytes apart along K and 256 bytes apart
+// along M/N.  Every wait is bounded (about a second): a wait that gives
 // up raises a CTA-wide abort flag and sets the status word to TTO_E_TIMEOUT;
 // before the CTA exits, the copies and MMAs it issued are waited for (again
 // bounded) and the tensor memory is released.
@@ -67,10 +74,12 @@ __device__ __forceinline__ void bar_expect_tx(uint64_t* b, uint32_t bytes) {
 __device__ __forceinline__ void bar_arrive(uint64_t* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
 }
-__device__ __forceinline__ bool bar_test(uint64_t* b, uint32_t parity) {
+// mbarrier.try_wait: returns once the phase completed or after a
+// hardware-chosen suspension, so polling warps leave the issue slots free.
+__device__ __forceinline__ bool bar_try(uint64_t* b, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
       : "=r"(ok)
       : "r"(su32(b)), "r"(parity)
       : "memory");
@@ -78,11 +87,10 @@ __device__ __forceinline__ bool bar_test(uint64_t* b, uint32_t parity) {
 }
 // Bounded wait; false when it gave up or another role raised the abort flag.
 __device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
-  if (bar_test(b, parity)) return true;
+  if (bar_try(b, parity)) return true;
   const long long t0 = clock64();
   for (;;) {
-    __nanosleep(32);
-    if (bar_test(b, parity)) return true;
+    if (bar_try(b, parity)) return true;
     if (*abort_flag) return false;
     if (clock64() - t0 > kUWaitCycles) return false;
   }
@@ -122,57 +130,62 @@ __device__ __forceinline__ void umma_commit(uint64_t* b) {
                : "memory");
 }
 
-// 32 lanes x 16 columns of 32-bit accumulators: thread i gets lane (base + i),
-// columns col .. col+15 in r[0..15].
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
+// Two 16-lane x 8-column blocks (16x256b.x2): thread i gets lanes base + i/4
+// and base + i/4 + 8, columns 2 (i % 4) and 2 (i % 4) + 1 of each block, in
+// r[4 blk + {0, 1}] (first lane) and r[4 blk + {2, 3}] (second lane).
+__device__ __forceinline__ void tmem_ld_2blk(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.16x256b.x2.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
 }
 // Wait for the thread's outstanding tcgen05.ld; the registers are tied to the
 // wait so that no use of them moves above it.
-__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[16]) {
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r0)[8], uint32_t (&r1)[8]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;"
-               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
-                 "+r"(r[15])
+               : "+r"(r0[0]), "+r"(r0[1]), "+r"(r0[2]), "+r"(r0[3]), "+r"(r0[4]), "+r"(r0[5]), "+r"(r0[6]),
+                 "+r"(r0[7]), "+r"(r1[0]), "+r"(r1[1]), "+r"(r1[2]), "+r"(r1[3]), "+r"(r1[4]), "+r"(r1[5]),
+                 "+r"(r1[6]), "+r"(r1[7])
                :
                : "memory");
 }
 
+// One step of 16 columns (two 8-column blocks): A holds U V^T of rows {r,
+// r+8} and B of rows {r+16, r+24} of the warp's 32 (r = lane / 4), columns
+// 2 (lane % 4) + {0, 1} of each block; nf points at this lane's -N fragment
+// of the first 16-row tile and block (the second 16-row tile is 8 fragment
+// tiles further on); g values of the two columns are loaded once for the 4 rows.
 template <int TC>
-__device__ __forceinline__ void epilogue16(const uint32_t (&P)[16], const float4* nq, const float* gs, int c0,
-                                           const float (&f)[TC], float (&m)[TC]) {
+__device__ __forceinline__ void epilogue_step(const uint32_t (&A)[8], const uint32_t (&B)[8], const float4* nf,
+                                              const float* gs, int c0, const float (&f)[4][TC],
+                                              float (&m)[4][TC]) {
 #pragma unroll
-  for (int cq = 0; cq < 4; ++cq) {
-    const float4 nv = nq[(c0 / 4 + cq) * 128];
-    const float n4[4] = {nv.x, nv.y, nv.z, nv.w};
+  for (int blk = 0; blk < 2; ++blk) {
+    const float4 na = nf[(c0 / 8 + blk) * 32], nb = nf[(8 + c0 / 8 + blk) * 32];
+    const int c = c0 + 8 * blk + 2 * (threadIdx.x & 3);
+    float g[2 * TC];  // g[c][0..TC), g[c + 1][0..TC)
+    if constexpr (2 * TC >= 4) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int c = c0 + 4 * cq + i;
-      const float D = __uint_as_float(P[4 * cq + i]) + n4[i];
-      float g[TC];
-      if constexpr (TC >= 4) {
-#pragma unroll
-        for (int x = 0; x < TC / 4; ++x) {
-          const float4 v = *reinterpret_cast<const float4*>(gs + c * TC + 4 * x);
-          g[4 * x] = v.x;
-          g[4 * x + 1] = v.y;
-          g[4 * x + 2] = v.z;
-          g[4 * x + 3] = v.w;
-        }
-      } else if constexpr (TC == 2) {
-        const float2 v = *reinterpret_cast<const float2*>(gs + c * 2);
-        g[0] = v.x;
-        g[1] = v.y;
-      } else {
-        g[0] = gs[c];
+      for (int x = 0; x < TC / 2; ++x) {
+        const float4 v = *reinterpret_cast<const float4*>(gs + c * TC + 4 * x);
+        g[4 * x] = v.x;
+        g[4 * x + 1] = v.y;
+        g[4 * x + 2] = v.z;
+        g[4 * x + 3] = v.w;
       }
-#pragma unroll
-      for (int t = 0; t < TC; ++t) m[t] = fmaxf(m[t], fabsf(fmaf(D, g[t], f[t])));
+    } else {
+      const float2 v = *reinterpret_cast<const float2*>(gs + c);
+      g[0] = v.x;
+      g[1] = v.y;
     }
+    const float d[4][2] = {{__uint_as_float(A[4 * blk]) + na.x, __uint_as_float(A[4 * blk + 1]) + na.y},
+                           {__uint_as_float(A[4 * blk + 2]) + na.z, __uint_as_float(A[4 * blk + 3]) + na.w},
+                           {__uint_as_float(B[4 * blk]) + nb.x, __uint_as_float(B[4 * blk + 1]) + nb.y},
+                           {__uint_as_float(B[4 * blk + 2]) + nb.z, __uint_as_float(B[4 * blk + 3]) + nb.w}};
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int t = 0; t < TC; ++t)
+        m[r][t] = fmaxf(m[r][t], fmaxf(fabsf(fmaf(d[r][0], g[t], f[r][t])), fabsf(fmaf(d[r][1], g[TC + t], f[r][t]))));
   }
 }
 
@@ -243,7 +256,10 @@ __global__ void __launch_bounds__(kUThreads, 1)
       }
       unsigned char* st = smS + (size_t)slot * C::kStage;
       bar_expect_tx(&full[slot], kUN + n_topo * C::kTopoBytes);
-      bulk_g2s(st, a.Nq + ((size_t)band * (a.O_pad / 4) + (size_t)s * (kUNC / 4)) * 128, kUN, &full[slot]);
+      // -N fragments of the band's 8 16-row tiles x the chunk's 8 column blocks
+      for (int i = 0; i < 8; ++i)
+        bulk_g2s(st + i * (kUN / 8), a.Nf + ((size_t)(band * 8 + i) * (a.O_pad / 8) + (size_t)s * (kUNC / 8)) * 32,
+                 kUN / 8, &full[slot]);
       for (int b = 0; b < n_topo; ++b) {
         const size_t bt = (size_t)grp * kUTopo + b;
         unsigned char* tb = st + kUN + b * C::kTopoBytes;
@@ -288,14 +304,17 @@ __global__ void __launch_bounds__(kUThreads, 1)
     const int e = warp - 2, b = e >> 2, q = warp & 3;  // q: this warp's tensor-memory lane quarter
     if (b < n_topo) {
       const size_t bt = (size_t)grp * kUTopo + b;
-      const int rib = 32 * q + lane, row = band * 128 + rib;
       const int t0 = tci * TC;
-      float f[TC], m[TC];
+      // rows of this thread within the band: 32 q + lane / 4 + {0, 8, 16, 24}
+      const int rb = 32 * q + (lane >> 2);
+      float f[4][TC], m[4][TC];
 #pragma unroll
-      for (int t = 0; t < TC; ++t) {
-        f[t] = a.fp[(bt * a.TT + t0 + t) * (size_t)a.E_mon_pad + row];
-        m[t] = 0.f;
-      }
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int t = 0; t < TC; ++t) {
+          f[r][t] = a.fp[(bt * a.TT + t0 + t) * (size_t)a.E_mon_pad + band * 128 + rb + 8 * r];
+          m[r][t] = 0.f;
+        }
       bool ok = true;
       for (int s = 0; s < n_chunks && ok; ++s) {
         const int slot = s % kUStages, buf = s & 1;
@@ -304,22 +323,28 @@ __global__ void __launch_bounds__(kUThreads, 1)
         if (!ok) break;
         tc_fence_after();
         const unsigned char* st = smS + (size_t)slot * C::kStage;
-        const float4* nq = reinterpret_cast<const float4*>(st) + rib;
         const float* gs = reinterpret_cast<const float*>(st + kUN + b * C::kTopoBytes + kUV);
-        const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 2 * kUNC + buf * kUNC);
-        uint32_t P0[16], P1[16];
-        tmem_ld16(taddr, P0);
-        tmem_wait_ld(P0);
-        tmem_ld16(taddr + 16, P1);
-        epilogue16<TC>(P0, nq, gs, 0, f, m);
-        tmem_wait_ld(P1);
-        tmem_ld16(taddr + 32, P0);
-        epilogue16<TC>(P1, nq, gs, 16, f, m);
-        tmem_wait_ld(P0);
-        tmem_ld16(taddr + 48, P1);
-        epilogue16<TC>(P0, nq, gs, 32, f, m);
-        tmem_wait_ld(P1);
-        epilogue16<TC>(P1, nq, gs, 48, f, m);
+        // this lane's fragment of 16-row tile 2 q (rows 32 q .. 32 q + 15), block 0
+        const float4* nf = reinterpret_cast<const float4*>(st) + (2 * q) * 8 * 32 + lane;
+        const uint32_t col = (uint32_t)(b * 2 * kUNC + buf * kUNC);
+        const uint32_t lo = tmem + ((uint32_t)(32 * q) << 16) + col, hi = lo + (16u << 16);
+        uint32_t A0[8], B0[8], A1[8], B1[8];
+        tmem_ld_2blk(lo, A0);
+        tmem_ld_2blk(hi, B0);
+        tmem_wait_ld(A0, B0);
+        tmem_ld_2blk(lo + 16, A1);
+        tmem_ld_2blk(hi + 16, B1);
+        epilogue_step<TC>(A0, B0, nf, gs, 0, f, m);
+        tmem_wait_ld(A1, B1);
+        tmem_ld_2blk(lo + 32, A0);
+        tmem_ld_2blk(hi + 32, B0);
+        epilogue_step<TC>(A1, B1, nf, gs, 16, f, m);
+        tmem_wait_ld(A0, B0);
+        tmem_ld_2blk(lo + 48, A1);
+        tmem_ld_2blk(hi + 48, B1);
+        epilogue_step<TC>(A0, B0, nf, gs, 32, f, m);
+        tmem_wait_ld(A1, B1);
+        epilogue_step<TC>(A1, B1, nf, gs, 48, f, m);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) {
@@ -330,18 +355,30 @@ __global__ void __launch_bounds__(kUThreads, 1)
       if (!ok) {
         give_up();
       } else {
-        // per-row metrics of this warp's 32 rows, then one partial record
+        // combine the 4 lanes that share rows, then per-row metrics and one
+        // partial record per warp (its 32 rows)
         float over = 0.f, cnt = 0.f, ml = 0.f;
-        if (row < a.E_mon) {
-          const float lim = a.lim[row];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int row = band * 128 + rb + 8 * r;
 #pragma unroll
           for (int t = 0; t < TC; ++t) {
-            const int tt = t0 + t;
-            if (tt < a.n_t) {
-              over += fmaxf(m[t] - lim, 0.f);
-              cnt += m[t] > lim ? 1.f : 0.f;
-              ml = fmaxf(ml, fmaxf(fabsf(f[t]), m[t]) / lim);
-              if (a.fmax) a.fmax[(bt * a.n_t + tt) * a.E_mon + row] = m[t];
+            float v = m[r][t];
+            v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 1));
+            v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 2));
+            m[r][t] = v;
+          }
+          if ((lane & 3) == 0 && row < a.E_mon) {
+            const float lim = a.lim[row];
+#pragma unroll
+            for (int t = 0; t < TC; ++t) {
+              const int tt = t0 + t;
+              if (tt < a.n_t) {
+                over += fmaxf(m[r][t] - lim, 0.f);
+                cnt += m[r][t] > lim ? 1.f : 0.f;
+                ml = fmaxf(ml, fmaxf(fabsf(f[r][t]), m[r][t]) / lim);
+                if (a.fmax) a.fmax[(bt * a.n_t + tt) * a.E_mon + row] = m[r][t];
+              }
             }
           }
         }
@@ -378,18 +415,6 @@ __global__ void __launch_bounds__(kUThreads, 1)
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kUTmemCols) : "memory");
   }
-}
-
-// -N in row-quad order per band of 128 rows: Nq[band][c / 4][r][c % 4] =
-// -N[128 band + r][c].
-__global__ void quad_N_kernel(const float* __restrict__ Nmo, float4* __restrict__ Nq, int n_bands, int O_pad) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const size_t nq = (size_t)O_pad / 4;
-  if (i >= (size_t)n_bands * nq * 128) return;
-  const int r = (int)(i % 128);
-  const size_t cq = (i / 128) % nq, band = i / (128 * nq);
-  const float* src = Nmo + ((size_t)band * 128 + r) * O_pad + 4 * cq;
-  Nq[i] = make_float4(-src[0], -src[1], -src[2], -src[3]);
 }
 
 __device__ __forceinline__ uint32_t tf32_bits(float x) {
@@ -468,20 +493,14 @@ int launch_umma_tc(EvalArgs& a, int tci, cudaStream_t s) {
 
 }  // namespace
 
-int ensure_quad_N(tto_grid* g, cudaStream_t s) {
-  if (g->d_Nq) return TTO_OK;
-  const int n_bands = g->E_mon_pad / 128;
-  const size_t n4 = (size_t)n_bands * (g->O_pad / 4) * 128;
-  TTO_CUDA_TRY(cudaMalloc(&g->d_Nq, n4 * sizeof(float4)));
-  quad_N_kernel<<<(unsigned)((n4 + 255) / 256), 256, 0, s>>>(g->d_Nmo, g->d_Nq, n_bands, g->O_pad);
-  TTO_CUDA_TRY(cudaGetLastError());
-  return TTO_OK;
-}
-
 int launch_sweep_umma(EvalArgs& a, cudaStream_t s) {
   if (a.precision != TTO_PREC_TF32X3) return set_error(TTO_E_ARG, "the tcgen05 sweep runs in TF32X3 only");
   if (a.E_mon_pad % 128 != 0 || a.O_pad % kUNC != 0) return set_error(TTO_E_ARG, "padding does not fit the tcgen05 tiles");
-  if (!a.Nq) return set_error(TTO_E_ARG, "quad-ordered -N missing");
+  if (!a.Nf) return set_error(TTO_E_ARG, "fragment-ordered -N missing");
+  // at most 4 timesteps per pass (the running maxima of 4 rows x 4 timesteps
+  // stay in registers); more timesteps take more passes
+  a.TC = a.TT < 4 ? a.TT : 4;
+  a.n_tch = a.TT / a.TC;
   const size_t threads = ((size_t)a.E_mon_pad + a.O_pad) * a.B;
   pack_umma_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
   TTO_CUDA_TRY(cudaGetLastError());
@@ -492,7 +511,6 @@ int launch_sweep_umma(EvalArgs& a, cudaStream_t s) {
       case 1: rc = launch_umma_tc<1>(a, ci, s); break;
       case 2: rc = launch_umma_tc<2>(a, ci, s); break;
       case 4: rc = launch_umma_tc<4>(a, ci, s); break;
-      case 8: rc = launch_umma_tc<8>(a, ci, s); break;
       default: return set_error(TTO_E_ARG, "unsupported timestep chunk %d", a.TC);
     }
     if (rc) return rc;

@@ -71,7 +71,6 @@ struct tto_grid {
   // device copies
   float* d_Nmo = nullptr;      // [E_mon_pad][O_pad] N[mon l][out c], FP32
   float4* d_Nf = nullptr;      // -N in mma C-fragment order, built on first tensor-core use
-  float4* d_Nq = nullptr;      // -N in row-quad order per 128-row band, built with d_Nf
   double* d_Nsw = nullptr;     // [n_sw][E] full N columns of movable branches, FP64
   int* d_swcol = nullptr;      // [E] column of a movable branch in d_Nsw, else -1
   double* d_f0 = nullptr;      // [T][E] base flows
