@@ -470,7 +470,9 @@ def main():
         instr = 2.0 * B * T * E_mon * O  # one FMA + one |.|-max per (topology, t, l, c)
         achieved = instr / (sweep_ms / 1000.0) / 1e12
         peak = sms * 128 * sm_mhz * 1e6 / 1e12
-        traffic = ncu_traffic("sweep_fp32" if prec == PREC_FP32 else "sweep_tc", args.config)
+        kname = ("sweep_fp32" if prec == PREC_FP32 else
+                 ("sweep_umma" if prec == PREC_TF32X3 and tuned_shape == 4 else "sweep_tc"))
+        traffic = ncu_traffic(kname, args.config)
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             cores = os.cpu_count() or 1
@@ -489,7 +491,7 @@ def main():
                        "sweep_variant": {"chosen": tuned_shape, "ms_per_variant_at_B512": tuned_ms}},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "N-1 sweep", "sweep_ms_per_launch": sweep_ms,
+                         "kernel": f"N-1 sweep ({kname}, variant {tuned_shape})", "sweep_ms_per_launch": sweep_ms,
                          "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({pk_kind} SM max clock)"},
             "stage_ms_per_step": {"split_update": stage_ms[0] / max(ncalls, 1), "sweep": sweep_ms,
                                   "metrics": stage_ms[2] / max(ncalls, 1)},
