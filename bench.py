@@ -261,6 +261,7 @@ def run_surrogate(args, prec):
     ds, dm = c["archive"]
     sg, g, _ = make_grid(cfg, 0, seed=0)
     g.reserve(B)
+    g.autotune(512, precision=prec)
     sur_kw = dict(hidden=512, n_load=256, replay=262144, minibatch=8192, lr=1e-3)
     variants = []
     for v in args.variants.split(","):
