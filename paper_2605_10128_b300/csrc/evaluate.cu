@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
   __shared__ int s_injbus[TTO_MAX_K];
   __shared__ double s_K[TTO_MAX_K][TTO_MAX_K];
   __shared__ double s_Ki[TTO_MAX_K][TTO_MAX_K];
+  __shared__ float s_Kif[TTO_MAX_K][TTO_MAX_K];  // FP32 copy for the monitored rows' U
   __shared__ double s_rhs[TTO_MAX_T][TTO_MAX_K];
   __shared__ double s_psi[TTO_MAX_T][TTO_MAX_K];
   __shared__ double s_sb[TTO_MAX_K];
@@ -178,7 +179,10 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
           for (int q = i + 1; q < k; ++q) v -= L[q][i] * x[q];
           x[i] = v;
         }
-        for (int i = 0; i < k; ++i) s_Ki[i][c] = x[i];
+        for (int i = 0; i < k; ++i) {
+          s_Ki[i][c] = x[i];
+          s_Kif[i][c] = (float)x[i];
+        }
       }
     }
   }
@@ -208,16 +212,20 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
       continue;
     }
     double W[TTO_MAX_K];
+    float Wf[TTO_MAX_K];
     for (int j = 0; j < k; ++j) {
       double w = 0.0;
       for (int q = s_slot[j]; q < s_slot[j + 1]; ++q) w += s_coef[q] * s_col[q][e];
       W[j] = w;
+      Wf[j] = (float)w;
     }
+    // U of a monitored row only enters the TF32-split contraction: FP32 is
+    // exact enough and spares the slow FP64 pipe k^2 products per row
     for (int jj = 0; jj < TTO_MAX_K; ++jj) {
-      double uu = 0.0;
+      float uu = 0.f;
       if (jj < k)
-        for (int j = 0; j < k; ++j) uu += W[j] * s_Ki[j][jj];
-      u[jj] = (float)uu;
+        for (int j = 0; j < k; ++j) uu = fmaf(Wf[j], s_Kif[j][jj], uu);
+      u[jj] = uu;
       umax = fmaxf(umax, fabsf(u[jj]));
     }
     store_row_factors(a, b, l, u);
