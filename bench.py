@@ -34,6 +34,27 @@ UNIT = "evals/s"
 LAUNCHES_PER_STEP = 8  # propose, split update, sweep, metrics, 4 insert kernels (+1 pack on tensor cores)
 
 
+def rank_seed(rank):
+    """Search seed of a rank: every rank runs its own independent search."""
+    return 1000 + rank
+
+
+def max_over_ranks(ms, world, device):
+    """The largest of the ranks' times (collective over the default group)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(per_rank_units, world, steps, max_ms):
+    """Whole-job units per second: every rank's units over the slowest rank's time."""
+    return per_rank_units * world * steps / (max_ms / 1000.0)
+
+
 def workload_desc(cfg, B):
     c = CONFIGS[cfg]
     return (f"{cfg}: synthetic {c['n_bus']}-bus grid, {c['n_branch']} branches, "
@@ -399,7 +420,7 @@ def main():
     else:
         tuned_shape, tuned_ms = g.autotune(min(B, 512), precision=prec)
     A = Archive(g, ds, dm)
-    seed = 1000 + rank
+    seed = rank_seed(rank)
     stream = torch.cuda.current_stream()
 
     for it in range(args.warmup):
@@ -427,11 +448,8 @@ def main():
     elapsed_ms = t0.elapsed_time(t1)
     stage_ms, ncalls = g.profile_read()
     g.sync_status()
-    if world > 1:
-        tt = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(tt.item())
-    value = B * world * args.steps / (elapsed_ms / 1000.0)
+    elapsed_ms = max_over_ranks(elapsed_ms, world, "cuda")
+    value = job_throughput(B, world, args.steps, elapsed_ms)
 
     # end to end through the C ABI: pinned host topologies in, fitness out
     topo_h = torch.from_numpy(random_topologies(sg, B, seed=77 + rank)).pin_memory()
@@ -453,11 +471,8 @@ def main():
     e1.record(stream)
     barrier()
     e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        tt = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
-    e2e = B * world * args.steps / (e2e_ms / 1000.0)
+    e2e_ms = max_over_ranks(e2e_ms, world, "cuda")
+    e2e = job_throughput(B, world, args.steps, e2e_ms)
 
     if rank == 0:
         pk, pk_kind = peaks()
