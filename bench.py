@@ -270,9 +270,11 @@ def run_surrogate(args, prec):
     candidates per iteration, scores them, evaluates the best-ranked 8192
     exactly (rank "score": by predicted fitness; "gain": by predicted gain over
     the cell's elite, empty cells first), then runs --train-steps training
-    steps.  The target of a seed is the best fitness its plain run reaches in
-    --iters iterations; each arm's time to target is the wall time of the
-    first iteration whose archive holds a fitness at least as good."""
+    steps; "rank:n@w" runs plain iterations (whose exact pairs still train
+    the surrogate) before screening from iteration w on.  The target of a
+    seed is the best fitness its plain run reaches in --iters iterations;
+    each arm's time to target is the wall time of the first iteration whose
+    archive holds a fitness at least as good."""
     import torch
     from scipy.stats import spearmanr
     from paper_2605_10128_b300 import Archive, Surrogate, SCREEN_SCORE, SCREEN_CELL_GAIN
@@ -286,8 +288,9 @@ def run_surrogate(args, prec):
     sur_kw = dict(hidden=512, n_load=256, replay=262144, minibatch=8192, lr=1e-3)
     variants = []
     for v in args.variants.split(","):
-        mode, n = v.split(":")
-        variants.append((v, {"score": SCREEN_SCORE, "gain": SCREEN_CELL_GAIN}[mode], int(n)))
+        mode, rest = v.split(":")
+        n, _, w = rest.partition("@")
+        variants.append((v, {"score": SCREEN_SCORE, "gain": SCREEN_CELL_GAIN}[mode], int(n), int(w or 0)))
     # warm-up: lazily built device data and every kernel of both arms
     wa = Archive(g, ds, dm)
     ws = Surrogate(g, seed=1, **sur_kw)
@@ -304,9 +307,16 @@ def run_surrogate(args, prec):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         curve = []
+        topo_o = torch.empty(B, g.k_max, dtype=torch.int32, device="cuda")
+        fit_o = torch.empty(B, dtype=torch.float32, device="cuda")
         for it in range(args.iters):
             if S is None:
                 A.step(seed, it, B, precision=prec)
+            elif it < variant[3]:
+                # warm start: plain iteration whose exact pairs train the surrogate
+                A.step(seed, it, B, precision=prec, topo_out=topo_o, fitness_out=fit_o)
+                S.add(topo_o, fit_o)
+                S.train(args.train_steps, want_loss=False)
             else:
                 A.step_screened(S, seed, it, variant[2], B, rank_by=variant[1], precision=prec,
                                 train_steps=args.train_steps)
@@ -377,8 +387,9 @@ def main():
                     help="fix the sweep tile variant instead of autotuning (4 = tcgen05, TF32X3 only)")
     ap.add_argument("--iters", type=int, default=60, help="--config surrogate: iterations per arm")
     ap.add_argument("--seeds", type=int, default=3, help="--config surrogate: seeds")
-    ap.add_argument("--variants", default="score:16384,score:65536",
-                    help="--config surrogate: screened variants rank:proposals (rank = score or gain)")
+    ap.add_argument("--variants", default="score:16384,score:65536,score:16384@16,score:65536@16",
+                    help="--config surrogate: screened variants rank:proposals[@first screened iteration] "
+                         "(rank = score or gain)")
     ap.add_argument("--train-steps", type=int, default=8, help="--config surrogate: training steps per iteration")
     args = ap.parse_args()
 
