@@ -520,6 +520,8 @@ def main():
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": f"N-1 sweep ({kname}, variant {tuned_shape})", "sweep_ms_per_launch": sweep_ms,
                          "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({pk_kind} SM max clock)"},
+            "pair_rate": {"value": B * world * T * E_mon * O * args.steps / (elapsed_ms / 1000.0),
+                          "unit": "(topology, t, monitored branch, outage) pairs/s"},
             "stage_ms_per_step": {"split_update": stage_ms[0] / max(ncalls, 1), "sweep": sweep_ms,
                                   "metrics": stage_ms[2] / max(ncalls, 1)},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(B * g.k_max * 4),

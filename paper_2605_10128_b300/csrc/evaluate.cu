@@ -57,12 +57,15 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
   __shared__ double s_sign[kMaxMoved];
   __shared__ double s_coef[kMaxMoved];
   __shared__ const double* s_col[kMaxMoved];
+  __shared__ const float* s_col32[kMaxMoved];
+  __shared__ float s_coef32[kMaxMoved];
   __shared__ int s_injbus[TTO_MAX_K];
   __shared__ double s_K[TTO_MAX_K][TTO_MAX_K];
   __shared__ double s_Ki[TTO_MAX_K][TTO_MAX_K];
   __shared__ float s_Kif[TTO_MAX_K][TTO_MAX_K];  // FP32 copy for the monitored rows' U
   __shared__ double s_rhs[TTO_MAX_T][TTO_MAX_K];
   __shared__ double s_psi[TTO_MAX_T][TTO_MAX_K];
+  __shared__ float s_psi32[TTO_MAX_T][TTO_MAX_K];
   __shared__ double s_sb[TTO_MAX_K];
   __shared__ int s_cnt_c0, s_cnt_isl;
   __shared__ float s_umax, s_vmax;
@@ -102,6 +105,8 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
         s_sign[ne] = sg;
         s_coef[ne] = sg * a.b[e];
         s_col[ne] = a.Nsw + (size_t)a.swcol[e] * a.E;
+        s_coef32[ne] = (float)(sg * a.b[e]);
+        s_col32[ne] = a.Nsw32 + (size_t)a.swcol[e] * a.E;
         ++ne;
       }
       ++k;
@@ -193,6 +198,7 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
     double v = 0.0;
     for (int q = 0; q < k; ++q) v += s_Ki[j][q] * s_rhs[t][q];
     s_psi[t][j] = v;
+    s_psi32[t][j] = (float)v;
   }
   __syncthreads();
 
@@ -211,16 +217,26 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
       for (int t = 0; t < TT; ++t) a.fp[((size_t)b * TT + t) * a.E_mon_pad + l] = 0.f;
       continue;
     }
-    double W[TTO_MAX_K];
-    float Wf[TTO_MAX_K];
+    // FP32 first (B300's FP64 pipe is narrow): W from the FP32 copy of the N
+    // columns, U = W K^-1, f' = f0 + W psi, with an a-priori bound on the
+    // rounding error of f': each FP32 sum of n terms errs by at most n u times
+    // the sum of the absolute terms (u = 2^-24), and W's own sums and the FP32
+    // N values add the same for W's terms, so |err f'| <= 32 u (|f0| + sum_j
+    // |W|_j |psi_j|) with |W|_j the sum of the absolute W terms.  A row whose
+    // bound exceeds 1e-5 of its limit is recomputed in FP64.
+    float Wf[TTO_MAX_K], Wa[TTO_MAX_K];
     for (int j = 0; j < k; ++j) {
-      double w = 0.0;
-      for (int q = s_slot[j]; q < s_slot[j + 1]; ++q) w += s_coef[q] * s_col[q][e];
-      W[j] = w;
-      Wf[j] = (float)w;
+      float w = 0.f, wa = 0.f;
+      for (int q = s_slot[j]; q < s_slot[j + 1]; ++q) {
+        const float n = s_col32[q][e];
+        w = fmaf(s_coef32[q], n, w);
+        wa = fmaf(fabsf(s_coef32[q]), fabsf(n), wa);
+      }
+      Wf[j] = w;
+      Wa[j] = wa;
     }
     // U of a monitored row only enters the TF32-split contraction: FP32 is
-    // exact enough and spares the slow FP64 pipe k^2 products per row
+    // exact enough
     for (int jj = 0; jj < TTO_MAX_K; ++jj) {
       float uu = 0.f;
       if (jj < k)
@@ -230,15 +246,37 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
     }
     store_row_factors(a, b, l, u);
     const float lim = a.lim[lr];
+    float fv[TTO_MAX_T];
+    bool fp32_ok = true;
     for (int t = 0; t < TT; ++t) {
-      float fv = 0.f;
+      fv[t] = 0.f;
       if (t < nt) {
+        const float f0 = (float)a.f0[(size_t)a.tsel[t] * a.E + e];
+        float f = f0, bound = fabsf(f0);
+        for (int j = 0; j < k; ++j) {
+          f = fmaf(Wf[j], s_psi32[t][j], f);
+          bound = fmaf(Wa[j], fabsf(s_psi32[t][j]), bound);
+        }
+        fv[t] = f;
+        fp32_ok = fp32_ok && bound * (32.f / 16777216.f) <= 1e-5f * lim;
+      }
+    }
+    if (!fp32_ok) {
+      double W[TTO_MAX_K];
+      for (int j = 0; j < k; ++j) {
+        double w = 0.0;
+        for (int q = s_slot[j]; q < s_slot[j + 1]; ++q) w += s_coef[q] * s_col[q][e];
+        W[j] = w;
+      }
+      for (int t = 0; t < nt; ++t) {
         double f = a.f0[(size_t)a.tsel[t] * a.E + e];
         for (int j = 0; j < k; ++j) f += W[j] * s_psi[t][j];
-        fv = (float)f;
-        if (l < a.E_mon && fabsf(fv) > lim) ++c0cnt;
+        fv[t] = (float)f;
       }
-      a.fp[((size_t)b * TT + t) * a.E_mon_pad + l] = fv;
+    }
+    for (int t = 0; t < TT; ++t) {
+      if (t < nt && l < a.E_mon && fabsf(fv[t]) > lim) ++c0cnt;
+      a.fp[((size_t)b * TT + t) * a.E_mon_pad + l] = fv[t];
     }
   }
   // outage rows: V, g, islanding of each outage
@@ -422,6 +460,7 @@ int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, 
   Workspace& w = g->ws;
   a.Nmo = g->d_Nmo;
   a.Nsw = g->d_Nsw;
+  a.Nsw32 = g->d_Nsw32;
   a.swcol = g->d_swcol;
   a.f0 = g->d_f0;
   a.p = g->d_p;

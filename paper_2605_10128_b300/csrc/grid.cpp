@@ -380,6 +380,11 @@ static int build_grid(const tto_grid_desc* d, tto_grid* g) {
   int rc;
   if ((rc = upload(&g->d_Nmo, Nmo.data(), Nmo.size()))) return rc;
   if ((rc = upload(&g->d_Nsw, Nsw.data(), Nsw.size()))) return rc;
+  {
+    std::vector<float> Nsw32(Nsw.size());
+    for (size_t i = 0; i < Nsw.size(); ++i) Nsw32[i] = (float)Nsw[i];
+    if ((rc = upload(&g->d_Nsw32, Nsw32.data(), Nsw32.size()))) return rc;
+  }
   if ((rc = upload(&g->d_swcol, swcol.data(), swcol.size()))) return rc;
   if ((rc = upload(&g->d_f0, g->f0.data(), g->f0.size()))) return rc;
   if ((rc = upload(&g->d_p, g->p.data(), g->p.size()))) return rc;
@@ -407,7 +412,7 @@ static void release(tto_grid* g) {
   cudaSetDevice(g->device);
   forget_grid_graphs(g);
   free_workspace(g);
-  void* ptrs[] = {g->d_from, g->d_Nf, g->d_Nmo, g->d_Nsw, g->d_swcol, g->d_f0, g->d_p, g->d_b, g->d_lim,
+  void* ptrs[] = {g->d_from, g->d_Nf, g->d_Nmo, g->d_Nsw, g->d_Nsw32, g->d_swcol, g->d_f0, g->d_p, g->d_b, g->d_lim,
                   g->d_mon, g->d_out, g->d_Ncc, g->d_station_bus, g->d_asset_off,
                   g->d_asset_br, g->d_act_st, g->d_act_off, g->d_act_mask, g->d_status};
   for (void* p : ptrs)

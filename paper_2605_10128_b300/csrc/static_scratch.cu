@@ -105,6 +105,7 @@ extern "C" int tto_evaluate_batch_static(tto_grid* g, const int32_t* topo, int32
 
   a.Nmo = g->d_Nmo;
   a.Nsw = g->d_Nsw;
+  a.Nsw32 = g->d_Nsw32;
   a.swcol = g->d_swcol;
   a.f0 = g->d_f0;
   a.p = g->d_p;

@@ -12,6 +12,7 @@ struct EvalArgs {
   const float* Nmo;
   const float4* Nf;  // -N in mma C-fragment order (tensor-core sweep)
   const double* Nsw;
+  const float* Nsw32;  // FP32 copy of Nsw
   const int* swcol;
   const double* f0;
   const double* p;

@@ -72,6 +72,7 @@ struct tto_grid {
   float* d_Nmo = nullptr;      // [E_mon_pad][O_pad] N[mon l][out c], FP32
   float4* d_Nf = nullptr;      // -N in mma C-fragment order, built on first tensor-core use
   double* d_Nsw = nullptr;     // [n_sw][E] full N columns of movable branches, FP64
+  float* d_Nsw32 = nullptr;    // [n_sw][E] FP32 copy (monitored rows of the split update)
   int* d_swcol = nullptr;      // [E] column of a movable branch in d_Nsw, else -1
   double* d_f0 = nullptr;      // [T][E] base flows
   double* d_p = nullptr;       // [T][n_bus]
