@@ -228,7 +228,9 @@ int tto_evaluate_batch_static(tto_grid* g, const int32_t* topo, int32_t B, const
                               void* stream);
 
 /* Synchronise the stream and return (then clear) the device status word:
- * TTO_OK, TTO_E_TOPOLOGY or TTO_E_TIMEOUT. */
+ * TTO_OK, TTO_E_TOPOLOGY or TTO_E_TIMEOUT.  After a TTO_E_TIMEOUT (a bounded
+ * wait inside a sweep gave up), tcgen05 sweeps on the grid return at once
+ * until this call clears the word. */
 int tto_grid_sync_status(tto_grid* g, void* stream);
 
 /* Archive of d_split x d_moved cells, one elite per cell, device resident.

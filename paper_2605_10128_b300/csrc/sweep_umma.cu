@@ -85,13 +85,16 @@ __device__ __forceinline__ bool bar_try(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait; false when it gave up or another role raised the abort flag.
-__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+// Bounded wait; false when it gave up, when another role of the CTA raised
+// the abort flag, or when another CTA already timed out (status word), so that
+// one timeout ends the whole launch within about a second.
+__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag,
+                                         const volatile int* status) {
   if (bar_try(b, parity)) return true;
   const long long t0 = clock64();
   for (;;) {
     if (bar_try(b, parity)) return true;
-    if (*abort_flag) return false;
+    if (*abort_flag || *status == TTO_E_TIMEOUT) return false;
     if (clock64() - t0 > kUWaitCycles) return false;
   }
 }
@@ -211,6 +214,7 @@ __global__ void __launch_bounds__(kUThreads, 1)
   const int band = (tile % tiles_b) * 16 + within % 16;
   const int grp = (tile / tiles_b) * 16 + within / 16;
   if (band >= n_bands || grp >= n_groups) return;  // CTA-uniform, before any barrier or allocation
+  if (*(const volatile int*)a.status == TTO_E_TIMEOUT) return;  // an earlier CTA gave up: end at once
   const int n_topo = min(kUTopo, a.B - grp * kUTopo);
   const int n_chunks = a.O_pad / kUNC;
   unsigned char* smA = smem;                          // [topo][hi, lo][128 x 8]
@@ -250,7 +254,7 @@ __global__ void __launch_bounds__(kUThreads, 1)
       bulk_g2s(smA + b * kUA, a.Ua + (((size_t)(grp * kUTopo + b) * n_bands + band) * (kUA / 4)), kUA, &bar_a);
     for (int s = 0; s < n_chunks; ++s) {
       const int slot = s % kUStages;
-      if (s >= kUStages && !bar_wait(&empty[slot], (uint32_t)((s / kUStages) - 1) & 1u, abort_flag)) {
+      if (s >= kUStages && !bar_wait(&empty[slot], (uint32_t)((s / kUStages) - 1) & 1u, abort_flag, a.status)) {
         give_up();
         break;
       }
@@ -269,19 +273,19 @@ __global__ void __launch_bounds__(kUThreads, 1)
       issued = s + 1;
     }
   } else if (warp == 1 && lane == 0) {
-    if (!bar_wait(&bar_a, 0, abort_flag)) {
+    if (!bar_wait(&bar_a, 0, abort_flag, a.status)) {
       give_up();
     } else {
       for (int s = 0; s < n_chunks; ++s) {
         const int slot = s % kUStages, buf = s & 1;
-        if (!bar_wait(&full[slot], (uint32_t)(s / kUStages) & 1u, abort_flag)) {
+        if (!bar_wait(&full[slot], (uint32_t)(s / kUStages) & 1u, abort_flag, a.status)) {
           give_up();
           break;
         }
         const unsigned char* st = smS + (size_t)slot * C::kStage;
         bool ok = true;
         for (int b = 0; b < n_topo; ++b) {
-          if (s >= 2 && !bar_wait(&tempty[b][buf], (uint32_t)((s >> 1) - 1) & 1u, abort_flag)) {
+          if (s >= 2 && !bar_wait(&tempty[b][buf], (uint32_t)((s >> 1) - 1) & 1u, abort_flag, a.status)) {
             give_up();
             ok = false;
             break;
@@ -318,8 +322,8 @@ __global__ void __launch_bounds__(kUThreads, 1)
       bool ok = true;
       for (int s = 0; s < n_chunks && ok; ++s) {
         const int slot = s % kUStages, buf = s & 1;
-        ok = __all_sync(0xffffffffu, bar_wait(&full[slot], (uint32_t)(s / kUStages) & 1u, abort_flag) &&
-                                         bar_wait(&tfull[b][buf], (uint32_t)(s >> 1) & 1u, abort_flag));
+        ok = __all_sync(0xffffffffu, bar_wait(&full[slot], (uint32_t)(s / kUStages) & 1u, abort_flag, a.status) &&
+                                         bar_wait(&tfull[b][buf], (uint32_t)(s >> 1) & 1u, abort_flag, a.status));
         if (!ok) break;
         tc_fence_after();
         const unsigned char* st = smS + (size_t)slot * C::kStage;
@@ -403,12 +407,12 @@ __global__ void __launch_bounds__(kUThreads, 1)
   if (warp == 0 && lane == 0) {
     for (int s = issued > kUStages ? issued - kUStages : 0; s < issued; ++s) {
       int dummy = 0;
-      bar_wait(&full[s % kUStages], (uint32_t)(s / kUStages) & 1u, &dummy);
+      bar_wait(&full[s % kUStages], (uint32_t)(s / kUStages) & 1u, &dummy, &dummy);
     }
   } else if (warp == 1 && lane == 0) {
     int dummy = 0;
     umma_commit(&mma_done);
-    bar_wait(&mma_done, 0, &dummy);
+    bar_wait(&mma_done, 0, &dummy, &dummy);
   }
   __syncthreads();
   if (warp == 1) {
