@@ -227,6 +227,14 @@ int tto_evaluate_batch_static(tto_grid* g, const int32_t* topo, int32_t B, const
                               int32_t* cell, uint8_t* island, float* metrics, float* fmax,
                               void* stream);
 
+/* Test hook for the timeout path (the paper has no counterpart): runs one
+ * thread that waits, through the sweeps' own bounded-wait routine, on an
+ * mbarrier that nothing completes, for at most `cycles` SM clock cycles
+ * (1 .. 2^32); when the wait gives up it writes TTO_E_TIMEOUT to the grid's
+ * status word as a sweep would.  Faults, traps and unbounded waits are never
+ * used.  Asynchronous on stream. */
+int tto_debug_bounded_wait(tto_grid* g, int64_t cycles, void* stream);
+
 /* Synchronise the stream and return (then clear) the device status word:
  * TTO_OK, TTO_E_TOPOLOGY or TTO_E_TIMEOUT.  After a TTO_E_TIMEOUT (a bounded
  * wait inside a sweep gave up), tcgen05 sweeps on the grid return at once

@@ -102,6 +102,10 @@ class Grid:
     def sync_status(self, stream=None):
         _lib.tto_grid_sync_status(self._h, _stream(stream))
 
+    def debug_bounded_wait(self, cycles=2_000_000, stream=None):
+        """Make one bounded device wait run out (timeout-path test)."""
+        _lib.tto_debug_bounded_wait(self._h, cycles, _stream(stream))
+
     def autotune(self, B, n_t=None, precision=PREC_FP32, stream=None):
         """Time the sweep tile variants on this grid and keep the fastest;
         returns (variant, [ms per variant])."""

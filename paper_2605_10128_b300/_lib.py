@@ -84,6 +84,7 @@ _SIGS = {
     "tto_evaluate_batch_static": ([_vp, _vp, C.c_int32, _i32p, C.c_int32, C.POINTER(EvalOpts), _vp,
                                    _vp, _vp, _vp, _vp, _vp, _vp], C.c_int),
     "tto_grid_sync_status": ([_vp, _vp], C.c_int),
+    "tto_debug_bounded_wait": ([_vp, C.c_int64, _vp], C.c_int),
     "tto_grid_autotune": ([_vp, C.c_int32, C.c_int32, C.c_int32, _i32p, C.POINTER(C.c_float), _vp], C.c_int),
     "tto_grid_set_sweep_shape": ([_vp, C.c_int32, C.c_int32], C.c_int),
     "tto_evaluate_multi": ([C.POINTER(EvalJob), C.c_int32, C.POINTER(EvalOpts), C.c_int32, _vp], C.c_int),
@@ -287,6 +288,10 @@ def tto_evaluate_multi(jobs, opts, mode, stream):
         for f in ("fitness", "desc", "cell", "island", "metrics"):
             setattr(e, f, _dp(j.get(f)))
     return check(lib().tto_evaluate_multi(arr, len(jobs), C.byref(opts), int(mode), _vp(stream)))
+
+
+def tto_debug_bounded_wait(h, cycles, stream):
+    return check(lib().tto_debug_bounded_wait(h, int(cycles), _vp(stream)))
 
 
 def tto_grid_sync_status(h, stream):

@@ -581,6 +581,12 @@ int tto_grid_profile_read(tto_grid* g, float* ms_stage, int32_t* n_calls) {
   return TTO_OK;
 }
 
+int tto_debug_bounded_wait(tto_grid* g, int64_t cycles, void* stream) {
+  if (!g || cycles < 1 || cycles > (int64_t)1 << 32) return tto::set_error(TTO_E_ARG, "cycles must be in [1, 2^32]");
+  TTO_CUDA_TRY(cudaSetDevice(g->device));
+  return tto::bounded_wait_probe(g->d_status, (long long)cycles, (cudaStream_t)stream);
+}
+
 int tto_grid_sync_status(tto_grid* g, void* stream) {
   if (!g) return tto::set_error(TTO_E_ARG, "null grid");
   TTO_CUDA_TRY(cudaSetDevice(g->device));

@@ -70,6 +70,8 @@ int sweep_shapes(int precision);
 size_t max_parts(const tto_grid* g);
 // Build the fragment-ordered copy of -N used by the tensor-core sweep (once).
 int ensure_fragment_N(tto_grid* g, cudaStream_t s);
+// One bounded wait on an mbarrier nothing completes (timeout-path test).
+int bounded_wait_probe(int* status, long long cycles, cudaStream_t s);
 // The tcgen05 sweep (TF32X3 only); sets a.n_parts.
 int launch_sweep_umma(EvalArgs& a, cudaStream_t s);
 // Sweep tile variant of TF32X3 that runs the tcgen05 kernel.

@@ -89,14 +89,26 @@ __device__ __forceinline__ bool bar_try(uint64_t* b, uint32_t parity) {
 // the abort flag, or when another CTA already timed out (status word), so that
 // one timeout ends the whole launch within about a second.
 __device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag,
-                                         const volatile int* status) {
+                                         const volatile int* status, long long limit = kUWaitCycles) {
   if (bar_try(b, parity)) return true;
   const long long t0 = clock64();
   for (;;) {
     if (bar_try(b, parity)) return true;
     if (*abort_flag || *status == TTO_E_TIMEOUT) return false;
-    if (clock64() - t0 > kUWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   }
+}
+
+// One thread waits, through the sweep's bounded wait, on an mbarrier that
+// nothing completes; when the wait gives up it records TTO_E_TIMEOUT exactly
+// as a sweep does.
+__global__ void bounded_wait_probe_kernel(int* status, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int s_abort;
+  bar_init(&bar, 1);
+  s_abort = 0;
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (!bar_wait(&bar, 0, &s_abort, status, limit)) atomicExch(status, TTO_E_TIMEOUT);
 }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
   asm volatile(
@@ -496,6 +508,12 @@ int launch_umma_tc(EvalArgs& a, int tci, cudaStream_t s) {
 }
 
 }  // namespace
+
+int bounded_wait_probe(int* status, long long cycles, cudaStream_t s) {
+  bounded_wait_probe_kernel<<<1, 1, 0, s>>>(status, cycles);
+  TTO_CUDA_TRY(cudaGetLastError());
+  return TTO_OK;
+}
 
 int launch_sweep_umma(EvalArgs& a, cudaStream_t s) {
   if (a.precision != TTO_PREC_TF32X3) return set_error(TTO_E_ARG, "the tcgen05 sweep runs in TF32X3 only");
