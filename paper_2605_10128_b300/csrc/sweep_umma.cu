@@ -164,46 +164,73 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&r0)[8], uint32_t (&r1)[8
                : "memory");
 }
 
+// Packed pairs of FP32 values in one 64-bit register (sm_100 family):
+// add.rn.f32x2 / fma.rn.f32x2 process two elements per instruction, and the
+// three-input max takes both absolute values at once.
+__device__ __forceinline__ uint64_t pack2(float x, float y) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+  return r;
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+// max(m, |v.x|, |v.y|)
+__device__ __forceinline__ float max_abs_pair(float m, uint64_t v) {
+  float r;
+  asm("{\n .reg .f32 x, y;\n mov.b64 {x, y}, %2;\n abs.f32 x, x;\n abs.f32 y, y;\n max.f32 %0, %1, x, y;\n}"
+      : "=f"(r)
+      : "f"(m), "l"(v));
+  return r;
+}
+
 // One step of 16 columns (two 8-column blocks): A holds U V^T of rows {r,
 // r+8} and B of rows {r+16, r+24} of the warp's 32 (r = lane / 4), columns
-// 2 (lane % 4) + {0, 1} of each block; nf points at this lane's -N fragment
-// of the first 16-row tile and block (the second 16-row tile is 8 fragment
-// tiles further on); g values of the two columns are loaded once for the 4 rows.
+// 2 (lane % 4) + {0, 1} of each block, adjacent registers; nf points at this
+// lane's -N fragment of the first 16-row tile and block (the second 16-row
+// tile is 8 fragment tiles further on); gs holds g of column pairs with the
+// two columns interleaved per timestep, so each 64-bit load is the g pair of
+// one timestep.  f2 holds (f', f') per row and timestep.
 template <int TC>
 __device__ __forceinline__ void epilogue_step(const uint32_t (&A)[8], const uint32_t (&B)[8], const float4* nf,
-                                              const float* gs, int c0, const float (&f)[4][TC],
+                                              const float* gs, int c0, const uint64_t (&f2)[4][TC],
                                               float (&m)[4][TC]) {
 #pragma unroll
   for (int blk = 0; blk < 2; ++blk) {
-    const float4 na = nf[(c0 / 8 + blk) * 32], nb = nf[(8 + c0 / 8 + blk) * 32];
-    const int c = c0 + 8 * blk + 2 * (threadIdx.x & 3);
-    float g[2 * TC];  // g[c][0..TC), g[c + 1][0..TC)
-    if constexpr (2 * TC >= 4) {
+    const ulonglong2 na = *reinterpret_cast<const ulonglong2*>(nf + (c0 / 8 + blk) * 32);
+    const ulonglong2 nb = *reinterpret_cast<const ulonglong2*>(nf + (8 + c0 / 8 + blk) * 32);
+    const int pair = (c0 + 8 * blk) / 2 + (threadIdx.x & 3);
+    uint64_t g[TC];  // (g[c][t], g[c + 1][t])
+    if constexpr (TC >= 2) {
 #pragma unroll
       for (int x = 0; x < TC / 2; ++x) {
-        const float4 v = *reinterpret_cast<const float4*>(gs + c * TC + 4 * x);
-        g[4 * x] = v.x;
-        g[4 * x + 1] = v.y;
-        g[4 * x + 2] = v.z;
-        g[4 * x + 3] = v.w;
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(gs + pair * 2 * TC + 4 * x);
+        g[2 * x] = v.x;
+        g[2 * x + 1] = v.y;
       }
     } else {
-      const float2 v = *reinterpret_cast<const float2*>(gs + c);
-      g[0] = v.x;
-      g[1] = v.y;
+      g[0] = *reinterpret_cast<const uint64_t*>(gs + pair * 2);
     }
-    const float d[4][2] = {{__uint_as_float(A[4 * blk]) + na.x, __uint_as_float(A[4 * blk + 1]) + na.y},
-                           {__uint_as_float(A[4 * blk + 2]) + na.z, __uint_as_float(A[4 * blk + 3]) + na.w},
-                           {__uint_as_float(B[4 * blk]) + nb.x, __uint_as_float(B[4 * blk + 1]) + nb.y},
-                           {__uint_as_float(B[4 * blk + 2]) + nb.z, __uint_as_float(B[4 * blk + 3]) + nb.w}};
+    const uint64_t d[4] = {add2(pack2(__uint_as_float(A[4 * blk]), __uint_as_float(A[4 * blk + 1])), na.x),
+                           add2(pack2(__uint_as_float(A[4 * blk + 2]), __uint_as_float(A[4 * blk + 3])), na.y),
+                           add2(pack2(__uint_as_float(B[4 * blk]), __uint_as_float(B[4 * blk + 1])), nb.x),
+                           add2(pack2(__uint_as_float(B[4 * blk + 2]), __uint_as_float(B[4 * blk + 3])), nb.y)};
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
-      for (int t = 0; t < TC; ++t)
-        m[r][t] = fmaxf(m[r][t], fmaxf(fabsf(fmaf(d[r][0], g[t], f[r][t])), fabsf(fmaf(d[r][1], g[TC + t], f[r][t]))));
+      for (int t = 0; t < TC; ++t) m[r][t] = max_abs_pair(m[r][t], fma2(d[r], g[t], f2[r][t]));
   }
 }
 
+// 96 registers per thread: the most a 576-thread block can be given (at 104
+// the driver allows 512 threads per block; measured).
 template <int TC>
 __global__ void __launch_bounds__(kUThreads, 1)
     sweep_umma_kernel(EvalArgs a, int tci, int n_bands, int n_groups) {
@@ -323,12 +350,14 @@ __global__ void __launch_bounds__(kUThreads, 1)
       const int t0 = tci * TC;
       // rows of this thread within the band: 32 q + lane / 4 + {0, 8, 16, 24}
       const int rb = 32 * q + (lane >> 2);
-      float f[4][TC], m[4][TC];
+      float m[4][TC];
+      uint64_t f2[4][TC];  // (f', f') of every row and timestep
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int t = 0; t < TC; ++t) {
-          f[r][t] = a.fp[(bt * a.TT + t0 + t) * (size_t)a.E_mon_pad + band * 128 + rb + 8 * r];
+          const float fv = a.fp[(bt * a.TT + t0 + t) * (size_t)a.E_mon_pad + band * 128 + rb + 8 * r];
+          f2[r][t] = pack2(fv, fv);
           m[r][t] = 0.f;
         }
       bool ok = true;
@@ -350,17 +379,17 @@ __global__ void __launch_bounds__(kUThreads, 1)
         tmem_wait_ld(A0, B0);
         tmem_ld_2blk(lo + 16, A1);
         tmem_ld_2blk(hi + 16, B1);
-        epilogue_step<TC>(A0, B0, nf, gs, 0, f, m);
+        epilogue_step<TC>(A0, B0, nf, gs, 0, f2, m);
         tmem_wait_ld(A1, B1);
         tmem_ld_2blk(lo + 32, A0);
         tmem_ld_2blk(hi + 32, B0);
-        epilogue_step<TC>(A1, B1, nf, gs, 16, f, m);
+        epilogue_step<TC>(A1, B1, nf, gs, 16, f2, m);
         tmem_wait_ld(A0, B0);
         tmem_ld_2blk(lo + 48, A1);
         tmem_ld_2blk(hi + 48, B1);
-        epilogue_step<TC>(A0, B0, nf, gs, 32, f, m);
+        epilogue_step<TC>(A0, B0, nf, gs, 32, f2, m);
         tmem_wait_ld(A1, B1);
-        epilogue_step<TC>(A1, B1, nf, gs, 48, f, m);
+        epilogue_step<TC>(A1, B1, nf, gs, 48, f2, m);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) {
@@ -392,7 +421,7 @@ __global__ void __launch_bounds__(kUThreads, 1)
               if (tt < a.n_t) {
                 over += fmaxf(m[r][t] - lim, 0.f);
                 cnt += m[r][t] > lim ? 1.f : 0.f;
-                ml = fmaxf(ml, fmaxf(fabsf(f[r][t]), m[r][t]) / lim);
+                ml = fmaxf(ml, fmaxf(fabsf(__uint_as_float((uint32_t)f2[r][t])), m[r][t]) / lim);
                 if (a.fmax) a.fmax[(bt * a.n_t + tt) * a.E_mon + row] = m[r][t];
               }
             }
@@ -445,7 +474,8 @@ __device__ __forceinline__ uint32_t tf32_bits(float x) {
 __device__ __forceinline__ int canon(int row, int k) { return (row >> 3) * 64 + (k >> 2) * 32 + (row & 7) * 4 + (k & 3); }
 
 // U rows -> [B][band][hi, lo][128 x 8]; V columns -> [B][chunk][hi, lo][64 x 8];
-// g -> [B][t-chunk][O_pad][TC] (zero beyond the padded timesteps).
+// g -> [B][t-chunk][O_pad / 2][TC][2], column pairs interleaved (zero beyond
+// the padded timesteps).
 __global__ void pack_umma_kernel(EvalArgs a) {
   const int rows = a.E_mon_pad, cols = a.O_pad;
   const size_t per = (size_t)rows + cols;
@@ -477,10 +507,12 @@ __global__ void pack_umma_kernel(EvalArgs a) {
       base[canon(n, k)] = hi;
       base[512 + canon(n, k)] = tf32_bits(v[k] - __uint_as_float(hi));
     }
+    // g of column pairs, the two columns interleaved per timestep:
+    // [B][t-pass][O_pad / 2][TC][2]
     for (int ci = 0; ci < a.n_tch; ++ci)
       for (int t = 0; t < a.TC; ++t) {
         const int tt = ci * a.TC + t;
-        a.gq[(((size_t)b * a.n_tch + ci) * cols + c) * a.TC + t] =
+        a.gq[((((size_t)b * a.n_tch + ci) * (cols / 2) + c / 2) * a.TC + t) * 2 + (c & 1)] =
             tt < a.TT ? a.gg[((size_t)b * cols + c) * a.TT + tt] : 0.f;
       }
   }
@@ -503,7 +535,16 @@ int launch_umma_tc(EvalArgs& a, int tci, cudaStream_t s) {
   const size_t blocks = (size_t)tiles_b * tiles_g * 256;
   if (blocks > 0x7fffffffu) return set_error(TTO_E_ARG, "batch too large for one sweep launch");
   sweep_umma_kernel<TC><<<(unsigned)blocks, kUThreads, C::kSmem, s>>>(a, tci, n_bands, n_groups);
-  TTO_CUDA_TRY(cudaGetLastError());
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, sweep_umma_kernel<TC>);
+    return set_error(TTO_E_CUDA,
+                     "tcgen05 sweep launch: %s (threads %d, regs %d, max threads %d, static smem %zu, dynamic %u "
+                     "of max %d, local %zu)",
+                     cudaGetErrorString(e), kUThreads, fa.numRegs, fa.maxThreadsPerBlock, fa.sharedSizeBytes,
+                     C::kSmem, fa.maxDynamicSharedSizeBytes, fa.localSizeBytes);
+  }
   return TTO_OK;
 }
 
