@@ -386,8 +386,8 @@ def main():
     ap.add_argument("--sweep-variant", type=int, default=-1,
                     help="fix the sweep tile variant instead of autotuning (4 = tcgen05, TF32X3 only)")
     ap.add_argument("--iters", type=int, default=60, help="--config surrogate: iterations per arm")
-    ap.add_argument("--seeds", type=int, default=3, help="--config surrogate: seeds")
-    ap.add_argument("--variants", default="score:16384,score:65536,score:16384@16,score:65536@16",
+    ap.add_argument("--seeds", type=int, default=6, help="--config surrogate: seeds")
+    ap.add_argument("--variants", default="score:65536@16,score:65536@8",
                     help="--config surrogate: screened variants rank:proposals[@first screened iteration] "
                          "(rank = score or gain)")
     ap.add_argument("--train-steps", type=int, default=8, help="--config surrogate: training steps per iteration")
