@@ -18,7 +18,9 @@
 //                       into that topology's accumulator in tensor memory (two
 //                       64-column buffers per topology, 512 columns in all) and
 //                       commits them to an mbarrier;
-//   warps 2..17         four epilogue warpgroups, one per topology: each warp
+//   warps 2, 3          idle: they complete warpgroup 0, whose registers
+//                       (setmaxnreg) go to the epilogue;
+//   warps 4..19         four epilogue warpgroups, one per topology: each warp
 //                       reads its 32 accumulator lanes with tcgen05.ld.16x256b,
 //                       whose register layout is the mma C fragment (a thread
 //                       holds 4 rows x 2 columns of every 8-column block, so
@@ -48,7 +50,17 @@ constexpr int kUTopo = 4;                 // topologies per CTA (one epilogue wa
 constexpr int kUNC = 64;                  // outage columns per chunk (MMA N)
 constexpr int kUStages = 3;               // shared-memory ring slots
 constexpr int kUEpiWarps = 4 * kUTopo;    // 16 epilogue warps
-constexpr int kUThreads = 32 * (2 + kUEpiWarps);
+// warpgroup 0: producer (warp 0), MMA issuer (warp 1), two idle warps;
+// warpgroups 1-4: the epilogue
+constexpr int kUThreads = 32 * (4 + kUEpiWarps);
+// Register split (setmaxnreg): the block is launched at 96 registers per
+// thread (640 x 96 = 61440, five warps per sub-partition), warpgroup 0 gives
+// back down to 56 and the epilogue warps grow to 104: 128 x 56 + 512 x 104 =
+// 60416 registers, within the launch's 61440, so no increase can wait.
+constexpr int kULaunchRegs = 96, kUCtlRegs = 56, kUEpiRegs = 104;
+static_assert(128 * kUCtlRegs + 32 * kUEpiWarps * kUEpiRegs <= kUThreads * kULaunchRegs,
+              "register split exceeds the launch allocation");
+static_assert((kUThreads / 32 + 3) / 4 * 32 * kULaunchRegs <= 16384, "launch registers exceed a sub-partition");
 constexpr uint32_t kUTmemCols = 512;      // 4 topologies x 2 buffers x 64 columns
 constexpr uint32_t kUA = 2 * 128 * 8 * 4;        // U_hi + U_lo tiles of one topology (8 KB)
 constexpr uint32_t kUN = 128 * kUNC * 4;         // -N tile of a chunk (32 KB)
@@ -229,8 +241,9 @@ __device__ __forceinline__ void epilogue_step(const uint32_t (&A)[8], const uint
   }
 }
 
-// 96 registers per thread: the most a 576-thread block can be given (at 104
-// the driver allows 512 threads per block; measured).
+// Launched at 96 registers per thread (five warps per sub-partition allow no
+// more); the split above then moves registers from warpgroup 0 to the
+// epilogue, which at 96 spilled.
 template <int TC>
 __global__ void __launch_bounds__(kUThreads, 1)
     sweep_umma_kernel(EvalArgs a, int tci, int n_bands, int n_groups) {
@@ -253,7 +266,12 @@ __global__ void __launch_bounds__(kUThreads, 1)
   const int band = (tile % tiles_b) * 16 + within % 16;
   const int grp = (tile / tiles_b) * 16 + within / 16;
   if (band >= n_bands || grp >= n_groups) return;  // CTA-uniform, before any barrier or allocation
-  if (*(const volatile int*)a.status == TTO_E_TIMEOUT) return;  // an earlier CTA gave up: end at once
+  // an earlier CTA gave up: end at once, every warp alike (one thread reads
+  // the status word: the register split below needs all warps present)
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) s_skip = *(const volatile int*)a.status == TTO_E_TIMEOUT;
+  __syncthreads();
+  if (s_skip) return;
   const int n_topo = min(kUTopo, a.B - grp * kUTopo);
   const int n_chunks = a.O_pad / kUNC;
   unsigned char* smA = smem;                          // [topo][hi, lo][128 x 8]
@@ -286,65 +304,69 @@ __global__ void __launch_bounds__(kUThreads, 1)
   const uint32_t tmem = s_tmem;
 
   int issued = 0;  // producer: stages issued
-  if (warp == 0 && lane == 0) {
-    // U tiles of the group's topologies, then the ring
-    bar_expect_tx(&bar_a, n_topo * kUA);
-    for (int b = 0; b < n_topo; ++b)
-      bulk_g2s(smA + b * kUA, a.Ua + (((size_t)(grp * kUTopo + b) * n_bands + band) * (kUA / 4)), kUA, &bar_a);
-    for (int s = 0; s < n_chunks; ++s) {
-      const int slot = s % kUStages;
-      if (s >= kUStages && !bar_wait(&empty[slot], (uint32_t)((s / kUStages) - 1) & 1u, abort_flag, a.status)) {
-        give_up();
-        break;
-      }
-      unsigned char* st = smS + (size_t)slot * C::kStage;
-      bar_expect_tx(&full[slot], kUN + n_topo * C::kTopoBytes);
-      // -N fragments of the band's 8 16-row tiles x the chunk's 8 column blocks
-      for (int i = 0; i < 8; ++i)
-        bulk_g2s(st + i * (kUN / 8), a.Nf + ((size_t)(band * 8 + i) * (a.O_pad / 8) + (size_t)s * (kUNC / 8)) * 32,
-                 kUN / 8, &full[slot]);
-      for (int b = 0; b < n_topo; ++b) {
-        const size_t bt = (size_t)grp * kUTopo + b;
-        unsigned char* tb = st + kUN + b * C::kTopoBytes;
-        bulk_g2s(tb, a.Vb + (bt * n_chunks + s) * (kUV / 4), kUV, &full[slot]);
-        bulk_g2s(tb + kUV, a.gq + ((bt * a.n_tch + tci) * a.O_pad + (size_t)s * kUNC) * TC, C::kG, &full[slot]);
-      }
-      issued = s + 1;
-    }
-  } else if (warp == 1 && lane == 0) {
-    if (!bar_wait(&bar_a, 0, abort_flag, a.status)) {
-      give_up();
-    } else {
+  if (warp < 4) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kUCtlRegs) : "memory");
+    if (warp == 0 && lane == 0) {
+      // U tiles of the group's topologies, then the ring
+      bar_expect_tx(&bar_a, n_topo * kUA);
+      for (int b = 0; b < n_topo; ++b)
+        bulk_g2s(smA + b * kUA, a.Ua + (((size_t)(grp * kUTopo + b) * n_bands + band) * (kUA / 4)), kUA, &bar_a);
       for (int s = 0; s < n_chunks; ++s) {
-        const int slot = s % kUStages, buf = s & 1;
-        if (!bar_wait(&full[slot], (uint32_t)(s / kUStages) & 1u, abort_flag, a.status)) {
+        const int slot = s % kUStages;
+        if (s >= kUStages && !bar_wait(&empty[slot], (uint32_t)((s / kUStages) - 1) & 1u, abort_flag, a.status)) {
           give_up();
           break;
         }
-        const unsigned char* st = smS + (size_t)slot * C::kStage;
-        bool ok = true;
+        unsigned char* st = smS + (size_t)slot * C::kStage;
+        bar_expect_tx(&full[slot], kUN + n_topo * C::kTopoBytes);
+        // -N fragments of the band's 8 16-row tiles x the chunk's 8 column blocks
+        for (int i = 0; i < 8; ++i)
+          bulk_g2s(st + i * (kUN / 8), a.Nf + ((size_t)(band * 8 + i) * (a.O_pad / 8) + (size_t)s * (kUNC / 8)) * 32,
+                   kUN / 8, &full[slot]);
         for (int b = 0; b < n_topo; ++b) {
-          if (s >= 2 && !bar_wait(&tempty[b][buf], (uint32_t)((s >> 1) - 1) & 1u, abort_flag, a.status)) {
+          const size_t bt = (size_t)grp * kUTopo + b;
+          unsigned char* tb = st + kUN + b * C::kTopoBytes;
+          bulk_g2s(tb, a.Vb + (bt * n_chunks + s) * (kUV / 4), kUV, &full[slot]);
+          bulk_g2s(tb + kUV, a.gq + ((bt * a.n_tch + tci) * a.O_pad + (size_t)s * kUNC) * TC, C::kG, &full[slot]);
+        }
+        issued = s + 1;
+      }
+    } else if (warp == 1 && lane == 0) {
+      if (!bar_wait(&bar_a, 0, abort_flag, a.status)) {
+        give_up();
+      } else {
+        for (int s = 0; s < n_chunks; ++s) {
+          const int slot = s % kUStages, buf = s & 1;
+          if (!bar_wait(&full[slot], (uint32_t)(s / kUStages) & 1u, abort_flag, a.status)) {
             give_up();
-            ok = false;
             break;
           }
-          tc_fence_after();
-          const unsigned char* A = smA + b * kUA;
-          const unsigned char* V = st + kUN + b * C::kTopoBytes;
-          const uint64_t a_hi = smem_desc(A, 128, 256), a_lo = smem_desc(A + kUA / 2, 128, 256);
-          const uint64_t v_hi = smem_desc(V, 128, 256), v_lo = smem_desc(V + kUV / 2, 128, 256);
-          const uint32_t d = tmem + (uint32_t)(b * 2 * kUNC + buf * kUNC);
-          umma_tf32(d, a_hi, v_hi, 0u);
-          umma_tf32(d, a_lo, v_hi, 1u);
-          umma_tf32(d, a_hi, v_lo, 1u);
-          umma_commit(&tfull[b][buf]);
+          const unsigned char* st = smS + (size_t)slot * C::kStage;
+          bool ok = true;
+          for (int b = 0; b < n_topo; ++b) {
+            if (s >= 2 && !bar_wait(&tempty[b][buf], (uint32_t)((s >> 1) - 1) & 1u, abort_flag, a.status)) {
+              give_up();
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const unsigned char* A = smA + b * kUA;
+            const unsigned char* V = st + kUN + b * C::kTopoBytes;
+            const uint64_t a_hi = smem_desc(A, 128, 256), a_lo = smem_desc(A + kUA / 2, 128, 256);
+            const uint64_t v_hi = smem_desc(V, 128, 256), v_lo = smem_desc(V + kUV / 2, 128, 256);
+            const uint32_t d = tmem + (uint32_t)(b * 2 * kUNC + buf * kUNC);
+            umma_tf32(d, a_hi, v_hi, 0u);
+            umma_tf32(d, a_lo, v_hi, 1u);
+            umma_tf32(d, a_hi, v_lo, 1u);
+            umma_commit(&tfull[b][buf]);
+          }
+          if (!ok) break;
         }
-        if (!ok) break;
       }
     }
-  } else if (warp >= 2) {
-    const int e = warp - 2, b = e >> 2, q = warp & 3;  // q: this warp's tensor-memory lane quarter
+  } else {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kUEpiRegs) : "memory");
+    const int e = warp - 4, b = e >> 2, q = warp & 3;  // q: this warp's tensor-memory lane quarter
     if (b < n_topo) {
       const size_t bt = (size_t)grp * kUTopo + b;
       const int t0 = tci * TC;
@@ -527,6 +549,13 @@ int launch_umma_tc(EvalArgs& a, int tci, cudaStream_t s) {
   if (dev < 0 || dev >= 64) return set_error(TTO_E_ARG, "device %d out of range", dev);
   if (!attr_set[dev]) {
     TTO_CUDA_TRY(cudaFuncSetAttribute(sweep_umma_kernel<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmem));
+    // the register split is sized for a launch at exactly kULaunchRegs per
+    // thread; with fewer, an increase could wait for registers that never come
+    cudaFuncAttributes fa{};
+    TTO_CUDA_TRY(cudaFuncGetAttributes(&fa, sweep_umma_kernel<TC>));
+    if (fa.numRegs != kULaunchRegs)
+      return set_error(TTO_E_CUDA, "tcgen05 sweep built with %d registers per thread, its register split needs %d",
+                       fa.numRegs, kULaunchRegs);
     attr_set[dev] = true;
   }
   const int n_bands = a.E_mon_pad / 128;
