@@ -335,13 +335,22 @@ __global__ void __launch_bounds__(kUThreads, 1)
       if (!bar_wait(&bar_a, 0, abort_flag, a.status)) {
         give_up();
       } else {
+        // This thread shares its sub-partition with four busy epilogue warps,
+        // so its per-chunk work is kept to a few instructions: descriptors of
+        // the first U and V tiles are built once and the others reached by
+        // adding offsets to the start-address field (16-byte units; every
+        // offset is a multiple of 16 bytes and all of shared memory lies below
+        // 2^14 units, so the field never carries into its neighbours).
+        const uint64_t a_d0 = smem_desc(smA, 128, 256), v_d0 = smem_desc(smS + kUN, 128, 256);
+        constexpr uint32_t kDA = kUA >> 4, kDAlo = (kUA / 2) >> 4, kDV = C::kTopoBytes >> 4, kDVlo = (kUV / 2) >> 4,
+                           kDS = C::kStage >> 4;
         for (int s = 0; s < n_chunks; ++s) {
           const int slot = s % kUStages, buf = s & 1;
           if (!bar_wait(&full[slot], (uint32_t)(s / kUStages) & 1u, abort_flag, a.status)) {
             give_up();
             break;
           }
-          const unsigned char* st = smS + (size_t)slot * C::kStage;
+          const uint64_t v_ds = v_d0 + (uint64_t)(slot * kDS);
           bool ok = true;
           for (int b = 0; b < n_topo; ++b) {
             if (s >= 2 && !bar_wait(&tempty[b][buf], (uint32_t)((s >> 1) - 1) & 1u, abort_flag, a.status)) {
@@ -350,14 +359,11 @@ __global__ void __launch_bounds__(kUThreads, 1)
               break;
             }
             tc_fence_after();
-            const unsigned char* A = smA + b * kUA;
-            const unsigned char* V = st + kUN + b * C::kTopoBytes;
-            const uint64_t a_hi = smem_desc(A, 128, 256), a_lo = smem_desc(A + kUA / 2, 128, 256);
-            const uint64_t v_hi = smem_desc(V, 128, 256), v_lo = smem_desc(V + kUV / 2, 128, 256);
+            const uint64_t a_hi = a_d0 + (uint64_t)(b * kDA), v_hi = v_ds + (uint64_t)(b * kDV);
             const uint32_t d = tmem + (uint32_t)(b * 2 * kUNC + buf * kUNC);
             umma_tf32(d, a_hi, v_hi, 0u);
-            umma_tf32(d, a_lo, v_hi, 1u);
-            umma_tf32(d, a_hi, v_lo, 1u);
+            umma_tf32(d, a_hi + kDAlo, v_hi, 1u);
+            umma_tf32(d, a_hi, v_hi + kDVlo, 1u);
             umma_commit(&tfull[b][buf]);
           }
           if (!ok) break;
