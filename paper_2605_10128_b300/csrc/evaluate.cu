@@ -297,19 +297,24 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
       for (int q = s_slot[j]; q < s_slot[j + 1]; ++q) w += s_coef[q] * s_col[q][e];
       W[j] = w;
     }
-    const double be = a.b[e];
-    double npcc = a.Ncc[cr];
+    // N'_cc = N_cc - U_c . V_c = N_cc - (W^T K^-1 W) / b_c.  FP64 division is
+    // a long instruction sequence on this part, so each row divides twice
+    // (1 / b_c, 1 / N'_cc) and multiplies elsewhere.
+    const double inv_be = 1.0 / a.b[e];
+    double q = 0.0;
     for (int jj = 0; jj < k; ++jj) {
       double uu = 0.0;
       for (int j = 0; j < k; ++j) uu += W[j] * s_Ki[j][jj];
-      npcc -= uu * (W[jj] / be);
+      q += uu * W[jj];
     }
+    const double npcc = a.Ncc[cr] - q * inv_be;
     for (int jj = 0; jj < TTO_MAX_K; ++jj) {
-      v[jj] = jj < k ? (float)(W[jj] / be) : 0.f;
+      v[jj] = jj < k ? (float)(W[jj] * inv_be) : 0.f;
       vmax = fmaxf(vmax, fabsf(v[jj]));
     }
     const bool isl = !(npcc > kIslandTol);
     if (isl && c < a.O) ++islcnt;
+    const double inv_np = isl ? 0.0 : 1.0 / npcc;
     for (int t = 0; t < TT; ++t) {
       float g = 0.f;
       if (t < nt) {
@@ -318,7 +323,7 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
         } else {
           double f = a.f0[(size_t)a.tsel[t] * a.E + e];
           for (int j = 0; j < k; ++j) f += W[j] * s_psi[t][j];
-          g = (float)(f / npcc);
+          g = (float)(f * inv_np);
         }
       }
       gv[t] = g;
