@@ -26,7 +26,13 @@ Readings where the paper is silent (each also listed in the design notes):
     (fitness -inf);
   * with several timesteps, lambda_o / lambda_c / lambda_c0 sum over timesteps
     and max loading takes the maximum over timesteps;
-  * cell = min(lambda_s, D_s - 1) * D_m + min(moved, D_m - 1).
+  * cell = min(lambda_s, D_s - 1) * D_m + min(moved, D_m - 1), times D_d plus
+    min(lambda_d, D_d - 1) when the archive also spans disconnections;
+  * disconnection slots (Sec. "Repertoire design": a genome holds N_a split
+    slots and N_d disconnection slots) open their branch in every state; an
+    outage of a branch the topology already opened is no contingency and is
+    skipped without counting as islanding; a split whose busbar B keeps only
+    opened branches leaves its new node isolated, which islands the grid.
 """
 from __future__ import annotations
 
@@ -69,6 +75,32 @@ def _is_connected_cs(n_node, fr, to, keep):
     return nc == 1
 
 
+def split_part(grid, genome):
+    """The split slots of a genome: all of it for a grid without disconnection
+    slots, else its first k_max entries."""
+    return list(genome) if getattr(grid, "n_dslot", 0) == 0 else list(genome)[: grid.k_max]
+
+
+def open_branches(grid, genome):
+    """Sorted branch ids opened by the disconnection slots of ``genome``
+    (indices into the grid's disconnection set, -1 = empty)."""
+    nd = getattr(grid, "n_dslot", 0)
+    if nd == 0:
+        return []
+    out = []
+    for d in list(genome)[grid.k_max: grid.k_max + nd]:
+        d = int(d)
+        if d < 0:
+            continue
+        if d >= grid.n_disc:
+            raise TopologyError(f"unknown disconnection {d}")
+        e = int(grid.disc[d])
+        if e in out:
+            raise TopologyError(f"branch {e} opened twice")
+        out.append(e)
+    return sorted(out)
+
+
 def post_split_graph(grid, genome):
     """Apply the split actions of ``genome`` (action ids, -1 = empty slot).
 
@@ -79,7 +111,7 @@ def post_split_graph(grid, genome):
     fr = grid.from_bus.astype(np.int64).copy()
     to = grid.to_bus.astype(np.int64).copy()
     n = grid.n_bus
-    acts = [int(a) for a in genome if int(a) >= 0]
+    acts = [int(a) for a in split_part(grid, genome) if int(a) >= 0]
     seen = set()
     slots = []
     for a in acts:
@@ -113,12 +145,12 @@ def post_split_graph(grid, genome):
     return n_node, fr, to, p, slots
 
 
-def solve_flows(n_node, fr, to, b, p, slack, skip=-1):
+def solve_flows(n_node, fr, to, b, p, slack, skip=-1, keep=None):
     """DC loadflow: branch flows [T][E] for injections p [T][n_node]; branch
-    ``skip`` is out of service (flow 0).  The slack angle is fixed at 0 and the
-    slack absorbs any imbalance."""
+    ``skip`` and the branches outside ``keep`` are out of service (flow 0).  The
+    slack angle is fixed at 0 and the slack absorbs any imbalance."""
     E = len(fr)
-    keep = np.ones(E, dtype=bool)
+    keep = np.ones(E, dtype=bool) if keep is None else np.array(keep, dtype=bool)
     if skip >= 0:
         keep[skip] = False
     f, t, w = fr[keep], to[keep], b[keep]
@@ -146,11 +178,12 @@ def base_flows(grid):
                        grid.b, grid.p, grid.slack)
 
 
-def descriptors(grid, genome, d_split, d_moved):
-    """(lambda_s, moved assets, cell) of a genome."""
+def descriptors(grid, genome, d_split, d_moved, d_disc=1):
+    """(lambda_s, moved assets, cell) of a genome; with d_disc > 1 the cell
+    also spans lambda_d, the number of opened branches."""
     ns = 0
     nm = 0
-    for a in genome:
+    for a in split_part(grid, genome):
         a = int(a)
         if a < 0:
             continue
@@ -160,10 +193,12 @@ def descriptors(grid, genome, d_split, d_moved):
         ns += 1
         nm += min(on_b, m - on_b)
     cell = min(ns, d_split - 1) * d_moved + min(nm, d_moved - 1)
+    if d_disc > 1:
+        cell = cell * d_disc + min(len(open_branches(grid, genome)), d_disc - 1)
     return ns, nm, cell
 
 
-def evaluate(grid, genome, timesteps=None, outages=None, d_split=8, d_moved=8, want_flows=False):
+def evaluate(grid, genome, timesteps=None, outages=None, d_split=8, d_moved=8, want_flows=False, d_disc=1):
     """Evaluate one topology by brute force.
 
     ``outages`` optionally restricts the outage list (indices into
@@ -173,16 +208,19 @@ def evaluate(grid, genome, timesteps=None, outages=None, d_split=8, d_moved=8, w
     """
     tsel = np.arange(grid.T) if timesteps is None else np.asarray(timesteps)
     n_node, fr, to, p, _ = post_split_graph(grid, genome)
+    opened = open_branches(grid, genome)
+    live = np.ones(len(fr), dtype=bool)
+    live[opened] = False
     p = p[tsel]
-    ns, nm, cell = descriptors(grid, genome, d_split, d_moved)
+    ns, nm, cell = descriptors(grid, genome, d_split, d_moved, d_disc)
     mon = grid.monitored.astype(np.int64)
     lim = grid.limit[mon]
-    res = dict(ns=ns, nm=nm, cell=cell)
-    if not is_connected_uf(n_node, fr, to):
+    res = dict(ns=ns, nm=nm, nd=len(opened), cell=cell)
+    if not (is_connected_uf(n_node, fr, to) if not opened else _is_connected_cs(n_node, fr, to, live)):
         res.update(island_base=True, island_any=False, n_islanded=0, fitness=-np.inf,
                    lambda_f1=-np.inf)
         return res
-    f_n0 = solve_flows(n_node, fr, to, grid.b, p, grid.slack)
+    f_n0 = solve_flows(n_node, fr, to, grid.b, p, grid.slack, keep=live)
     fprime = f_n0[:, mon]
     out_idx = np.arange(grid.outages.size) if outages is None else np.asarray(outages)
     fmax = np.zeros_like(fprime)
@@ -190,12 +228,14 @@ def evaluate(grid, genome, timesteps=None, outages=None, d_split=8, d_moved=8, w
     per_outage = {} if want_flows else None
     for oi in out_idx:
         c = int(grid.outages[oi])
-        keep = np.ones(len(fr), dtype=bool)
+        if not live[c]:
+            continue  # already open: no contingency
+        keep = live.copy()
         keep[c] = False
         if not _is_connected_cs(n_node, fr, to, keep):
             n_isl += 1
             continue
-        F = solve_flows(n_node, fr, to, grid.b, p, grid.slack, skip=c)[:, mon]
+        F = solve_flows(n_node, fr, to, grid.b, p, grid.slack, keep=keep)[:, mon]
         if want_flows:
             per_outage[int(oi)] = F
         fmax = np.maximum(fmax, np.abs(F))

@@ -33,7 +33,10 @@ class SynthGrid:
     stations as CSR (``asset_offset`` [S+1], ``asset_branch`` with -1 for the
     injection), actions grouped by station (``action_offset`` [S+1],
     ``action_station`` [A], ``action_mask`` uint32 [A], bit i set = asset i on
-    busbar B; asset 0 always stays on busbar A).
+    busbar B; asset 0 always stays on busbar A).  ``disc`` int32 is the
+    disconnection set (branch ids that a genome may open) and ``n_dslot`` the
+    number of disconnection slots that follow the ``k_max`` split slots in a
+    genome (Sec. "Repertoire design": N_a split slots, N_d disconnection slots).
     """
 
     name: str
@@ -55,6 +58,8 @@ class SynthGrid:
     k_max: int
     xy: np.ndarray = field(repr=False, default=None)
     seed: int = 0
+    disc: np.ndarray = field(default_factory=lambda: np.zeros(0, dtype=np.int32))
+    n_dslot: int = 0
 
     @property
     def n_branch(self) -> int:
@@ -71,6 +76,14 @@ class SynthGrid:
     @property
     def n_action(self) -> int:
         return int(self.action_station.shape[0])
+
+    @property
+    def n_disc(self) -> int:
+        return int(self.disc.shape[0])
+
+    @property
+    def genome_width(self) -> int:
+        return self.k_max + self.n_dslot
 
     def with_limits(self, limit: np.ndarray) -> "SynthGrid":
         return replace(self, limit=np.ascontiguousarray(limit, dtype=np.float64))
@@ -199,8 +212,10 @@ def _non_bridge_mask(n, edges, is_tree):
 def make_grid(n_bus: int, n_branch: int, n_station: int, assets=(4, 6), T: int = 1,
               b_dist=("uniform", 5.0, 50.0), noise: float = 0.0, seed: int = 0,
               n_outage: int | None = None, k_max: int = 2, name: str = "grid",
-              knn: int = 6) -> SynthGrid:
-    """Build a synthetic grid (limits left unset; see :func:`limits_from_flows`)."""
+              knn: int = 6, n_disc: int = 0, n_dslot: int = 0) -> SynthGrid:
+    """Build a synthetic grid (limits left unset; see :func:`limits_from_flows`).
+    ``n_disc`` non-bridge branches form the disconnection set (drawn from a
+    separate stream, so the rest of the grid does not depend on it)."""
     rng = np.random.default_rng(seed)
     xy = rng.random((n_bus, 2))
     edges, is_tree = _spanning_tree_plus_extras(xy, n_branch, rng, knn=knn)
@@ -263,13 +278,23 @@ def make_grid(n_bus: int, n_branch: int, n_station: int, assets=(4, 6), T: int =
             act_mask.append(mask)
         act_off.append(len(act_st))
 
+    nb_mask = None
     if n_outage is None:
         outages = np.arange(E, dtype=np.int32)
     else:
-        nb = np.flatnonzero(_non_bridge_mask(n_bus, edges, is_tree))
+        nb_mask = _non_bridge_mask(n_bus, edges, is_tree)
+        nb = np.flatnonzero(nb_mask)
         if nb.size < n_outage:
             raise ValueError("not enough non-bridge branches for the outage set")
         outages = np.sort(rng.choice(nb, n_outage, replace=False)).astype(np.int32)
+    disc = np.zeros(0, dtype=np.int32)
+    if n_disc > 0:
+        if nb_mask is None:
+            nb_mask = _non_bridge_mask(n_bus, edges, is_tree)
+        nb = np.flatnonzero(nb_mask)
+        if nb.size < n_disc:
+            raise ValueError("not enough non-bridge branches for the disconnection set")
+        disc = np.sort(np.random.default_rng(seed + 31337).choice(nb, n_disc, replace=False)).astype(np.int32)
     return SynthGrid(
         name=name, n_bus=n_bus, from_bus=fr, to_bus=to, b=b.astype(np.float64), slack=slack,
         p=np.ascontiguousarray(p, dtype=np.float64), limit=None,
@@ -278,7 +303,8 @@ def make_grid(n_bus: int, n_branch: int, n_station: int, assets=(4, 6), T: int =
         asset_branch=np.array(a_br, dtype=np.int32),
         action_offset=np.array(act_off, dtype=np.int32),
         action_station=np.array(act_st, dtype=np.int32),
-        action_mask=np.array(act_mask, dtype=np.uint32), k_max=k_max, xy=xy, seed=seed)
+        action_mask=np.array(act_mask, dtype=np.uint32), k_max=k_max, xy=xy, seed=seed,
+        disc=disc, n_dslot=int(n_dslot))
 
 
 def limits_from_flows(f0_t0: np.ndarray, n_tight: int, seed: int = 0) -> np.ndarray:
@@ -299,7 +325,9 @@ def random_topologies(grid: SynthGrid, B: int, k_max: int | None = None, seed: i
                       min_splits: int = 1) -> np.ndarray:
     """B genomes of ``k_max`` action slots (-1 = empty): the number of splits is
     uniform in [min_splits, k_max], stations are distinct, and each station's
-    action is uniform over its action list."""
+    action is uniform over its action list.  A grid with disconnection slots
+    appends ``n_dslot`` of them: the number of disconnections is uniform in
+    [0, n_dslot], the branches distinct and uniform over the disconnection set."""
     k_max = grid.k_max if k_max is None else k_max
     rng = np.random.default_rng(seed + 104729)
     S = grid.n_station
@@ -318,6 +346,18 @@ def random_topologies(grid: SynthGrid, B: int, k_max: int | None = None, seed: i
         for j in range(kk):
             sel = ns[s0:s1] > j
             out[s0:s1, j] = np.where(sel, act[:, j], -1)
+    if grid.n_dslot > 0 and grid.n_disc > 0:
+        drng = np.random.default_rng(seed + 7777)
+        nd_max = min(grid.n_dslot, grid.n_disc)
+        nd = drng.integers(0, nd_max + 1, size=B)
+        dpart = np.full((B, grid.n_dslot), -1, dtype=np.int32)
+        keys = drng.random((B, grid.n_disc))
+        pick = np.argsort(keys, axis=1)[:, :nd_max]
+        for j in range(nd_max):
+            dpart[:, j] = np.where(nd > j, pick[:, j], -1)
+        out = np.concatenate([out, dpart], axis=1)
+    elif grid.n_dslot > 0:
+        out = np.concatenate([out, np.full((B, grid.n_dslot), -1, dtype=np.int32)], axis=1)
     return out
 
 
@@ -356,4 +396,4 @@ def config_grid(name: str, seed: int = 0, **overrides) -> SynthGrid:
     c.update(overrides)
     return make_grid(c["n_bus"], c["n_branch"], c["n_station"], assets=c["assets"], T=c["T"],
                      b_dist=c["b_dist"], noise=c["noise"], seed=seed, n_outage=c["n_outage"],
-                     k_max=c["k_max"], name=name)
+                     k_max=c["k_max"], name=name, n_disc=c.get("n_disc", 0), n_dslot=c.get("n_dslot", 0))

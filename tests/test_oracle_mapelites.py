@@ -142,3 +142,103 @@ def test_insert_matches_definition():
                 assert arch.elites[c][0] == best and arch.elites[c][1][0] == first + 100
             else:
                 assert arch.elites[c] is inc
+
+
+# ------------------------------------------- disconnection mutation, crossover
+def _grid_with_disc(seed=3, n_dslot=2, stride=2):
+    from dataclasses import replace
+    g = small_grid(seed)
+    return replace(g, disc=np.arange(0, g.n_branch, stride, dtype=np.int32), n_dslot=n_dslot)
+
+
+def test_disconnection_mutation_invariants_and_forced_add():
+    g = _grid_with_disc()
+    tab = me.ActionTable(g)
+    nd = g.n_dslot
+    empty = np.full(g.k_max + nd, -1, dtype=np.int32)
+    for cand in range(400):
+        ws = me.WordStream(5, 1, cand)
+        ws.next()
+        child = me.mutate(empty, tab, ws, n_dslot=nd, n_disc=g.n_disc)
+        d = [x for x in child[g.k_max:] if x >= 0]
+        st = [int(tab.station[a]) for a in child[: g.k_max] if a >= 0]
+        assert len(set(d)) == len(d) and all(0 <= x < g.n_disc for x in d)
+        assert len(set(st)) == len(st)
+        assert d or st  # never the unchanged default topology
+    # from a genome with all disconnection slots empty and no split, the
+    # disconnection step always adds one (the forced rule)
+    g1 = _grid_with_disc(n_dslot=1)
+    tab1 = me.ActionTable(g1)
+    for cand in range(200):
+        ws = me.WordStream(9, 2, cand)
+        d = [-1]
+        me.mutate_disc([-1] * g1.k_max, d, g1.n_disc, ws)
+        assert d[0] >= 0
+
+
+def test_disconnection_operation_frequencies():
+    """With every operation feasible, Add / Remove / Change follow 0.25 / 0.25
+    / 0.5 and Identity (weight 0) never happens."""
+    g = _grid_with_disc(n_dslot=3)
+    counts = np.zeros(4)
+    base = [0, -1, 5]
+    for cand in range(6000):
+        ws = me.WordStream(77, 3, cand)
+        d = list(base)
+        me.mutate_disc([1], d, g.n_disc, ws)
+        if d == base:
+            counts[me.IDENTITY] += 1
+        elif sum(x >= 0 for x in d) == 3:
+            counts[me.ADD] += 1
+        elif sum(x >= 0 for x in d) == 1:
+            counts[me.REMOVE] += 1
+        else:
+            counts[me.CHANGE] += 1
+    assert counts[me.IDENTITY] == 0
+    exp = 6000 * np.array([0.25, 0.25, 0.5])
+    chi2 = (((counts[:3] - exp) ** 2) / exp).sum()
+    assert chi2 < stats.chi2.ppf(0.999, 2)
+
+
+def test_crossover_definition():
+    """p_c1 = 1 reproduces parent 1; children draw only from the parents'
+    union with distinct stations and branches; with disjoint parents and
+    p_c1 = 0.5 the first slot comes from parent 1 half of the time."""
+    g = _grid_with_disc(n_dslot=2)
+    tab = me.ActionTable(g)
+    topo = random_topologies(g, 64, seed=4)
+    from1 = 0
+    trials = 0
+    for i in range(0, 64, 2):
+        p1, p2 = topo[i], topo[i + 1]
+        for cand in range(40):
+            ws = me.WordStream(3, i, cand)
+            c = me.crossover(p1, p2, tab, ws, n_dslot=2, p_c1=1.0)
+            assert set(x for x in c[: g.k_max] if x >= 0) == set(x for x in p1[: g.k_max] if x >= 0)
+            assert set(x for x in c[g.k_max:] if x >= 0) == set(x for x in p1[g.k_max:] if x >= 0)
+            ws = me.WordStream(4, i, cand)
+            c = me.crossover(p1, p2, tab, ws, n_dslot=2, p_c1=0.5)
+            acts = [int(x) for x in c[: g.k_max] if x >= 0]
+            dis = [int(x) for x in c[g.k_max:] if x >= 0]
+            assert set(acts) <= set(int(x) for x in np.concatenate([p1[: g.k_max], p2[: g.k_max]]) if x >= 0)
+            assert set(dis) <= set(int(x) for x in np.concatenate([p1[g.k_max:], p2[g.k_max:]]) if x >= 0)
+            assert len({int(tab.station[a]) for a in acts}) == len(acts)
+            assert len(set(dis)) == len(dis)
+            s1 = {int(tab.station[a]) for a in p1[: g.k_max] if a >= 0}
+            s2 = {int(tab.station[a]) for a in p2[: g.k_max] if a >= 0}
+            if s1 and s2 and not (s1 & s2) and acts:
+                trials += 1
+                from1 += int(tab.station[acts[0]]) in s1
+    assert trials > 200
+    assert abs(from1 / trials - 0.5) < 4 * math.sqrt(0.25 / trials)
+
+
+def test_mutation_crossover_split_is_uniform():
+    B = 10
+    counts = np.zeros(B + 1)
+    for it in range(5500):
+        counts[me.mutation_count(11, it, B, True)] += 1
+    assert me.mutation_count(11, 0, B, False) == B
+    exp = 5500 / (B + 1)
+    chi2 = (((counts - exp) ** 2) / exp).sum()
+    assert chi2 < stats.chi2.ppf(0.999, B)

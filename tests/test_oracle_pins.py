@@ -43,11 +43,12 @@ def test_three_bus_splits(case):
     np.testing.assert_array_equal(r["fmax"], 0.0)
 
 
-def _kcl_kvl(n_node, fr, to, b, p, slack, flows, skip=-1):
+def _kcl_kvl(n_node, fr, to, b, p, slack, flows, skip=-1, opened=()):
     E = len(fr)
+    out = set(opened) | {skip}
     net = np.zeros((p.shape[0], n_node))
     for l in range(E):
-        if l == skip:
+        if l in out:
             continue
         net[:, fr[l]] += flows[:, l]
         net[:, to[l]] -= flows[:, l]
@@ -57,7 +58,7 @@ def _kcl_kvl(n_node, fr, to, b, p, slack, flows, skip=-1):
     G = nx.Graph()
     G.add_nodes_from(range(n_node))
     for l in range(E):
-        if l != skip:
+        if l not in out:
             G.add_edge(int(fr[l]), int(to[l]), l=l)
     for cyc in nx.cycle_basis(G):
         s = np.zeros(p.shape[0])
@@ -233,3 +234,81 @@ def test_duplicate_station_rejected():
     a0 = int(g.action_offset[0])
     with pytest.raises(dcflow.TopologyError):
         dcflow.evaluate(g.with_limits(np.ones(g.n_branch)), [a0, a0 + 1, -1])
+
+
+# ----------------------------------------------------------- disconnection slots
+def _with_disc(g, disc, n_dslot):
+    from dataclasses import replace
+    return replace(g, disc=np.array(disc, dtype=np.int32), n_dslot=n_dslot)
+
+
+def test_disconnection_three_bus_pins():
+    """Opening branch 1->2 of the triangle (closed form in the golden fixture):
+    the N-0 flows equal that branch's outage, the open branch is no
+    contingency, and opening both branches at the slack islands the grid."""
+    g, d = three_bus()
+    c = d["cases"]["disconnect_1_2"]
+    gd = _with_disc(g, [0, 1, 2], 2)
+    r = dcflow.evaluate(gd, [-1, 1, -1])
+    np.testing.assert_allclose(r["fprime"][0], c["fprime"], atol=1e-12)
+    assert r["n_islanded"] == c["n_islanded"] and not r["island_base"]
+    for k in ["lambda_o", "maxload", "fitness", "lambda_f1"]:
+        assert r[k] == pytest.approx(c[k], abs=1e-12), k
+    assert (r["lambda_c"], r["lambda_c0"], r["nd"]) == (c["lambda_c"], c["lambda_c0"], 1)
+    r2 = dcflow.evaluate(gd, [-1, 0, 2])
+    assert r2["island_base"] and r2["fitness"] == -np.inf
+    with pytest.raises(dcflow.TopologyError):
+        dcflow.evaluate(gd, [-1, 1, 1])  # one branch opened twice
+    with pytest.raises(dcflow.TopologyError):
+        dcflow.evaluate(gd, [-1, 3, -1])  # not in the disconnection set
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_disconnection_kirchhoff_and_islanding(seed):
+    """With opened branches: KCL and KVL in the N-0 state and every outage
+    state, zero flow on opened branches, and islanding equal to networkx's
+    connectivity and bridges of the graph without the opened branches."""
+    g = small_grid(seed)
+    g = _with_disc(g, np.arange(0, g.n_branch, 3), 2).with_limits(np.ones(g.n_branch))
+    topo = random_topologies(g, 8, seed=seed)
+    assert topo.shape[1] == g.k_max + 2
+    seen_open = 0
+    for gen in topo:
+        opened = dcflow.open_branches(g, gen)
+        seen_open += len(opened)
+        n_node, fr, to, p, _ = dcflow.post_split_graph(g, gen)
+        G = nx.MultiGraph()
+        G.add_nodes_from(range(n_node))
+        for l in range(len(fr)):
+            if l not in opened:
+                G.add_edge(int(fr[l]), int(to[l]), key=l)
+        r = dcflow.evaluate(g, gen)
+        assert r["island_base"] == (not nx.is_connected(G))
+        if r["island_base"]:
+            continue
+        live = np.ones(len(fr), dtype=bool)
+        live[opened] = False
+        f = dcflow.solve_flows(n_node, fr, to, g.b, p, g.slack, keep=live)
+        assert np.all(f[:, opened] == 0.0)
+        _kcl_kvl(n_node, fr, to, g.b, p, g.slack, f, skip=-1, opened=opened)
+        for c in range(len(fr)):
+            if c in opened:
+                continue
+            keep = live.copy()
+            keep[c] = False
+            H = G.copy()
+            H.remove_edges_from([(u, v, k) for u, v, k in G.edges(keys=True) if k == c])
+            if not nx.is_connected(H):
+                continue
+            F = dcflow.solve_flows(n_node, fr, to, g.b, p, g.slack, keep=keep)
+            assert np.all(F[:, c] == 0.0) and np.all(F[:, opened] == 0.0)
+            _kcl_kvl(n_node, fr, to, g.b, p, g.slack, F, skip=c, opened=opened)
+        bridges = set()
+        for u, v, k in G.edges(keys=True):
+            H = G.copy()
+            H.remove_edge(u, v, key=k)
+            if not nx.is_connected(H):
+                bridges.add(k)
+        n_br = sum(1 for c in g.outages if int(c) in bridges)
+        assert r["n_islanded"] == n_br
+    assert seen_open > 0
