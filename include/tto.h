@@ -62,7 +62,12 @@ typedef struct tto_archive tto_archive;
  * assets asset_branch[asset_offset[s] .. asset_offset[s+1]) -- a branch id
  * incident to that bus, or -1 for the bus injection.  Actions: action a splits
  * station action_station[a]; bit i of action_mask[a] puts asset i on busbar B
- * (bit 0 must be clear; busbar B must hold at least one branch). */
+ * (bit 0 must be clear; busbar B must hold at least one branch).
+ * Disconnections (Sec. "Repertoire design": N_d disconnection slots beside the
+ * N_a = k_max split slots): disc_branch[0 .. n_disc) lists the branches a
+ * genome may open (distinct ids); n_dslot >= 0 slots, k_max + n_dslot <=
+ * TTO_MAX_K, follow the split slots in every genome.  Zero-initialise the
+ * struct so that grids without disconnections leave these fields 0. */
 typedef struct {
   int32_t n_bus;
   int32_t n_branch;
@@ -84,8 +89,11 @@ typedef struct {
   int32_t n_action;
   const int32_t* action_station;
   const uint32_t* action_mask;
-  int32_t k_max;   /* genome slots, 0 < k_max <= TTO_MAX_K */
+  int32_t k_max;   /* split slots, 0 < k_max <= TTO_MAX_K */
   int32_t device;  /* CUDA device ordinal */
+  int32_t n_disc;                /* size of the disconnection set (0: none) */
+  const int32_t* disc_branch;    /* [n_disc] branch ids, or NULL when n_disc == 0 */
+  int32_t n_dslot;               /* disconnection slots per genome */
 } tto_grid_desc;
 
 /* Options of one evaluation call. */
@@ -94,12 +102,22 @@ typedef struct {
   int32_t fitness_kind;  /* TTO_FIT_* */
   int32_t d_split;       /* archive extent over split stations (cell rows) */
   int32_t d_moved;       /* archive extent over moved assets (cell columns) */
+  int32_t d_disc;        /* archive extent over opened branches lambda_d; 0 or 1: not a dimension */
 } tto_eval_opts;
 
-/* Mutation parameters of Algorithm 1 (split part). */
+/* Mutation and crossover parameters (Algorithms 1-3).  The split part draws
+ * N_mut ~ clip(Poisson(n_mut_mean), 1, k_max) operation rounds with
+ * probabilities p_*; genomes with disconnection slots then take one
+ * disconnection operation with probabilities dp_* (the paper's 0.25 / 0.25 /
+ * 0.5 / 0).  crossover = 1 splits each batch as Algorithm 3 does: b_mc ~
+ * Uniform{0..B} children by mutation, the others by Algorithm 2 on two parents
+ * with bias p_c1 toward the first (crossover = 0: all by mutation). */
 typedef struct {
   double p_add, p_remove, p_change, p_identity;
   double n_mut_mean;     /* Poisson mean of the number of mutation rounds */
+  double dp_add, dp_remove, dp_change, dp_identity;
+  int32_t crossover;
+  double p_c1;
 } tto_mut_params;
 
 /* tto_grid_create -- copy the grid, check it, and run the one-time FP64
@@ -120,6 +138,10 @@ int tto_grid_destroy(tto_grid* g);
 int tto_grid_info(const tto_grid* g, int32_t* n_branch, int32_t* n_monitored, int32_t* n_outage,
                   int32_t* n_time, int32_t* k_max, int32_t* n_action);
 
+/* Size of the disconnection set and the number of disconnection slots per
+ * genome (either pointer may be NULL); genomes are k_max + n_dslot wide. */
+int tto_grid_disc_info(const tto_grid* g, int32_t* n_disc, int32_t* n_dslot);
+
 /* Copy the FP64 base flows f0 [n_time][n_branch] of the unsplit grid into the
  * host buffer f0_host (the PTDF flows computed by tto_grid_create). */
 int tto_grid_base_flows(const tto_grid* g, double* f0_host);
@@ -133,11 +155,13 @@ int tto_grid_set_limits(tto_grid* g, const double* limit_host);
 int tto_grid_reserve(tto_grid* g, int32_t max_batch, int32_t n_t);
 
 /* tto_evaluate_batch -- exact DC N-1 evaluation of B topologies.
- *   topo      device int32 [B][k_max]: action ids, -1 = empty slot;
+ *   topo      device int32 [B][k_max + n_dslot]: action ids, then indices into
+ *             the disconnection set; -1 = empty slot;
  *   timesteps host int32 [n_t] indices into the grid's timesteps (NULL = all);
  *   fitness   device float [B]   (-inf when the split itself islands the grid);
  *   desc      device int32 [B][2] (split stations, moved assets);
- *   cell      device int32 [B]   archive cell of the descriptors;
+ *   cell      device int32 [B]   archive cell of the descriptors: split stations,
+ *             moved assets and, when opts->d_disc > 1, opened branches (fastest);
  *   island    device uint8 [B]   bit0: split islands the grid, bit1: some outage islands;
  *   metrics   device float [B][4] (lambda_o, max loading, lambda_c, lambda_c0) or NULL;
  *   fmax      device float [B][n_t][n_monitored] N-1 maximum |flow| or NULL.
@@ -146,8 +170,13 @@ int tto_grid_reserve(tto_grid* g, int32_t max_batch, int32_t n_t);
  * sweep over all (monitored branch, outage) pairs that never stores the
  * post-contingency flows, reduced to the metrics of Sec. "Fitness function
  * heuristics" (an outage that islands the split grid is skipped and counted).
- * Asynchronous on stream.  A genome with an unknown action id or a repeated
- * station is reported by the device; read it with tto_grid_sync_status. */
+ * An opened branch is one more rank-1 term of the same update (a phase shift
+ * across it with its post-topology flow held at zero); an outage of an opened
+ * branch is no contingency and is skipped without counting; a split whose
+ * busbar B keeps only opened branches islands the grid.
+ * Asynchronous on stream.  A genome with an unknown action or disconnection
+ * id, a repeated station or a repeated disconnection is reported by the
+ * device; read it with tto_grid_sync_status. */
 int tto_evaluate_batch(tto_grid* g, const int32_t* topo, int32_t B, const int32_t* timesteps,
                        int32_t n_t, const tto_eval_opts* opts, float* fitness, int32_t* desc,
                        int32_t* cell, uint8_t* island, float* metrics, float* fmax, void* stream);
@@ -244,10 +273,14 @@ int tto_grid_sync_status(tto_grid* g, void* stream);
 /* Archive of d_split x d_moved cells, one elite per cell, device resident.
  * Starts empty. */
 int tto_archive_create(tto_grid* g, int32_t d_split, int32_t d_moved, tto_archive** out);
+/* The same with a third descriptor, the number of opened branches lambda_d,
+ * over d_disc >= 1 values (d_split x d_moved x d_disc cells, lambda_d fastest,
+ * as the paper's cell map beta puts it first). */
+int tto_archive_create_ex(tto_grid* g, int32_t d_split, int32_t d_moved, int32_t d_disc, tto_archive** out);
 int tto_archive_destroy(tto_archive* a);
 
 /* Copy the archive to host buffers: fitness [cells] (-inf = empty cell),
- * genome [cells][k_max], filled [cells] (0/1).  Synchronous. */
+ * genome [cells][k_max + n_dslot], filled [cells] (0/1).  Synchronous. */
 int tto_archive_export(const tto_archive* a, float* fitness, int32_t* genome, uint8_t* filled);
 /* Overwrite the archive from host buffers of the same layout. */
 int tto_archive_import(tto_archive* a, const float* fitness, const int32_t* genome,
@@ -261,16 +294,19 @@ int tto_archive_import(tto_archive* a, const float* fitness, const int32_t* geno
 int tto_archive_insert(tto_archive* a, const int32_t* topo, int32_t B, const float* fitness,
                        const int32_t* cell, void* stream);
 
-/* Propose B mutated genomes (device int32 [B][k_max]) from parents drawn
- * uniformly over the filled cells, with Algorithm 1's split mutation driven by
- * Philox4x32-10 keyed by seed and countered by (word block, candidate,
- * iteration).  Deterministic given (archive, seed, iteration).  Errors:
- * TTO_E_ARG if the archive is empty. */
+/* Propose B genomes (device int32 [B][k_max + n_dslot]) from parents drawn
+ * uniformly over the filled cells (an empty archive offers the unsplit
+ * topology): Algorithm 1's mutation, and with mp->crossover Algorithm 2's
+ * crossover for the children past b_mc, driven by Philox4x32-10 keyed by seed
+ * and countered by (word block, candidate, iteration); b_mc comes from
+ * candidate 0xFFFFFFFF's first word.  Deterministic given (archive, seed,
+ * iteration). */
 int tto_mapelites_propose(tto_archive* a, uint64_t seed, uint64_t iteration, int32_t B,
                           const tto_mut_params* mp, int32_t* topo_out, void* stream);
 
 /* One full MapElites iteration on the device: propose B candidates, evaluate
- * them exactly (tto_evaluate_batch with opts), insert them.  The candidates
+ * them exactly (tto_evaluate_batch with opts, whose cell extents must equal
+ * the archive's), insert them.  The candidates
  * and their fitness stay in library workspace; topo_out / fitness_out
  * (device, optional) receive copies.  Asynchronous. */
 int tto_mapelites_step(tto_archive* a, uint64_t seed, uint64_t iteration, int32_t B,

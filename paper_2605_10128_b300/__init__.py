@@ -46,6 +46,8 @@ class Grid:
         self.n_time = info["n_time"]
         self.k_max = info["k_max"]
         self.n_action = info["n_action"]
+        self.n_disc, self.n_dslot = _lib.tto_grid_disc_info(self._h)
+        self.genome_width = self.k_max + self.n_dslot
 
     @property
     def handle(self):
@@ -72,14 +74,15 @@ class Grid:
         _lib.tto_grid_reserve(self._h, max_batch, self.n_time if n_t is None else n_t)
 
     def evaluate(self, topo, timesteps=None, precision=PREC_FP32, fitness_kind=FIT_WORKLOAD,
-                 d_split=8, d_moved=8, metrics=False, fmax=False, stream=None, out=None):
-        """Exact N-1 evaluation of ``topo`` (CUDA int32 tensor [B][k_max]).
-        Returns a dict of CUDA tensors: fitness, desc, cell, island and, when
-        asked, metrics [B][4] and fmax [B][n_t][n_monitored]."""
+                 d_split=8, d_moved=8, metrics=False, fmax=False, stream=None, out=None, d_disc=1):
+        """Exact N-1 evaluation of ``topo`` (CUDA int32 tensor [B][k_max +
+        n_dslot]: split actions, then disconnections).  Returns a dict of CUDA
+        tensors: fitness, desc, cell, island and, when asked, metrics [B][4]
+        and fmax [B][n_t][n_monitored]."""
         torch = _torch()
         B = int(topo.shape[0])
-        if topo.dtype != torch.int32 or not topo.is_cuda or topo.shape[1] != self.k_max:
-            raise TTOError(_lib.TTO_E_ARG, "topo must be a CUDA int32 tensor [B][k_max]")
+        if topo.dtype != torch.int32 or not topo.is_cuda or topo.shape[1] != self.genome_width:
+            raise TTOError(_lib.TTO_E_ARG, "topo must be a CUDA int32 tensor [B][k_max + n_dslot]")
         topo = topo.contiguous()
         n_t = self.n_time if timesteps is None else len(timesteps)
         dev = topo.device
@@ -92,7 +95,7 @@ class Grid:
                 out["metrics"] = torch.empty(B, 4, dtype=torch.float32, device=dev)
             if fmax:
                 out["fmax"] = torch.empty(B, n_t, self.n_monitored, dtype=torch.float32, device=dev)
-        o = _lib.EvalOpts(precision, fitness_kind, d_split, d_moved)
+        o = _lib.EvalOpts(precision, fitness_kind, d_split, d_moved, d_disc)
         _lib.tto_evaluate_batch(self._h, topo, B, timesteps, o, out["fitness"], out.get("desc"),
                                 out.get("cell"), out.get("island"), out.get("metrics"),
                                 out.get("fmax"), _stream(stream))
@@ -127,12 +130,13 @@ class Grid:
 class Archive:
     """Device-resident MapElites archive (one elite per cell)."""
 
-    def __init__(self, grid: Grid, d_split: int, d_moved: int):
+    def __init__(self, grid: Grid, d_split: int, d_moved: int, d_disc: int = 1):
         self.grid = grid
         self.d_split = d_split
         self.d_moved = d_moved
-        self.cells = d_split * d_moved
-        self._h = _lib.tto_archive_create(grid.handle, d_split, d_moved)
+        self.d_disc = d_disc
+        self.cells = d_split * d_moved * d_disc
+        self._h = _lib.tto_archive_create(grid.handle, d_split, d_moved, d_disc)
 
     def close(self):
         if self._h is not None:
@@ -146,7 +150,7 @@ class Archive:
             pass
 
     def export(self):
-        return _lib.tto_archive_export(self._h, self.cells, self.grid.k_max)
+        return _lib.tto_archive_export(self._h, self.cells, self.grid.genome_width)
 
     def load(self, fitness, genome, filled):
         _lib.tto_archive_import(self._h, fitness, genome, filled)
@@ -156,13 +160,13 @@ class Archive:
 
     def propose(self, seed, iteration, B, mutation=DEFAULT_MUTATION, stream=None):
         torch = _torch()
-        out = torch.empty(B, self.grid.k_max, dtype=torch.int32, device=f"cuda:{self.grid.device}")
+        out = torch.empty(B, self.grid.genome_width, dtype=torch.int32, device=f"cuda:{self.grid.device}")
         _lib.tto_mapelites_propose(self._h, seed, iteration, B, mutation, out, _stream(stream))
         return out
 
     def step(self, seed, iteration, B, mutation=DEFAULT_MUTATION, precision=PREC_FP32,
              fitness_kind=FIT_WORKLOAD, topo_out=None, fitness_out=None, stream=None):
-        o = _lib.EvalOpts(precision, fitness_kind, self.d_split, self.d_moved)
+        o = _lib.EvalOpts(precision, fitness_kind, self.d_split, self.d_moved, self.d_disc)
         _lib.tto_mapelites_step(self._h, seed, iteration, B, mutation, o, topo_out, fitness_out,
                                 _stream(stream))
 
@@ -171,7 +175,7 @@ class Archive:
                       train_steps=1, topo_out=None, fitness_out=None, score_out=None, stream=None):
         """One surrogate-screened iteration: propose n_propose, evaluate the
         n_exact ranked first exactly, insert, learn from them."""
-        o = _lib.EvalOpts(precision, fitness_kind, self.d_split, self.d_moved)
+        o = _lib.EvalOpts(precision, fitness_kind, self.d_split, self.d_moved, self.d_disc)
         _lib.tto_mapelites_step_screened(self._h, surrogate.handle, seed, iteration, n_propose,
                                          n_exact, rank_by, mutation, o, train_steps, topo_out,
                                          fitness_out, score_out, _stream(stream))
@@ -267,7 +271,7 @@ def evaluate_multi(jobs, precision=PREC_FP32, fitness_kind=FIT_WORKLOAD, d_split
                  metrics=torch.empty(B, 4, dtype=torch.float32, device=dev))
         outs.append(o)
         recs.append(dict(grid=g.handle, topo=topo, B=B, timesteps=ts, **o))
-    _lib.tto_evaluate_multi(recs, _lib.EvalOpts(precision, fitness_kind, d_split, d_moved), mode,
+    _lib.tto_evaluate_multi(recs, _lib.EvalOpts(precision, fitness_kind, d_split, d_moved, 1), mode,
                             _stream(stream))
     return outs
 

@@ -42,12 +42,13 @@ class GridDesc(C.Structure):
                 ("n_outage", C.c_int32), ("outage", _i32p), ("n_station", C.c_int32),
                 ("station_bus", _i32p), ("asset_offset", _i32p), ("asset_branch", _i32p),
                 ("n_action", C.c_int32), ("action_station", _i32p), ("action_mask", _u32p),
-                ("k_max", C.c_int32), ("device", C.c_int32)]
+                ("k_max", C.c_int32), ("device", C.c_int32), ("n_disc", C.c_int32),
+                ("disc_branch", _i32p), ("n_dslot", C.c_int32)]
 
 
 class EvalOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("fitness_kind", C.c_int32), ("d_split", C.c_int32),
-                ("d_moved", C.c_int32)]
+                ("d_moved", C.c_int32), ("d_disc", C.c_int32)]
 
 
 class EvalJob(C.Structure):
@@ -61,7 +62,15 @@ SCREEN_SCORE, SCREEN_CELL_GAIN = 0, 1
 
 class MutParams(C.Structure):
     _fields_ = [("p_add", C.c_double), ("p_remove", C.c_double), ("p_change", C.c_double),
-                ("p_identity", C.c_double), ("n_mut_mean", C.c_double)]
+                ("p_identity", C.c_double), ("n_mut_mean", C.c_double), ("dp_add", C.c_double),
+                ("dp_remove", C.c_double), ("dp_change", C.c_double), ("dp_identity", C.c_double),
+                ("crossover", C.c_int32), ("p_c1", C.c_double)]
+
+
+# Algorithm 1's disconnection-operation probabilities (add, remove, change,
+# identity) and Algorithm 2's default bias when a caller gives none.
+DEFAULT_DISC_PROBS = (0.25, 0.25, 0.5, 0.0)
+DEFAULT_P_C1 = 0.5
 
 
 class SurrogateCfg(C.Structure):
@@ -91,6 +100,8 @@ _SIGS = {
     "tto_grid_profile": ([_vp, C.c_int32], C.c_int),
     "tto_grid_profile_read": ([_vp, C.POINTER(C.c_float), _i32p], C.c_int),
     "tto_archive_create": ([_vp, C.c_int32, C.c_int32, C.POINTER(_vp)], C.c_int),
+    "tto_archive_create_ex": ([_vp, C.c_int32, C.c_int32, C.c_int32, C.POINTER(_vp)], C.c_int),
+    "tto_grid_disc_info": ([_vp, _i32p, _i32p], C.c_int),
     "tto_archive_destroy": ([_vp], C.c_int),
     "tto_archive_export": ([_vp, _vp, _vp, _vp], C.c_int),
     "tto_archive_import": ([_vp, _vp, _vp, _vp], C.c_int),
@@ -165,6 +176,7 @@ def tto_grid_create(grid, device=0):
         ab=np.ascontiguousarray(grid.asset_branch, dtype=np.int32),
         ast=np.ascontiguousarray(grid.action_station, dtype=np.int32),
         am=np.ascontiguousarray(grid.action_mask, dtype=np.uint32),
+        disc=np.ascontiguousarray(getattr(grid, "disc", np.zeros(0)), dtype=np.int32),
     )
     d = GridDesc()
     d.n_bus = int(grid.n_bus)
@@ -189,6 +201,9 @@ def tto_grid_create(grid, device=0):
     d.action_mask = _ptr(keep["am"], C.c_uint32)
     d.k_max = int(grid.k_max)
     d.device = int(device)
+    d.n_disc = int(keep["disc"].size)
+    d.disc_branch = _ptr(keep["disc"], C.c_int32) if keep["disc"].size else None
+    d.n_dslot = int(getattr(grid, "n_dslot", 0))
     h = _vp()
     check(lib().tto_grid_create(C.byref(d), C.byref(h)))
     return h
@@ -203,6 +218,12 @@ def tto_grid_info(h):
     check(lib().tto_grid_info(h, *[C.byref(x) for x in v]))
     keys = ["n_branch", "n_monitored", "n_outage", "n_time", "k_max", "n_action"]
     return {k: x.value for k, x in zip(keys, v)}
+
+
+def tto_grid_disc_info(h):
+    nd, ns = C.c_int32(), C.c_int32()
+    check(lib().tto_grid_disc_info(h, C.byref(nd), C.byref(ns)))
+    return nd.value, ns.value
 
 
 def tto_grid_base_flows(h, n_time, n_branch):
@@ -309,9 +330,12 @@ def tto_grid_profile_read(h):
     return [ms[0], ms[1], ms[2]], n.value
 
 
-def tto_archive_create(grid_h, d_split, d_moved):
+def tto_archive_create(grid_h, d_split, d_moved, d_disc=1):
     a = _vp()
-    check(lib().tto_archive_create(grid_h, int(d_split), int(d_moved), C.byref(a)))
+    if d_disc == 1:
+        check(lib().tto_archive_create(grid_h, int(d_split), int(d_moved), C.byref(a)))
+    else:
+        check(lib().tto_archive_create_ex(grid_h, int(d_split), int(d_moved), int(d_disc), C.byref(a)))
     return a
 
 
@@ -340,9 +364,15 @@ def tto_archive_insert(a, topo, B, fitness, cell, stream):
 
 
 def _mut(mp):
+    """MutParams from (p_add, p_remove, p_change, p_identity, n_mut_mean[,
+    dp_add, dp_remove, dp_change, dp_identity[, crossover, p_c1]])."""
     m = MutParams()
     m.p_add, m.p_remove, m.p_change, m.p_identity = mp[0], mp[1], mp[2], mp[3]
     m.n_mut_mean = mp[4]
+    dp = tuple(mp[5:9]) if len(mp) >= 9 else DEFAULT_DISC_PROBS
+    m.dp_add, m.dp_remove, m.dp_change, m.dp_identity = dp
+    m.crossover = int(mp[9]) if len(mp) >= 10 else 0
+    m.p_c1 = float(mp[10]) if len(mp) >= 11 else DEFAULT_P_C1
     return m
 
 

@@ -76,6 +76,7 @@ GraphKey make_key(const tto_eval_job* jobs, int n, const tto_eval_opts* o) {
   GraphKey k;
   k.words.push_back(((uint64_t)o->precision << 48) | ((uint64_t)o->fitness_kind << 32) |
                     ((uint64_t)o->d_split << 16) | (uint64_t)o->d_moved);
+  k.words.push_back((uint64_t)(uint32_t)o->d_disc);
   for (int i = 0; i < n; ++i) {
     const tto_eval_job& j = jobs[i];
     k.words.push_back(j.grid->uid);
@@ -141,10 +142,10 @@ extern "C" int tto_grid_autotune(tto_grid* g, int32_t B, int32_t n_t, int32_t pr
   int rc = ensure_workspace(g, B, padded_T(n_t));
   if (rc) return rc;
   Workspace& w = g->ws;
-  TTO_CUDA_TRY(cudaMemsetAsync(w.topo, 0xFF, (size_t)B * g->k_max * sizeof(int32_t), s));
+  TTO_CUDA_TRY(cudaMemsetAsync(w.topo, 0xFF, (size_t)B * g->gw * sizeof(int32_t), s));
   std::vector<int32_t> tsel(n_t);
   for (int t = 0; t < n_t; ++t) tsel[t] = t;
-  tto_eval_opts o;
+  tto_eval_opts o{};
   o.precision = precision;
   o.fitness_kind = TTO_FIT_WORKLOAD;
   o.d_split = 8;

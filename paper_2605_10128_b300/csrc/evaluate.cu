@@ -69,13 +69,29 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
   __shared__ double s_sb[TTO_MAX_K];
   __shared__ int s_cnt_c0, s_cnt_isl;
   __shared__ float s_umax, s_vmax;
+  __shared__ int s_dis[TTO_MAX_K], s_nd;  // branches the genome opens
 
   if (tid == 0) {
-    int k = 0, ne = 0, bad = 0, ns = 0, nm = 0;
+    int k = 0, ne = 0, bad = 0, ns = 0, nm = 0, nd = 0;
     int stations[TTO_MAX_K];
+    const int32_t* row = a.topo + (size_t)b * a.gw;
+    // opened branches first: a split does not move a branch that is open
+    for (int j = 0; j < a.n_dslot; ++j) {
+      const int dj = row[a.k_max + j];
+      if (dj < 0) continue;
+      if (dj >= a.n_disc) {
+        bad = 1;
+        break;
+      }
+      const int e = a.disc[dj];
+      for (int q = 0; q < nd; ++q)
+        if (s_dis[q] == e) bad = 1;
+      if (bad) break;
+      s_dis[nd++] = e;
+    }
     s_slot[0] = 0;
-    for (int j = 0; j < a.k_max; ++j) {
-      int act = a.topo[(size_t)b * a.k_max + j];
+    for (int j = 0; j < a.k_max && !bad; ++j) {
+      int act = row[j];
       if (act < 0) continue;
       if (act >= a.A) {
         bad = 1;
@@ -100,6 +116,9 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
           s_injbus[k] = bus;
           continue;
         }
+        bool open = false;
+        for (int q = 0; q < nd; ++q) open = open || s_dis[q] == e;
+        if (open) continue;  // busbar B keeps only open branches: zero pivot, islanded
         double sg = (a.from[e] == bus) ? 1.0 : -1.0;
         s_e[ne] = e;
         s_sign[ne] = sg;
@@ -112,9 +131,25 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
       ++k;
       s_slot[k] = ne;
     }
+    // an opened branch is a phase shift across it whose constraint holds its
+    // flow at zero: one more slot with S = e_l (its from end) and no injection
+    for (int q = 0; q < nd && !bad; ++q) {
+      const int e = s_dis[q];
+      s_injbus[k] = -1;
+      s_e[ne] = e;
+      s_sign[ne] = 1.0;
+      s_coef[ne] = a.b[e];
+      s_col[ne] = a.Nsw + (size_t)a.swcol[e] * a.E;
+      s_coef32[ne] = (float)a.b[e];
+      s_col32[ne] = a.Nsw32 + (size_t)a.swcol[e] * a.E;
+      ++ne;
+      ++k;
+      s_slot[k] = ne;
+    }
     s_k = bad ? 0 : k;
     s_ns = ns;
     s_nm = nm;
+    s_nd = bad ? 0 : nd;
     s_island = bad;
     s_cnt_c0 = 0;
     s_cnt_isl = 0;
@@ -312,8 +347,10 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
       v[jj] = jj < k ? (float)(W[jj] * inv_be) : 0.f;
       vmax = fmaxf(vmax, fabsf(v[jj]));
     }
-    const bool isl = !(npcc > kIslandTol);
-    if (isl && c < a.O) ++islcnt;
+    bool opened = false;  // an outage of an open branch is no contingency
+    for (int q = 0; q < s_nd; ++q) opened = opened || s_dis[q] == e;
+    const bool isl = opened || !(npcc > kIslandTol);
+    if (isl && !opened && c < a.O) ++islcnt;
     const double inv_np = isl ? 0.0 : 1.0 / npcc;
     for (int t = 0; t < TT; ++t) {
       float g = 0.f;
@@ -345,7 +382,7 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
     inf.lambda_c0 = dead ? 0.f : (float)s_cnt_c0;
     inf.umax = s_umax;
     inf.vmax = s_vmax;
-    inf.pad = 0.f;
+    inf.nd = s_nd;
     a.info[b] = inf;
   }
 }
@@ -372,12 +409,12 @@ __global__ void fitness_kernel(EvalArgs a) {
     fit = (float)(-(lo + (double)ml));
   }
   a.fitness[b] = fit;
-  const int cs = min(inf.ns, a.d_split - 1), cm = min(inf.nm, a.d_moved - 1);
+  const int cs = min(inf.ns, a.d_split - 1), cm = min(inf.nm, a.d_moved - 1), cd = min(inf.nd, a.d_disc - 1);
   if (a.desc) {
     a.desc[2 * b] = inf.ns;
     a.desc[2 * b + 1] = inf.nm;
   }
-  if (a.cell) a.cell[b] = cs * a.d_moved + cm;
+  if (a.cell) a.cell[b] = (cs * a.d_moved + cm) * a.d_disc + cd;
   if (a.island) a.island[b] = (uint8_t)((inf.island_base ? 1 : 0) | (inf.n_islanded > 0 ? 2 : 0));
   if (a.metrics) {
     float* m = a.metrics + (size_t)b * 4;
@@ -419,7 +456,7 @@ int ensure_workspace(tto_grid* g, int B, int T) {
   TTO_CUDA_TRY(cudaMalloc(&w.cell, (size_t)nB * sizeof(int32_t)));
   TTO_CUDA_TRY(cudaMalloc(&w.desc, (size_t)nB * 2 * sizeof(int32_t)));
   TTO_CUDA_TRY(cudaMalloc(&w.island, (size_t)nB * sizeof(uint8_t)));
-  TTO_CUDA_TRY(cudaMalloc(&w.topo, (size_t)nB * g->k_max * sizeof(int32_t)));
+  TTO_CUDA_TRY(cudaMalloc(&w.topo, (size_t)nB * g->gw * sizeof(int32_t)));
   w.cap_B = nB;
   w.cap_T = nT;
   return TTO_OK;
@@ -440,7 +477,7 @@ int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, 
   if (!g || !o) return set_error(TTO_E_ARG, "null argument");
   if (B < 0) return set_error(TTO_E_ARG, "negative batch");
   if (B > 0 && (!topo || !fitness)) return set_error(TTO_E_ARG, "null topology or fitness buffer");
-  if (o->d_split < 1 || o->d_moved < 1) return set_error(TTO_E_ARG, "archive extents must be >= 1");
+  if (o->d_split < 1 || o->d_moved < 1 || o->d_disc < 0) return set_error(TTO_E_ARG, "archive extents must be >= 1");
   if (o->precision < TTO_PREC_FP32 || o->precision > TTO_PREC_FP16X3) return set_error(TTO_E_ARG, "unknown precision");
   if (o->fitness_kind != TTO_FIT_WORKLOAD && o->fitness_kind != TTO_FIT_F1) return set_error(TTO_E_ARG, "unknown fitness kind");
   if (n_t < 0 || n_t > TTO_MAX_T || (tsel == nullptr && g->T > TTO_MAX_T))
@@ -479,6 +516,7 @@ int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, 
   a.asset_br = g->d_asset_br;
   a.act_st = g->d_act_st;
   a.act_mask = g->d_act_mask;
+  a.disc = g->d_disc;
   a.status = g->d_status;
   a.E = g->E;
   a.n_bus = g->n_bus;
@@ -488,13 +526,17 @@ int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, 
   a.O_pad = g->O_pad;
   a.A = g->A;
   a.k_max = g->k_max;
+  a.n_disc = g->n_disc;
+  a.n_dslot = g->n_dslot;
+  a.gw = g->gw;
   a.n_t = n_t;
   a.TT = TT;
   a.TC = TT <= 4 ? TT : 8;
   a.n_tch = (TT + a.TC - 1) / a.TC;
-  a.KP = padded_K(g->k_max);
+  a.KP = padded_K(g->gw);
   a.d_split = o->d_split;
   a.d_moved = o->d_moved;
+  a.d_disc = o->d_disc > 1 ? o->d_disc : 1;
   a.topo = topo;
   a.B = B;
   a.U = w.U;

@@ -151,6 +151,9 @@ int validate(const tto_grid_desc* d) {
   if (d->slack < 0 || d->slack >= d->n_bus) return set_error(TTO_E_ARG, "slack out of range");
   if (d->n_time < 1) return set_error(TTO_E_ARG, "n_time must be >= 1");
   if (d->k_max < 1 || d->k_max > TTO_MAX_K) return set_error(TTO_E_ARG, "k_max must be in [1, %d]", TTO_MAX_K);
+  if (d->n_dslot < 0 || d->k_max + d->n_dslot > TTO_MAX_K)
+    return set_error(TTO_E_ARG, "k_max + n_dslot must be <= %d (n_dslot >= 0)", TTO_MAX_K);
+  if (d->n_disc < 0 || (d->n_disc > 0 && !d->disc_branch)) return set_error(TTO_E_ARG, "bad disconnection set");
   for (int l = 0; l < d->n_branch; ++l) {
     int f = d->from[l], t = d->to[l];
     if (f < 0 || f >= d->n_bus || t < 0 || t >= d->n_bus || f == t)
@@ -166,6 +169,12 @@ int validate(const tto_grid_desc* d) {
   for (int i = 0; i < d->n_monitored; ++i) {
     int l = d->monitored[i];
     if (l < 0 || l >= d->n_branch || seen[l]) return set_error(TTO_E_ARG, "monitored id %d invalid or repeated", l);
+    seen[l] = 1;
+  }
+  std::fill(seen.begin(), seen.end(), 0);
+  for (int i = 0; i < d->n_disc; ++i) {
+    int l = d->disc_branch[i];
+    if (l < 0 || l >= d->n_branch || seen[l]) return set_error(TTO_E_ARG, "disconnection id %d invalid or repeated", l);
     seen[l] = 1;
   }
   std::fill(seen.begin(), seen.end(), 0);
@@ -233,6 +242,10 @@ static int build_grid(const tto_grid_desc* d, tto_grid* g) {
   g->S = d->n_station;
   g->A = d->n_action;
   g->k_max = d->k_max;
+  g->n_disc = d->n_disc;
+  g->n_dslot = d->n_dslot;
+  g->gw = d->k_max + d->n_dslot;
+  if (g->n_disc > 0) g->disc.assign(d->disc_branch, d->disc_branch + g->n_disc);
   g->E_mon_pad = (g->E_mon + kRowTile - 1) / kRowTile * kRowTile;
   g->O_pad = (g->O + kColPad - 1) / kColPad * kColPad;
   g->n_rowtiles = g->E_mon_pad / kRowTile;
@@ -302,7 +315,7 @@ static int build_grid(const tto_grid_desc* d, tto_grid* g) {
   SparseLDL ldl;
   if (!ldl.factor(nr, adj, dg)) return set_error(TTO_E_DISCONNECTED, "reduced susceptance matrix is singular");
 
-  // columns needed: outages and movable branches
+  // columns needed: outages and the branches a split can move or a genome open
   std::vector<int> swcol(E, -1);
   std::vector<int> swlist;
   for (int s = 0; s < g->S; ++s)
@@ -312,6 +325,11 @@ static int build_grid(const tto_grid_desc* d, tto_grid* g) {
         swcol[e] = (int)swlist.size();
         swlist.push_back(e);
       }
+    }
+  for (int e : g->disc)
+    if (swcol[e] < 0) {
+      swcol[e] = (int)swlist.size();
+      swlist.push_back(e);
     }
   g->n_sw = (int)swlist.size();
   std::vector<int> outpos(E, -1);
@@ -402,6 +420,7 @@ static int build_grid(const tto_grid_desc* d, tto_grid* g) {
   if ((rc = upload(&g->d_act_st, g->act_st.data(), g->act_st.size()))) return rc;
   if ((rc = upload(&g->d_act_off, g->act_off.data(), g->act_off.size()))) return rc;
   if ((rc = upload(&g->d_act_mask, g->act_mask.data(), g->act_mask.size()))) return rc;
+  if ((rc = upload(&g->d_disc, g->disc.empty() ? nullptr : g->disc.data(), g->disc.size()))) return rc;
   int zero = 0;
   if ((rc = upload(&g->d_status, &zero, 1))) return rc;
   return TTO_OK;
@@ -414,7 +433,7 @@ static void release(tto_grid* g) {
   free_workspace(g);
   void* ptrs[] = {g->d_from, g->d_Nf, g->d_Nmo, g->d_Nsw, g->d_Nsw32, g->d_swcol, g->d_f0, g->d_p, g->d_b, g->d_lim,
                   g->d_mon, g->d_out, g->d_Ncc, g->d_station_bus, g->d_asset_off,
-                  g->d_asset_br, g->d_act_st, g->d_act_off, g->d_act_mask, g->d_status};
+                  g->d_asset_br, g->d_act_st, g->d_act_off, g->d_act_mask, g->d_disc, g->d_status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& e : g->prof_ev) cudaEventDestroy(e);
@@ -467,6 +486,13 @@ int tto_grid_info(const tto_grid* g, int32_t* n_branch, int32_t* n_monitored, in
   if (n_time) *n_time = g->T;
   if (k_max) *k_max = g->k_max;
   if (n_action) *n_action = g->A;
+  return TTO_OK;
+}
+
+int tto_grid_disc_info(const tto_grid* g, int32_t* n_disc, int32_t* n_dslot) {
+  if (!g) return tto::set_error(TTO_E_ARG, "null grid");
+  if (n_disc) *n_disc = g->n_disc;
+  if (n_dslot) *n_dslot = g->n_dslot;
   return TTO_OK;
 }
 

@@ -1,15 +1,22 @@
-// MapElites on the device: Philox-driven split mutation (Algorithm 1, action
-// part), deterministic scatter insert into a one-elite-per-cell archive
-// (Algorithm 3), and the fused iteration.
+// MapElites on the device: Philox-driven mutation (Algorithm 1, split and
+// disconnection parts) and crossover (Algorithm 2), deterministic scatter
+// insert into a one-elite-per-cell archive (Algorithm 3), and the fused
+// iteration.
 //
 // Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed, counter =
 // (word block, candidate, iteration lo, iteration hi).  Every decision compares
 // one 32-bit word with an integer threshold computed on the host in FP64 from
 // the mutation probabilities, so the draws are reproducible bit for bit by any
 // implementation that follows the same word order:
-//   parent word, N_mut word, then per mutation round one operation word and the
-//   operation's own words (Add: slot, action; Remove: slot; Change: slot, new
-//   action), and a final forced Add (slot, action) if the genome ended empty.
+//   mutation: parent word, N_mut word, then per mutation round one operation
+//   word and the operation's own words (Add: slot, action; Remove: slot;
+//   Change: slot, new action); then, with disconnection slots, one operation
+//   word and its words (Add: slot, branch; Remove: slot; Change: branch, slot),
+//   else a forced split Add (slot, action) if the genome ended empty;
+//   crossover: two parent words, then per child slot (splits, then
+//   disconnections) a parent word and an entry word until a part runs dry.
+// The batch's mutation/crossover split b_mc is candidate 0xFFFFFFFF's first
+// word.
 #include <math.h>
 #include <string.h>
 
@@ -44,17 +51,20 @@ __device__ __forceinline__ int uniform_index(uint32_t w, int n) {
 }
 
 struct MutArgs {
-  const int32_t* parents;     // archive genomes [cells][k_max]
+  const int32_t* parents;     // archive genomes [cells][gw]
   const int32_t* filled_list; // count, then filled cells
   const int* act_off;         // [S+1]
   const int* act_st;          // [A]
-  int A, k_max;
+  int A, k_max, n_dslot, n_disc, gw;
   uint2 key;
   uint32_t it_lo, it_hi;
   int B;
+  int crossover;
+  unsigned long long t_c1;    // parent-1 threshold floor(p_c1 2^32) (2^32 at p_c1 = 1)
   unsigned long long op_thr[16][4];
+  unsigned long long dop_thr[16][4];
   unsigned long long poi_thr[TTO_MAX_K];
-  int32_t* out;               // [B][k_max]
+  int32_t* out;               // [B][gw]
 };
 
 __device__ int sample_allowed(const int* g, int k, const MutArgs& a, uint32_t w) {
@@ -88,6 +98,106 @@ __device__ void do_add(int* g, int k, const MutArgs& a, Words& ws) {
   g[slot] = sample_allowed(g, k, a, ws.next());
 }
 
+// Uniform disconnection index among those not in d[0 .. nd).
+__device__ int sample_free(const int* d, int nd, int n_disc, uint32_t w) {
+  int ex[TTO_MAX_K], ne = 0;
+  for (int i = 0; i < nd; ++i) {
+    if (d[i] < 0) continue;
+    int j = ne++;
+    while (j > 0 && ex[j - 1] > d[i]) {
+      ex[j] = ex[j - 1];
+      --j;
+    }
+    ex[j] = d[i];
+  }
+  int pos = uniform_index(w, n_disc - ne);
+  for (int i = 0; i < ne; ++i) {
+    if (pos >= ex[i]) ++pos;
+    else break;
+  }
+  return pos;
+}
+
+// The disconnection part of Algorithm 1 on slots d[0 .. nd), after the split
+// rounds left the split slots g[0 .. k).
+__device__ void mutate_disc(const int* g, int k, int* d, int nd, const MutArgs& a, Words& ws) {
+  int filled[TTO_MAX_K], nfl = 0, empty[TTO_MAX_K], nem = 0;
+  for (int i = 0; i < nd; ++i) {
+    if (d[i] >= 0) filled[nfl++] = i;
+    else empty[nem++] = i;
+  }
+  const int free = a.n_disc - nfl;
+  int feas = 1 << kIdentity;
+  if (nem > 0 && free > 0) feas |= 1 << kAdd;
+  if (nfl > 0) feas |= 1 << kRemove;
+  if (nfl > 0 && free > 0) feas |= 1 << kChange;
+  const unsigned long long w = ws.next();
+  int op = kIdentity;
+  for (int i = 0; i < 4; ++i)
+    if (w < a.dop_thr[feas][i]) {
+      op = i;
+      break;
+    }
+  bool no_split = true;
+  for (int i = 0; i < k; ++i) no_split = no_split && g[i] < 0;
+  if (nfl == 0 && no_split && ((feas >> kAdd) & 1)) op = kAdd;  // never the unchanged default
+  if (op == kAdd) {
+    const int slot = empty[uniform_index(ws.next(), nem)];
+    d[slot] = sample_free(d, nd, a.n_disc, ws.next());
+  } else if (op == kRemove) {
+    d[filled[uniform_index(ws.next(), nfl)]] = -1;
+  } else if (op == kChange) {
+    const int x = sample_free(d, nd, a.n_disc, ws.next());
+    d[filled[uniform_index(ws.next(), nfl)]] = x;
+  }
+}
+
+// One part of Algorithm 2: child slots take, in turn, an entry of the
+// parents' union that is feasible for the child (distinct stations for
+// splits, distinct branches for disconnections); parent 1 with probability
+// p_c1 when both parents offer one, a parent whose weight is zero never; the
+// first slot with nothing to take ends the part.  An entry both parents hold
+// counts as parent 1's.
+__device__ void cross_part(const int* x1, const int* x2, int width, bool split, const MutArgs& a, Words& ws,
+                           int* child) {
+  int n = 0;
+  for (int slot = 0; slot < width; ++slot) {
+    int r1[TTO_MAX_K], n1 = 0, r2[TTO_MAX_K], n2 = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+      const int* x = pass == 0 ? x1 : x2;
+      for (int i = 0; i < width; ++i) {
+        const int v = x[i];
+        if (v < 0) continue;
+        if (pass == 1) {
+          bool in1 = false;
+          for (int j = 0; j < width; ++j) in1 = in1 || x1[j] == v;
+          if (in1) continue;
+        }
+        bool taken = false;
+        for (int j = 0; j < n; ++j)
+          taken = taken || (split ? a.act_st[child[j]] == a.act_st[v] : child[j] == v);
+        if (taken) continue;
+        if (pass == 0) r1[n1++] = v;
+        else r2[n2++] = v;
+      }
+    }
+    if (n1 == 0 && n2 == 0) break;
+    const unsigned long long w = ws.next();
+    bool from1;
+    if (n1 > 0 && n2 > 0) {
+      from1 = w < a.t_c1;
+    } else if (n1 > 0) {
+      if (a.t_c1 == 0) break;
+      from1 = true;
+    } else {
+      if (a.t_c1 >= (1ull << 32)) break;
+      from1 = false;
+    }
+    child[n++] = from1 ? r1[uniform_index(ws.next(), n1)] : r2[uniform_index(ws.next(), n2)];
+  }
+  for (int i = n; i < width; ++i) child[i] = -1;
+}
+
 __global__ void propose_kernel(MutArgs a) {
   const int cand = blockIdx.x * blockDim.x + threadIdx.x;
   if (cand >= a.B) return;
@@ -98,15 +208,33 @@ __global__ void propose_kernel(MutArgs a) {
   ws.it_hi = a.it_hi;
   ws.block = 0;
   ws.idx = 4;
-  const int k = a.k_max;
-  int g[TTO_MAX_K];
+  const int k = a.k_max, nd = a.n_dslot, gw = a.gw;
+  int g[TTO_MAX_K];  // split slots, then disconnection slots
   const int nf = a.filled_list[0];
+  int b_mc = a.B;
+  if (a.crossover) {
+    Words wr = ws;
+    wr.cand = 0xFFFFFFFFu;
+    b_mc = uniform_index(wr.next(), a.B + 1);
+  }
+  if (cand >= b_mc) {
+    int p1[TTO_MAX_K], p2[TTO_MAX_K];
+    const uint32_t w1 = ws.next(), w2 = ws.next();
+    for (int i = 0; i < gw; ++i) {
+      p1[i] = nf > 0 ? a.parents[(size_t)a.filled_list[1 + uniform_index(w1, nf)] * gw + i] : -1;
+      p2[i] = nf > 0 ? a.parents[(size_t)a.filled_list[1 + uniform_index(w2, nf)] * gw + i] : -1;
+    }
+    cross_part(p1, p2, k, true, a, ws, g);
+    if (nd > 0) cross_part(p1 + k, p2 + k, nd, false, a, ws, g + k);
+    for (int i = 0; i < gw; ++i) a.out[(size_t)cand * gw + i] = g[i];
+    return;
+  }
   const uint32_t wp = ws.next();
   if (nf > 0) {
     const int cell = a.filled_list[1 + uniform_index(wp, nf)];
-    for (int i = 0; i < k; ++i) g[i] = a.parents[(size_t)cell * k + i];
+    for (int i = 0; i < gw; ++i) g[i] = a.parents[(size_t)cell * gw + i];
   } else {
-    for (int i = 0; i < k; ++i) g[i] = -1;
+    for (int i = 0; i < gw; ++i) g[i] = -1;
   }
   // N_mut ~ clip(Poisson(mean), 1, k_max) by inversion
   const uint32_t wn = ws.next();
@@ -154,10 +282,14 @@ __global__ void propose_kernel(MutArgs a) {
       g[slot] = off + rr + (rr >= cur ? 1 : 0);
     }
   }
-  bool empty = true;
-  for (int i = 0; i < k; ++i) empty = empty && g[i] < 0;
-  if (empty) do_add(g, k, a, ws);
-  for (int i = 0; i < k; ++i) a.out[(size_t)cand * k + i] = g[i];
+  if (nd > 0 && a.n_disc > 0) {
+    mutate_disc(g, k, g + k, nd, a, ws);
+  } else {
+    bool empty = true;
+    for (int i = 0; i < k; ++i) empty = empty && g[i] < 0;
+    if (empty) do_add(g, k, a, ws);
+  }
+  for (int i = 0; i < gw; ++i) a.out[(size_t)cand * gw + i] = g[i];
 }
 
 __global__ void philox_blocks_kernel(uint2 key, uint32_t cand, uint32_t it_lo, uint32_t it_hi,
@@ -193,7 +325,7 @@ __global__ void insert_key_kernel(const float* fit, const int32_t* cell, int B, 
 }
 
 __global__ void insert_apply_kernel(const float* fit, const int32_t* cell, const int32_t* topo,
-                                    int B, int cells, int k_max, const unsigned long long* key,
+                                    int B, int cells, int gw, const unsigned long long* key,
                                     float* afit, int32_t* agen, uint8_t* afilled) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= B) return;
@@ -204,7 +336,7 @@ __global__ void insert_apply_kernel(const float* fit, const int32_t* cell, const
   if (key[c] != k) return;  // not this cell's batch winner
   if (afilled[c] && !(f > afit[c])) return;
   afit[c] = f;
-  for (int j = 0; j < k_max; ++j) agen[(size_t)c * k_max + j] = topo[(size_t)i * k_max + j];
+  for (int j = 0; j < gw; ++j) agen[(size_t)c * gw + j] = topo[(size_t)i * gw + j];
   afilled[c] = 1;
 }
 
@@ -218,8 +350,9 @@ __global__ void filled_list_kernel(const uint8_t* filled, int cells, int32_t* li
 
 // Cumulative uint32 thresholds (2^32 for the last feasible operation) of the
 // operation draw, for each feasibility subset of {Add, Remove, Change, Identity}.
-void op_thresholds(const tto_mut_params* mp, unsigned long long thr[16][4]) {
-  const double p[4] = {mp->p_add, mp->p_remove, mp->p_change, mp->p_identity};
+// With identity_fallback, a subset where no feasible operation has weight
+// draws Identity.
+void op_thresholds(const double p[4], bool identity_fallback, unsigned long long thr[16][4]) {
   for (int f = 0; f < 16; ++f) {
     double w[4], cum[4], acc = 0.0;
     int last = -1;
@@ -230,6 +363,10 @@ void op_thresholds(const tto_mut_params* mp, unsigned long long thr[16][4]) {
       if (w[i] > 0.0) last = i;
     }
     const double total = cum[3];
+    if (last < 0 && identity_fallback) {
+      for (int i = 0; i < 4; ++i) thr[f][i] = i == kIdentity ? 1ull << 32 : 0ull;
+      continue;
+    }
     for (int i = 0; i < 4; ++i) {
       if (last < 0 || i >= last)
         thr[f][i] = 1ull << 32;
@@ -258,6 +395,11 @@ int check_mut(const tto_mut_params* mp) {
   if (!(mp->p_identity > 0.0) && !(mp->p_add > 0.0 && mp->p_remove > 0.0))
     return set_error(TTO_E_ARG, "some operation must be feasible for every genome (p_identity > 0, or p_add and p_remove > 0)");
   if (!(mp->n_mut_mean >= 0.0) || !isfinite(mp->n_mut_mean)) return set_error(TTO_E_ARG, "n_mut_mean must be >= 0");
+  const double dp[4] = {mp->dp_add, mp->dp_remove, mp->dp_change, mp->dp_identity};
+  for (double x : dp)
+    if (!(x >= 0.0) || !isfinite(x)) return set_error(TTO_E_ARG, "disconnection probabilities must be >= 0");
+  if (mp->crossover != 0 && mp->crossover != 1) return set_error(TTO_E_ARG, "crossover must be 0 or 1");
+  if (!(mp->p_c1 >= 0.0 && mp->p_c1 <= 1.0)) return set_error(TTO_E_ARG, "p_c1 must be in [0, 1]");
   return TTO_OK;
 }
 
@@ -277,11 +419,19 @@ int propose_impl(tto_archive* ar, uint64_t seed, uint64_t it, int B, const tto_m
   a.act_st = g->d_act_st;
   a.A = g->A;
   a.k_max = g->k_max;
+  a.n_dslot = g->n_dslot;
+  a.n_disc = g->n_disc;
+  a.gw = g->gw;
+  a.crossover = mp->crossover;
+  a.t_c1 = mp->p_c1 >= 1.0 ? (1ull << 32) : (unsigned long long)floor(mp->p_c1 * 4294967296.0);
   a.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
   a.it_lo = (uint32_t)it;
   a.it_hi = (uint32_t)(it >> 32);
   a.B = B;
-  op_thresholds(mp, a.op_thr);
+  const double p[4] = {mp->p_add, mp->p_remove, mp->p_change, mp->p_identity};
+  const double dp[4] = {mp->dp_add, mp->dp_remove, mp->dp_change, mp->dp_identity};
+  op_thresholds(p, false, a.op_thr);
+  op_thresholds(dp, true, a.dop_thr);
   poisson_thresholds(mp->n_mut_mean, g->k_max, a.poi_thr);
   a.out = out;
   if (B > 0) {
@@ -297,7 +447,7 @@ int insert_impl(tto_archive* ar, const int32_t* topo, int B, const float* fit, c
   const int cells = ar->cells;
   key_reset_kernel<<<(cells + 255) / 256, 256, 0, s>>>(ar->d_key, cells);
   insert_key_kernel<<<(B + 255) / 256, 256, 0, s>>>(fit, cell, B, cells, ar->d_key);
-  insert_apply_kernel<<<(B + 255) / 256, 256, 0, s>>>(fit, cell, topo, B, cells, ar->g->k_max,
+  insert_apply_kernel<<<(B + 255) / 256, 256, 0, s>>>(fit, cell, topo, B, cells, ar->g->gw,
                                                       ar->d_key, ar->d_fit, ar->d_genome,
                                                       ar->d_filled);
   filled_list_kernel<<<1, 32, 0, s>>>(ar->d_filled, cells, ar->d_filled_list);
@@ -312,7 +462,12 @@ using namespace tto;
 extern "C" {
 
 int tto_archive_create(tto_grid* g, int32_t d_split, int32_t d_moved, tto_archive** out) {
-  if (!g || !out || d_split < 1 || d_moved < 1) return set_error(TTO_E_ARG, "bad archive arguments");
+  return tto_archive_create_ex(g, d_split, d_moved, 1, out);
+}
+
+int tto_archive_create_ex(tto_grid* g, int32_t d_split, int32_t d_moved, int32_t d_disc, tto_archive** out) {
+  if (!g || !out || d_split < 1 || d_moved < 1 || d_disc < 1) return set_error(TTO_E_ARG, "bad archive arguments");
+  if ((int64_t)d_split * d_moved * d_disc > (1 << 24)) return set_error(TTO_E_ARG, "more than 2^24 archive cells");
   *out = nullptr;
   TTO_CUDA_TRY(cudaSetDevice(g->device));
   tto_archive* a = new (std::nothrow) tto_archive();
@@ -320,17 +475,18 @@ int tto_archive_create(tto_grid* g, int32_t d_split, int32_t d_moved, tto_archiv
   a->g = g;
   a->d_split = d_split;
   a->d_moved = d_moved;
-  a->cells = d_split * d_moved;
+  a->d_disc = d_disc;
+  a->cells = d_split * d_moved * d_disc;
   const size_t C = a->cells;
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMalloc(&a->d_fit, C * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&a->d_genome, C * g->k_max * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&a->d_genome, C * g->gw * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&a->d_filled, C);
   if (e == cudaSuccess) e = cudaMalloc(&a->d_key, C * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(&a->d_filled_list, (C + 1) * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemset(a->d_filled, 0, C);
   if (e == cudaSuccess) e = cudaMemset(a->d_filled_list, 0, (C + 1) * sizeof(int32_t));
-  if (e == cudaSuccess) e = cudaMemset(a->d_genome, 0xFF, C * g->k_max * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(a->d_genome, 0xFF, C * g->gw * sizeof(int32_t));
   if (e == cudaSuccess) {
     std::vector<float> ninf(C, -INFINITY);
     e = cudaMemcpy(a->d_fit, ninf.data(), C * sizeof(float), cudaMemcpyHostToDevice);
@@ -359,7 +515,7 @@ int tto_archive_export(const tto_archive* a, float* fitness, int32_t* genome, ui
   TTO_CUDA_TRY(cudaDeviceSynchronize());
   const size_t C = a->cells;
   if (fitness) TTO_CUDA_TRY(cudaMemcpy(fitness, a->d_fit, C * sizeof(float), cudaMemcpyDeviceToHost));
-  if (genome) TTO_CUDA_TRY(cudaMemcpy(genome, a->d_genome, C * a->g->k_max * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (genome) TTO_CUDA_TRY(cudaMemcpy(genome, a->d_genome, C * a->g->gw * sizeof(int32_t), cudaMemcpyDeviceToHost));
   if (filled) TTO_CUDA_TRY(cudaMemcpy(filled, a->d_filled, C, cudaMemcpyDeviceToHost));
   return TTO_OK;
 }
@@ -368,13 +524,14 @@ int tto_archive_import(tto_archive* a, const float* fitness, const int32_t* geno
                        const uint8_t* filled) {
   if (!a || !fitness || !genome || !filled) return set_error(TTO_E_ARG, "null argument");
   const size_t C = a->cells;
-  const int k = a->g->k_max;
+  const int k = a->g->gw;
   for (size_t c = 0; c < C; ++c) {
     if (!filled[c]) continue;
     if (!isfinite(fitness[c])) return set_error(TTO_E_ARG, "filled cell %zu has non-finite fitness", c);
     for (int j = 0; j < k; ++j) {
-      int act = genome[c * k + j];
-      if (act < -1 || act >= a->g->A) return set_error(TTO_E_ARG, "cell %zu holds invalid action %d", c, act);
+      const int v = genome[c * k + j];
+      const int hi = j < a->g->k_max ? a->g->A : a->g->n_disc;
+      if (v < -1 || v >= hi) return set_error(TTO_E_ARG, "cell %zu slot %d holds invalid id %d", c, j, v);
     }
   }
   TTO_CUDA_TRY(cudaSetDevice(a->g->device));
@@ -406,7 +563,7 @@ int tto_mapelites_step(tto_archive* a, uint64_t seed, uint64_t iteration, int32_
                        const tto_mut_params* mp, const tto_eval_opts* opts, int32_t* topo_out,
                        float* fitness_out, void* stream) {
   if (!a || !opts || B < 1) return set_error(TTO_E_ARG, "bad step arguments");
-  if (opts->d_split != a->d_split || opts->d_moved != a->d_moved)
+  if (opts->d_split != a->d_split || opts->d_moved != a->d_moved || (opts->d_disc > 1 ? opts->d_disc : 1) != a->d_disc)
     return set_error(TTO_E_ARG, "evaluation cell extents differ from the archive's");
   tto_grid* g = a->g;
   cudaStream_t s = (cudaStream_t)stream;
@@ -423,7 +580,7 @@ int tto_mapelites_step(tto_archive* a, uint64_t seed, uint64_t iteration, int32_
   rc = insert_impl(a, w.topo, B, w.fit, w.cell, s);
   if (rc) return rc;
   if (topo_out)
-    TTO_CUDA_TRY(cudaMemcpyAsync(topo_out, w.topo, (size_t)B * g->k_max * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    TTO_CUDA_TRY(cudaMemcpyAsync(topo_out, w.topo, (size_t)B * g->gw * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   if (fitness_out)
     TTO_CUDA_TRY(cudaMemcpyAsync(fitness_out, w.fit, (size_t)B * sizeof(float), cudaMemcpyDeviceToDevice, s));
   return TTO_OK;

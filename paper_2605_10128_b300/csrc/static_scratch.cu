@@ -66,7 +66,7 @@ extern "C" int tto_evaluate_batch_static(tto_grid* g, const int32_t* topo, int32
   if (B > 0 && (!topo || !fitness)) return set_error(TTO_E_ARG, "null topology or fitness buffer");
   if (o->precision != TTO_PREC_FP32)
     return set_error(TTO_E_ARG, "the static-scratch entry point evaluates with TTO_PREC_FP32 only");
-  if (o->d_split < 1 || o->d_moved < 1) return set_error(TTO_E_ARG, "archive extents must be >= 1");
+  if (o->d_split < 1 || o->d_moved < 1 || o->d_disc < 0) return set_error(TTO_E_ARG, "archive extents must be >= 1");
   if (o->fitness_kind != TTO_FIT_WORKLOAD && o->fitness_kind != TTO_FIT_F1)
     return set_error(TTO_E_ARG, "unknown fitness kind");
   EvalArgs a;
@@ -120,6 +120,7 @@ extern "C" int tto_evaluate_batch_static(tto_grid* g, const int32_t* topo, int32
   a.asset_br = g->d_asset_br;
   a.act_st = g->d_act_st;
   a.act_mask = g->d_act_mask;
+  a.disc = g->d_disc;
   a.status = g->d_status;
   a.E = g->E;
   a.n_bus = g->n_bus;
@@ -129,13 +130,17 @@ extern "C" int tto_evaluate_batch_static(tto_grid* g, const int32_t* topo, int32
   a.O_pad = g->O_pad;
   a.A = g->A;
   a.k_max = g->k_max;
+  a.n_disc = g->n_disc;
+  a.n_dslot = g->n_dslot;
+  a.gw = g->gw;
   a.n_t = n_t;
   a.TT = TT;
   a.TC = TT <= 4 ? TT : 8;
   a.n_tch = (TT + a.TC - 1) / a.TC;
-  a.KP = g->k_max <= 2 ? 2 : (g->k_max <= 4 ? 4 : 8);
+  a.KP = g->gw <= 2 ? 2 : (g->gw <= 4 ? 4 : 8);
   a.d_split = o->d_split;
   a.d_moved = o->d_moved;
+  a.d_disc = o->d_disc > 1 ? o->d_disc : 1;
   a.precision = TTO_PREC_FP32;
   a.fitness_kind = o->fitness_kind;
   a.n_rowtiles = g->n_rowtiles;

@@ -1115,6 +1115,7 @@ int tto_surrogate_create(tto_grid* g, const tto_surrogate_cfg* cfg, tto_surrogat
       !(cfg->eps > 0.0))
     return set_error(TTO_E_ARG, "Adam needs lr > 0, 0 <= beta < 1, eps > 0");
   if (g->S < 1 || g->k_max < 1) return set_error(TTO_E_ARG, "the grid has no splittable stations");
+  if (g->n_dslot > 0) return set_error(TTO_E_ARG, "the surrogate screens split-only genomes (grid has disconnection slots)");
   TTO_CUDA_TRY(cudaSetDevice(g->device));
   tto_surrogate* s = new (std::nothrow) tto_surrogate();
   if (!s) return set_error(TTO_E_NOMEM, "host allocation failed");
@@ -1333,7 +1334,7 @@ int tto_mapelites_step_screened(tto_archive* a, tto_surrogate* s, uint64_t seed,
   if (n_propose > (1 << 30)) return set_error(TTO_E_ARG, "n_propose must be at most 2^30");
   if (train_steps < 0) return set_error(TTO_E_ARG, "train_steps must be >= 0");
   if (rank_by != TTO_SCREEN_SCORE && rank_by != TTO_SCREEN_CELL_GAIN) return set_error(TTO_E_ARG, "unknown rank_by");
-  if (opts->d_split != a->d_split || opts->d_moved != a->d_moved)
+  if (opts->d_split != a->d_split || opts->d_moved != a->d_moved || a->d_disc != 1 || opts->d_disc > 1)
     return set_error(TTO_E_ARG, "evaluation cell extents differ from the archive's");
   tto_grid* g = a->g;
   cudaStream_t st = (cudaStream_t)stream;

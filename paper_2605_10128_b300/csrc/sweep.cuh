@@ -27,12 +27,14 @@ struct EvalArgs {
   const int* asset_br;
   const int* act_st;
   const uint32_t* act_mask;
+  const int* disc;  // [n_disc] branches a genome may open
   int* status;
   int E, n_bus, E_mon, O, E_mon_pad, O_pad, A, k_max;
+  int n_disc, n_dslot, gw;  // disconnection set and slots; genome width k_max + n_dslot
   int n_t, TT, KP;
   int TC, n_tch;  // tensor-core sweep: timesteps per pass and number of passes
   int tsel[TTO_MAX_T];
-  int d_split, d_moved;
+  int d_split, d_moved, d_disc;
   int precision;
   int fitness_kind;
   int n_rowtiles;

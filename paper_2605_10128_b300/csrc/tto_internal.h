@@ -34,7 +34,7 @@ struct TopoInfo {
   int nm;            // moved assets
   float lambda_c0;   // N-0 critical branches (summed over timesteps)
   float umax, vmax;  // largest |U| (monitored rows) and |V| (outage columns)
-  float pad;
+  int nd;            // opened branches (disconnection slots in use)
 };
 
 // Evaluation workspace, grown on demand (or once by tto_grid_reserve).
@@ -54,7 +54,7 @@ struct Workspace {
   int32_t* cell = nullptr;   // [B]
   int32_t* desc = nullptr;   // [B][2]
   uint8_t* island = nullptr; // [B]
-  int32_t* topo = nullptr;   // [B][k_max] proposed genomes (MapElites step)
+  int32_t* topo = nullptr;   // [B][gw] proposed genomes (MapElites step)
 };
 
 }  // namespace tto
@@ -64,8 +64,9 @@ struct tto_grid {
   uint64_t ws_epoch = 0;  // bumped whenever the workspace is reallocated
   int device = 0;
   int n_bus = 0, E = 0, slack = 0, T = 0, E_mon = 0, O = 0, S = 0, A = 0, k_max = 0;
+  int n_disc = 0, n_dslot = 0, gw = 0;  // disconnection set, its slots, genome width k_max + n_dslot
   int E_mon_pad = 0, O_pad = 0, n_sw = 0, n_rowtiles = 0;
-  std::vector<int> from, to, mon, out, station_bus, asset_off, asset_br, act_st, act_off;
+  std::vector<int> from, to, mon, out, station_bus, asset_off, asset_br, act_st, act_off, disc;
   std::vector<uint32_t> act_mask;
   std::vector<double> b, p, limit, f0;
   // device copies
@@ -88,6 +89,7 @@ struct tto_grid {
   int* d_act_st = nullptr;
   int* d_act_off = nullptr;
   uint32_t* d_act_mask = nullptr;
+  int* d_disc = nullptr;       // [n_disc] branches a genome may open
   int* d_status = nullptr;
   tto::Workspace ws;
   // sweep tile variant per precision mode chosen by tto_grid_autotune (-1: default)
@@ -99,9 +101,9 @@ struct tto_grid {
 
 struct tto_archive {
   tto_grid* g = nullptr;
-  int d_split = 0, d_moved = 0, cells = 0;
+  int d_split = 0, d_moved = 0, d_disc = 1, cells = 0;
   float* d_fit = nullptr;         // [cells]
-  int32_t* d_genome = nullptr;    // [cells][k_max]
+  int32_t* d_genome = nullptr;    // [cells][gw]
   uint8_t* d_filled = nullptr;    // [cells]
   unsigned long long* d_key = nullptr;  // [cells] batch winner keys
   int32_t* d_filled_list = nullptr;     // [cells + 1]: count, then filled cells ascending

@@ -27,9 +27,9 @@ def n_procs():
     return max(1, min(16, os.cpu_count() or 1))
 
 
-def oracle_eval(grid, topo, idx, timesteps=None, d_split=8, d_moved=8):
+def oracle_eval(grid, topo, idx, timesteps=None, d_split=8, d_moved=8, d_disc=1):
     return dcflow.evaluate_many(grid, [topo[i] for i in idx], processes=min(n_procs(), len(idx)),
-                                timesteps=timesteps, d_split=d_split, d_moved=d_moved)
+                                timesteps=timesteps, d_split=d_split, d_moved=d_moved, d_disc=d_disc)
 
 
 def compare(grid, out, idx, refs, tol=TOL_FP32, fitness_kind=0):
