@@ -55,11 +55,14 @@ def job_throughput(per_rank_units, world, steps, max_ms):
     return per_rank_units * world * steps / (max_ms / 1000.0)
 
 
-def workload_desc(cfg, B):
+def workload_desc(cfg, B, n_dslot=0, n_disc=0):
     c = CONFIGS[cfg]
-    return (f"{cfg}: synthetic {c['n_bus']}-bus grid, {c['n_branch']} branches, "
-            f"{c['n_outage'] or c['n_branch']} outages x {c['n_branch']} monitored, T={c['T']}, "
-            f"batch {B} topologies with <= {c['k_max']} splits")
+    d = (f"{cfg}: synthetic {c['n_bus']}-bus grid, {c['n_branch']} branches, "
+         f"{c['n_outage'] or c['n_branch']} outages x {c['n_branch']} monitored, T={c['T']}, "
+         f"batch {B} topologies with <= {c['k_max']} splits")
+    if n_dslot:
+        d += f" and <= {n_dslot} of {n_disc} branch disconnections"
+    return d
 
 
 def peaks():
@@ -167,10 +170,10 @@ def oracle_sample(sg, n_topo, n_out, seed, cores):
     return equiv / wall, wall, desc
 
 
-def make_grid(cfg, device, seed):
+def make_grid(cfg, device, seed, n_disc=0, n_dslot=0):
     from paper_2605_10128_b300 import Grid
     c = CONFIGS[cfg]
-    sg = config_grid(cfg, seed=seed)
+    sg = config_grid(cfg, seed=seed, n_disc=n_disc, n_dslot=n_dslot)
     sg = sg.with_limits(np.ones(sg.n_branch))
     t0 = time.perf_counter()
     g = Grid(sg, device=device)
@@ -391,6 +394,11 @@ def main():
                     help="--config surrogate: screened variants rank:proposals[@first screened iteration] "
                          "(rank = score or gain)")
     ap.add_argument("--train-steps", type=int, default=8, help="--config surrogate: training steps per iteration")
+    ap.add_argument("--dslots", type=int, default=0, help="branch-disconnection slots per genome (0: splits only)")
+    ap.add_argument("--ndisc", type=int, default=0, help="disconnection set size (default: a hundredth of the branches)")
+    ap.add_argument("--ddisc", type=int, default=3, help="archive extent over opened branches when --dslots > 0")
+    ap.add_argument("--crossover", action="store_true", help="Algorithm 3's mutation/crossover split of each batch")
+    ap.add_argument("--p-c1", type=float, default=0.5, help="crossover bias toward the first parent")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -421,7 +429,10 @@ def main():
     c = CONFIGS[args.config]
     B = args.batch or c["batch"]
     ds, dm = c["archive"]
-    sg, g, create_s = make_grid(args.config, local, seed=0)
+    n_disc = (args.ndisc or -(-c["n_branch"] // 100)) if args.dslots else 0
+    dd = args.ddisc if args.dslots else 1
+    mut = (0.2, 0.2, 0.5, 0.1, 2.0, 0.25, 0.25, 0.5, 0.0, int(args.crossover), args.p_c1)
+    sg, g, create_s = make_grid(args.config, local, seed=0, n_disc=n_disc, n_dslot=args.dslots)
     g.reserve(B)
     # sweep tile variant chosen by the library's autotuner (timed on 512
     # topologies), unless --sweep-variant fixes it
@@ -430,12 +441,12 @@ def main():
         tuned_shape, tuned_ms = args.sweep_variant, None
     else:
         tuned_shape, tuned_ms = g.autotune(min(B, 512), precision=prec)
-    A = Archive(g, ds, dm)
+    A = Archive(g, ds, dm, dd)
     seed = rank_seed(rank)
     stream = torch.cuda.current_stream()
 
     for it in range(args.warmup):
-        A.step(seed, it, B, precision=prec)
+        A.step(seed, it, B, mutation=mut, precision=prec)
     g.sync_status()
 
     def barrier():
@@ -451,7 +462,7 @@ def main():
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
     for it in range(args.warmup, args.warmup + args.steps):
-        A.step(seed, it, B, precision=prec)
+        A.step(seed, it, B, mutation=mut, precision=prec)
     t1.record(stream)
     barrier()
     clk = clocks.stop()
@@ -469,7 +480,7 @@ def main():
     out = None
     for _ in range(2):
         topo_d.copy_(topo_h, non_blocking=True)
-        out = g.evaluate(topo_d, precision=prec, d_split=ds, d_moved=dm, out=out)
+        out = g.evaluate(topo_d, precision=prec, d_split=ds, d_moved=dm, d_disc=dd, out=out)
         fit_h.copy_(out["fitness"], non_blocking=True)
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -477,7 +488,7 @@ def main():
     e0.record(stream)
     for _ in range(args.steps):
         topo_d.copy_(topo_h, non_blocking=True)
-        out = g.evaluate(topo_d, precision=prec, d_split=ds, d_moved=dm, out=out)
+        out = g.evaluate(topo_d, precision=prec, d_split=ds, d_moved=dm, d_disc=dd, out=out)
         fit_h.copy_(out["fitness"], non_blocking=True)
     e1.record(stream)
     barrier()
@@ -510,10 +521,13 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_desc(args.config, B), "batch": B, "timesteps": T,
+            "config": {"workload": workload_desc(args.config, B, args.dslots, n_disc), "batch": B, "timesteps": T,
                        "precision": args.precision, "parallelism": f"independent searches x{world}",
                        "l2": "inputs larger than L2 (N tile 305 MB + per-batch workspace ~8 GB)",
                        "step": "one MapElites iteration: propose, exact N-1 evaluation, insert",
+                       "genome": {"split_slots": c["k_max"], "disconnection_slots": args.dslots,
+                                  "disconnection_set": n_disc, "archive": [ds, dm, dd],
+                                  "crossover": bool(args.crossover), "p_c1": args.p_c1},
                        "grid_create_s": round(create_s, 2),
                        "sweep_variant": {"chosen": tuned_shape, "ms_per_variant_at_B512": tuned_ms}},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
