@@ -252,6 +252,36 @@ def evaluate(grid, genome, timesteps=None, outages=None, d_split=8, d_moved=8, w
     return res
 
 
+def outage_energy(grid, genome, timesteps=None):
+    """Overload energy of every N-1 case of one topology (Sec. "AC-Validator":
+    the DC optimiser computes each N-1 case's overload energy to pick the worst
+    k): E_c = sum over timesteps and monitored branches of max(|F_l^(c)| -
+    fbar_l, 0).  NaN for an outage that islands the topology or whose branch it
+    already opened; all NaN when the topology itself islands the grid."""
+    r = evaluate(grid, genome, timesteps=timesteps, want_flows=True)
+    E = np.full(grid.outages.size, np.nan)
+    if r["island_base"]:
+        return E
+    lim = grid.limit[grid.monitored.astype(np.int64)]
+    for oi, F in r["per_outage"].items():
+        E[oi] = float(np.maximum(np.abs(F) - lim[None, :], 0.0).sum())
+    return E
+
+
+def worst_k(energy, k):
+    """The k outages (indices into the outage list) of largest overload energy,
+    larger energy first and the lower index first among equal energies; NaN
+    entries never qualify.  Returns (indices, energies), padded with -1 / NaN."""
+    e = np.asarray(energy, dtype=np.float64)
+    ok = np.flatnonzero(~np.isnan(e))
+    order = ok[np.lexsort((ok, -e[ok]))][:k]
+    idx = np.full(k, -1, dtype=np.int64)
+    val = np.full(k, np.nan)
+    idx[: order.size] = order
+    val[: order.size] = e[order]
+    return idx, val
+
+
 def _pool(processes):
     """A spawn-started process pool whose workers run single-threaded BLAS
     (one solve per process; threaded BLAS in every worker oversubscribes the

@@ -312,3 +312,60 @@ def test_disconnection_kirchhoff_and_islanding(seed):
         n_br = sum(1 for c in g.outages if int(c) in bridges)
         assert r["n_islanded"] == n_br
     assert seen_open > 0
+
+
+# ------------------------------------------------------------- worst-k export
+def test_outage_energy_and_worst_k_three_bus():
+    """Per-outage overload energy and the worst-k selection on the triangle,
+    from the closed-form outage flows of the golden fixture."""
+    g, d = three_bus()
+    c = d["cases"]["base"]
+    E = dcflow.outage_energy(g, [-1])
+    np.testing.assert_allclose(E, c["outage_energy"], atol=1e-12)
+    idx, val = dcflow.worst_k(E, 2)
+    assert list(idx) == c["worst_2"]
+    idx, val = dcflow.worst_k(E, 5)
+    assert list(idx) == [1, 0, 2, -1, -1] and np.isnan(val[3:]).all()
+    # every outage of the disconnect-1->2 state islands or is the open branch
+    gd = _with_disc(g, [0, 1, 2], 2)
+    E2 = dcflow.outage_energy(gd, [-1, 1, -1])
+    assert np.isnan(E2).all()
+    assert list(dcflow.worst_k(E2, 2)[0]) == [-1, -1]
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_outage_energies_sum_like_the_definition(seed):
+    """Each N-1 case's energy equals its overloads summed over branches and
+    timesteps, recomputed here from networkx-independent re-solves of the
+    outage (the plain Laplacian solve with the branch removed)."""
+    g = small_grid(seed)
+    g = g.with_limits(0.6 * np.abs(dcflow.base_flows(g)).max(axis=0) + 0.05)
+    topo = random_topologies(g, 3, seed=seed)
+    for gen in topo:
+        E = dcflow.outage_energy(g, gen)
+        n_node, fr, to, p, _ = dcflow.post_split_graph(g, gen)
+        if not dcflow.is_connected_uf(n_node, fr, to):
+            assert np.isnan(E).all()
+            continue
+        L = np.zeros((n_node, n_node))
+        for oi, c in enumerate(g.outages):
+            if not dcflow.is_connected_uf(n_node, fr, to, skip=int(c)):
+                assert np.isnan(E[oi])
+                continue
+            L[:] = 0.0
+            for l in range(len(fr)):
+                if l == c:
+                    continue
+                a, b_ = fr[l], to[l]
+                L[a, a] += g.b[l]
+                L[b_, b_] += g.b[l]
+                L[a, b_] -= g.b[l]
+                L[b_, a] -= g.b[l]
+            keep = [i for i in range(n_node) if i != g.slack]
+            th = np.zeros((p.shape[0], n_node))
+            th[:, keep] = np.linalg.solve(L[np.ix_(keep, keep)], p[:, keep].T).T
+            F = g.b[None, :] * (th[:, fr] - th[:, to])
+            F[:, c] = 0.0
+            lim = g.limit[g.monitored]
+            ref = np.maximum(np.abs(F[:, g.monitored]) - lim[None, :], 0.0).sum()
+            assert E[oi] == pytest.approx(ref, rel=1e-9, abs=1e-12)
