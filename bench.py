@@ -496,6 +496,24 @@ def main():
     e2e_ms = max_over_ranks(e2e_ms, world, "cuda")
     e2e = job_throughput(B, world, args.steps, e2e_ms)
 
+    # worst-k N-1 export of the archive's elites, the per-epoch hand-over to AC
+    # validation (Sec. "AC-Validator", k = 20); timed on its own, outside the steps
+    _, gen_a, filled_a = A.export()
+    elites = torch.tensor(gen_a[filled_a.astype(bool)], dtype=torch.int32, device="cuda")
+    wk = None
+    if elites.shape[0] > 0:
+        g.worst_k(elites, k=20)
+        g.sync_status()
+        w0 = torch.cuda.Event(enable_timing=True)
+        w1 = torch.cuda.Event(enable_timing=True)
+        w0.record(stream)
+        g.worst_k(elites, k=20)
+        w1.record(stream)
+        torch.cuda.synchronize()
+        wk_ms = w0.elapsed_time(w1)
+        wk = {"topologies": int(elites.shape[0]), "k": 20, "ms": wk_ms,
+              "ms_per_topology": wk_ms / int(elites.shape[0])}
+
     if rank == 0:
         pk, pk_kind = peaks()
         props = torch.cuda.get_device_properties(local)
@@ -538,7 +556,8 @@ def main():
                           "unit": "(topology, t, monitored branch, outage) pairs/s"},
             "stage_ms_per_step": {"split_update": stage_ms[0] / max(ncalls, 1), "sweep": sweep_ms,
                                   "metrics": stage_ms[2] / max(ncalls, 1)},
-            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(B * g.k_max * 4),
+            "worst_k_export": wk,
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(B * g.genome_width * 4),
                     "d2h_bytes_per_step": int(B * 4)},
             "gpu_launches": (LAUNCHES_PER_STEP + (0 if prec == PREC_FP32 else 1)) * args.steps,
             "clocks": clk,

@@ -256,6 +256,23 @@ int tto_evaluate_batch_static(tto_grid* g, const int32_t* topo, int32_t B, const
                               int32_t* cell, uint8_t* island, float* metrics, float* fmax,
                               void* stream);
 
+/* tto_worst_k -- worst-k N-1 export for AC validation (Sec. "AC-Validator":
+ * the DC optimiser computes each N-1 case's overload energy and writes out the
+ * worst k).  For n topologies (device int32 [n][k_max + n_dslot]) over the
+ * selected timesteps (host, NULL = all): the split update, then per outage c
+ *   E_c = sum_t sum_l max(|F_lc[t]| - limit_l, 0)   (FP32, fixed summation order),
+ * and the k outages of largest E_c, larger first, the lower outage index first
+ * among equal energies.  outage_out device int32 [n][k]: indices into the
+ * grid's outage list, -1 where fewer than k qualify; energy_out device float
+ * [n][k] (NaN with -1).  An outage that islands the topology, or whose branch
+ * the topology opened, never qualifies (its all_energy entry is NaN); a
+ * topology that islands the grid yields -1 throughout.  all_energy (device
+ * float [n][n_outage], may be NULL) receives every E_c.  1 <= k <= 1024.
+ * Shares the evaluation workspace with the other calls on this grid.
+ * Asynchronous on stream; genome errors as for tto_evaluate_batch. */
+int tto_worst_k(tto_grid* g, const int32_t* topo, int32_t n, const int32_t* timesteps, int32_t n_t, int32_t k,
+                int32_t* outage_out, float* energy_out, float* all_energy, void* stream);
+
 /* Test hook for the timeout path (the paper has no counterpart): runs one
  * thread that waits, through the sweeps' own bounded-wait routine, on an
  * mbarrier that nothing completes, for at most `cycles` SM clock cycles

@@ -198,7 +198,8 @@ def descriptors(grid, genome, d_split, d_moved, d_disc=1):
     return ns, nm, cell
 
 
-def evaluate(grid, genome, timesteps=None, outages=None, d_split=8, d_moved=8, want_flows=False, d_disc=1):
+def evaluate(grid, genome, timesteps=None, outages=None, d_split=8, d_moved=8, want_flows=False, d_disc=1,
+             want_energy=False):
     """Evaluate one topology by brute force.
 
     ``outages`` optionally restricts the outage list (indices into
@@ -226,6 +227,7 @@ def evaluate(grid, genome, timesteps=None, outages=None, d_split=8, d_moved=8, w
     fmax = np.zeros_like(fprime)
     n_isl = 0
     per_outage = {} if want_flows else None
+    energy = np.full(grid.outages.size, np.nan) if want_energy else None
     for oi in out_idx:
         c = int(grid.outages[oi])
         if not live[c]:
@@ -238,6 +240,8 @@ def evaluate(grid, genome, timesteps=None, outages=None, d_split=8, d_moved=8, w
         F = solve_flows(n_node, fr, to, grid.b, p, grid.slack, keep=keep)[:, mon]
         if want_flows:
             per_outage[int(oi)] = F
+        if want_energy:
+            energy[oi] = float(np.maximum(np.abs(F) - lim[None, :], 0.0).sum())
         fmax = np.maximum(fmax, np.abs(F))
     over = np.maximum(fmax - lim[None, :], 0.0)
     lam_o = float(over.sum())
@@ -249,6 +253,8 @@ def evaluate(grid, genome, timesteps=None, outages=None, d_split=8, d_moved=8, w
                fitness=-(lam_o + maxload), lambda_f1=-(lam_o + 200.0 * lam_c0 + 50.0 * lam_c))
     if want_flows:
         res["per_outage"] = per_outage
+    if want_energy:
+        res["outage_energy"] = energy
     return res
 
 
@@ -258,14 +264,10 @@ def outage_energy(grid, genome, timesteps=None):
     k): E_c = sum over timesteps and monitored branches of max(|F_l^(c)| -
     fbar_l, 0).  NaN for an outage that islands the topology or whose branch it
     already opened; all NaN when the topology itself islands the grid."""
-    r = evaluate(grid, genome, timesteps=timesteps, want_flows=True)
-    E = np.full(grid.outages.size, np.nan)
+    r = evaluate(grid, genome, timesteps=timesteps, want_energy=True)
     if r["island_base"]:
-        return E
-    lim = grid.limit[grid.monitored.astype(np.int64)]
-    for oi, F in r["per_outage"].items():
-        E[oi] = float(np.maximum(np.abs(F) - lim[None, :], 0.0).sum())
-    return E
+        return np.full(grid.outages.size, np.nan)
+    return r["outage_energy"]
 
 
 def worst_k(energy, k):

@@ -102,6 +102,26 @@ class Grid:
         out["_topo"] = topo
         return out
 
+    def worst_k(self, topo, k=20, timesteps=None, all_energy=False, stream=None):
+        """Worst-k N-1 export: per topology the k outages (indices into the
+        outage list, -1 = none) of largest overload energy and those energies;
+        with all_energy, also every outage's energy [n][n_outage] (NaN where the
+        outage islands the topology or its branch is open)."""
+        torch = _torch()
+        n = int(topo.shape[0])
+        if topo.dtype != torch.int32 or not topo.is_cuda or topo.shape[1] != self.genome_width:
+            raise TTOError(_lib.TTO_E_ARG, "topo must be a CUDA int32 tensor [n][k_max + n_dslot]")
+        topo = topo.contiguous()
+        dev = topo.device
+        idx = torch.empty(n, k, dtype=torch.int32, device=dev)
+        val = torch.empty(n, k, dtype=torch.float32, device=dev)
+        allE = torch.empty(n, self.n_outage, dtype=torch.float32, device=dev) if all_energy else None
+        _lib.tto_worst_k(self._h, topo, n, timesteps, k, idx, val, allE, _stream(stream))
+        out = {"outage": idx, "energy": val}
+        if allE is not None:
+            out["all_energy"] = allE
+        return out
+
     def sync_status(self, stream=None):
         _lib.tto_grid_sync_status(self._h, _stream(stream))
 

@@ -102,6 +102,7 @@ _SIGS = {
     "tto_archive_create": ([_vp, C.c_int32, C.c_int32, C.POINTER(_vp)], C.c_int),
     "tto_archive_create_ex": ([_vp, C.c_int32, C.c_int32, C.c_int32, C.POINTER(_vp)], C.c_int),
     "tto_grid_disc_info": ([_vp, _i32p, _i32p], C.c_int),
+    "tto_worst_k": ([_vp, _vp, C.c_int32, _i32p, C.c_int32, C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
     "tto_archive_destroy": ([_vp], C.c_int),
     "tto_archive_export": ([_vp, _vp, _vp, _vp], C.c_int),
     "tto_archive_import": ([_vp, _vp, _vp, _vp], C.c_int),
@@ -218,6 +219,17 @@ def tto_grid_info(h):
     check(lib().tto_grid_info(h, *[C.byref(x) for x in v]))
     keys = ["n_branch", "n_monitored", "n_outage", "n_time", "k_max", "n_action"]
     return {k: x.value for k, x in zip(keys, v)}
+
+
+def tto_worst_k(h, topo, n, timesteps, k, outage_out, energy_out, all_energy, stream):
+    ts = None
+    n_t = 0
+    if timesteps is not None:
+        ts_arr = np.ascontiguousarray(timesteps, dtype=np.int32)
+        ts = _ptr(ts_arr, C.c_int32)
+        n_t = int(ts_arr.size)
+    return check(lib().tto_worst_k(h, _dp(topo), int(n), ts, n_t, int(k), _dp(outage_out), _dp(energy_out),
+                                   _dp(all_energy), _vp(stream)))
 
 
 def tto_grid_disc_info(h):

@@ -473,7 +473,7 @@ static int padded_K(int k) { return k <= 2 ? 2 : (k <= 4 ? 4 : 8); }
 
 int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, int n_t,
                   const tto_eval_opts* o, float* fitness, int32_t* desc, int32_t* cell,
-                  uint8_t* island, float* metrics, float* fmax, cudaStream_t s) {
+                  uint8_t* island, float* metrics, float* fmax, cudaStream_t s, EvalArgs* split_only) {
   if (!g || !o) return set_error(TTO_E_ARG, "null argument");
   if (B < 0) return set_error(TTO_E_ARG, "negative batch");
   if (B > 0 && (!topo || !fitness)) return set_error(TTO_E_ARG, "null topology or fitness buffer");
@@ -563,11 +563,15 @@ int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, 
   cudaEvent_t* ev = nullptr;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   TTO_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
-  if (g->prof_on && g->prof_n < kProfileCalls && cap == cudaStreamCaptureStatusNone)
+  if (g->prof_on && !split_only && g->prof_n < kProfileCalls && cap == cudaStreamCaptureStatusNone)
     ev = &g->prof_ev[4 * g->prof_n++];
   if (ev) TTO_CUDA_TRY(cudaEventRecord(ev[0], s));
   split_update_kernel<<<B, 256, 0, s>>>(a);
   TTO_CUDA_TRY(cudaGetLastError());
+  if (split_only) {
+    *split_only = a;
+    return TTO_OK;
+  }
   if (ev) TTO_CUDA_TRY(cudaEventRecord(ev[1], s));
   if (a.precision != TTO_PREC_FP32) {
     rc = ensure_fragment_N(g, s);

@@ -115,9 +115,13 @@ int padded_T(int n_t);  // timesteps rounded up to a compiled sweep width (-1 if
 void free_workspace(tto_grid* g);
 // Drop recorded multi-grid evaluation graphs that use this grid.
 void forget_grid_graphs(const tto_grid* g);
+struct EvalArgs;
+// Exact evaluation; with split_only set, stop after the split update (U, V,
+// f', g in the workspace) and return the launch arguments there.
 int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, int n_t,
                   const tto_eval_opts* o, float* fitness, int32_t* desc, int32_t* cell,
-                  uint8_t* island, float* metrics, float* fmax, cudaStream_t s);
+                  uint8_t* island, float* metrics, float* fmax, cudaStream_t s,
+                  EvalArgs* split_only = nullptr);
 // MapElites building blocks shared by the plain and the surrogate-screened step.
 int propose_impl(tto_archive* ar, uint64_t seed, uint64_t it, int B, const tto_mut_params* mp,
                  int32_t* out, cudaStream_t s);

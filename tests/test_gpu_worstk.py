@@ -1,0 +1,100 @@
+"""Worst-k N-1 export (Sec. "AC-Validator") on the GPU against the oracle:
+every outage's overload energy within the loading tolerance, the same
+islanded/opened exclusions, and a worst-k list that the oracle's energies
+confirm up to near-ties."""
+import numpy as np
+import pytest
+
+from oracle import dcflow
+from synth import config_grid, limits_from_flows, random_topologies
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+
+
+def _grid(name, n_tight, seed=0, **kw):
+    sg = config_grid(name, seed=seed, **kw)
+    return sg.with_limits(limits_from_flows(dcflow.base_flows(sg)[0], n_tight, seed=seed))
+
+
+def _energies(sg, topo, idx):
+    res = dcflow.evaluate_many(sg, [topo[i] for i in idx], processes=min(parity.n_procs(), len(idx)),
+                               want_energy=True)
+    return [np.full(sg.outages.size, np.nan) if r["island_base"] else r["outage_energy"] for r in res]
+
+
+def _check(sg, out, idx, refs, k):
+    lim = sg.limit[sg.monitored.astype(np.int64)]
+    bound0 = parity.TOL_FP32 * float(lim.sum()) * sg.T
+    for row, (i, E) in enumerate(zip(idx, refs)):
+        got = out["all_energy"][i].astype(np.float64)
+        assert np.array_equal(np.isnan(got), np.isnan(E)), f"exclusions differ at {i}"
+        ok = ~np.isnan(E)
+        bound = bound0 + 1e-5 * np.abs(E[ok])
+        assert np.all(np.abs(got[ok] - E[ok]) <= bound), (i, float(np.max(np.abs(got[ok] - E[ok]))))
+        sel = out["outage"][i]
+        val = out["energy"][i]
+        n_ok = int(ok.sum())
+        assert int((sel >= 0).sum()) == min(k, n_ok)
+        assert np.all(sel[min(k, n_ok):] == -1) and np.isnan(val[min(k, n_ok):]).all()
+        ref_idx, ref_val = dcflow.worst_k(E, k)
+        if n_ok == 0:
+            continue
+        kth = np.nanmin(ref_val)
+        for r_, c in enumerate(sel[: min(k, n_ok)]):
+            assert E[c] >= kth - 2 * (bound0 + 1e-5 * abs(kth)), (i, r_, c, E[c], kth)
+            assert val[r_] == np.float32(got[c])
+        # the GPU's list is in its own energy order
+        v = val[: min(k, n_ok)]
+        assert np.all(np.diff(v) <= 0)
+
+
+def test_worst_k_tto30_with_disconnections():
+    from paper_2605_10128_b300 import Grid
+    sg = _grid("tto30", 5, n_disc=12, n_dslot=2)
+    g = Grid(sg)
+    topo = random_topologies(sg, 48, seed=6)
+    topo[0] = -1  # the unchanged topology
+    out = g.worst_k(torch.tensor(topo, dtype=torch.int32, device="cuda"), k=20, all_energy=True)
+    g.sync_status()
+    out = {k_: v.cpu().numpy() for k_, v in out.items()}
+    idx = list(range(len(topo)))
+    refs = _energies(sg, topo, idx)
+    assert any(np.isnan(E).all() for E in refs)  # some topologies island the grid
+    _check(sg, out, idx, refs, 20)
+
+
+def test_worst_k_tto2k_sampled():
+    from paper_2605_10128_b300 import Grid
+    sg = _grid("tto2k", 30)
+    g = Grid(sg)
+    topo = random_topologies(sg, 64, seed=12)
+    out = g.worst_k(torch.tensor(topo, dtype=torch.int32, device="cuda"), k=20, all_energy=True)
+    g.sync_status()
+    out = {k_: v.cpu().numpy() for k_, v in out.items()}
+    idx = [0, 1, 2]
+    _check(sg, out, idx, _energies(sg, topo, idx), 20)
+
+
+def test_worst_k_validation_and_large_k():
+    from paper_2605_10128_b300 import Grid, TTOError
+    sg = _grid("tto30", 5)
+    g = Grid(sg)
+    t = torch.tensor(random_topologies(sg, 4, seed=1), dtype=torch.int32, device="cuda")
+    with pytest.raises(TTOError):
+        g.worst_k(t, k=0)
+    out = g.worst_k(t, k=200, all_energy=True)  # more than the 41 outages
+    g.sync_status()
+    sel = out["outage"].cpu().numpy()
+    E = out["all_energy"].cpu().numpy()
+    for i in range(4):
+        n_ok = int((~np.isnan(E[i])).sum())
+        assert sorted(sel[i][:n_ok].tolist()) == sorted(np.flatnonzero(~np.isnan(E[i])).tolist())
+        assert np.all(sel[i][n_ok:] == -1)
