@@ -399,6 +399,8 @@ def main():
     ap.add_argument("--ddisc", type=int, default=3, help="archive extent over opened branches when --dslots > 0")
     ap.add_argument("--crossover", action="store_true", help="Algorithm 3's mutation/crossover split of each batch")
     ap.add_argument("--p-c1", type=float, default=0.5, help="crossover bias toward the first parent")
+    ap.add_argument("--epoch", type=int, default=0,
+                    help="iterations per epoch: export the archive and its worst-20 lists after each (0: never)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -461,10 +463,18 @@ def main():
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
+    n_export = 0
     for it in range(args.warmup, args.warmup + args.steps):
         A.step(seed, it, B, mutation=mut, precision=prec)
+        if args.epoch and (it - args.warmup + 1) % args.epoch == 0:
+            # end-of-epoch hand-over: archive snapshot + worst-20 N-1 cases of
+            # every cell, copied to the host while the next epoch runs
+            A.epoch_wait()
+            A.epoch_export(k=20, stream=stream)
+            n_export += 1
     t1.record(stream)
     barrier()
+    A.epoch_wait()
     clk = clocks.stop()
     g.profile(False)
     elapsed_ms = t0.elapsed_time(t1)
@@ -557,6 +567,8 @@ def main():
             "stage_ms_per_step": {"split_update": stage_ms[0] / max(ncalls, 1), "sweep": sweep_ms,
                                   "metrics": stage_ms[2] / max(ncalls, 1)},
             "worst_k_export": wk,
+            "epoch_export": ({"every_steps": args.epoch, "exports_in_timed_region": n_export, "k": 20,
+                              "cells": A.cells} if args.epoch else None),
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(B * g.genome_width * 4),
                     "d2h_bytes_per_step": int(B * 4)},
             "gpu_launches": (LAUNCHES_PER_STEP + (0 if prec == PREC_FP32 else 1)) * args.steps,

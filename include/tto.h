@@ -330,6 +330,23 @@ int tto_mapelites_step(tto_archive* a, uint64_t seed, uint64_t iteration, int32_
                        const tto_mut_params* mp, const tto_eval_opts* opts, int32_t* topo_out,
                        float* fitness_out, void* stream);
 
+/* tto_epoch_export -- the end-of-epoch hand-over (Sec. "High-level Genetic
+ * Algorithm loop": iterations are grouped into epochs and results leave the
+ * GPU only at an epoch's end).  Queued on stream after the epoch's
+ * iterations: a device snapshot of the archive and, for k > 0, the worst-k N-1
+ * cases (tto_worst_k) of every filled cell's genome (an empty cell's list is
+ * -1 / NaN); the snapshot is then copied on
+ * an internal stream to the host buffers fitness [cells], genome
+ * [cells][k_max + n_dslot], filled [cells], worst_outage / worst_energy
+ * [cells][k] (pinned memory keeps the copy asynchronous).  Iterations queued
+ * on stream afterwards overlap the copy.  The host buffers are complete after
+ * tto_epoch_export_wait; a later export orders itself after the previous
+ * copy.  0 <= k <= 1024.  Uses the grid's evaluation workspace. */
+int tto_epoch_export(tto_archive* a, int32_t k, float* fitness, int32_t* genome, uint8_t* filled,
+                     int32_t* worst_outage, float* worst_energy, void* stream);
+/* Block until the last tto_epoch_export's host buffers are complete. */
+int tto_epoch_export_wait(tto_archive* a);
+
 /* The 4x32-bit Philox words of counter block `block` of candidate `cand` in
  * `iteration` under `seed`, written to device uint32 [n][4] for blocks
  * block .. block+n-1 (exposes the generator that drives the mutation). */

@@ -175,6 +175,27 @@ class Archive:
     def load(self, fitness, genome, filled):
         _lib.tto_archive_import(self._h, fitness, genome, filled)
 
+    def epoch_export(self, k=20, stream=None):
+        """Queue the end-of-epoch hand-over: a snapshot of the archive and the
+        worst-k N-1 cases of every cell, copied to pinned host tensors while
+        later work on the stream runs.  Returns the host tensors (fitness,
+        genome, filled, worst_outage, worst_energy), complete after
+        epoch_wait()."""
+        torch = _torch()
+        gw = self.grid.genome_width
+        out = {"fitness": torch.empty(self.cells, dtype=torch.float32).pin_memory(),
+               "genome": torch.empty(self.cells, gw, dtype=torch.int32).pin_memory(),
+               "filled": torch.empty(self.cells, dtype=torch.uint8).pin_memory(),
+               "worst_outage": torch.empty(self.cells, max(k, 1), dtype=torch.int32).pin_memory(),
+               "worst_energy": torch.empty(self.cells, max(k, 1), dtype=torch.float32).pin_memory()}
+        _lib.tto_epoch_export(self._h, k, out["fitness"], out["genome"], out["filled"], out["worst_outage"],
+                              out["worst_energy"], _stream(stream))
+        self._pending_export = out  # keep the buffers alive until the copy completes
+        return out
+
+    def epoch_wait(self):
+        _lib.tto_epoch_export_wait(self._h)
+
     def insert(self, topo, fitness, cell, stream=None):
         _lib.tto_archive_insert(self._h, topo, int(topo.shape[0]), fitness, cell, _stream(stream))
 

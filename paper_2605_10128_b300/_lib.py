@@ -103,6 +103,8 @@ _SIGS = {
     "tto_archive_create_ex": ([_vp, C.c_int32, C.c_int32, C.c_int32, C.POINTER(_vp)], C.c_int),
     "tto_grid_disc_info": ([_vp, _i32p, _i32p], C.c_int),
     "tto_worst_k": ([_vp, _vp, C.c_int32, _i32p, C.c_int32, C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
+    "tto_epoch_export": ([_vp, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp], C.c_int),
+    "tto_epoch_export_wait": ([_vp], C.c_int),
     "tto_archive_destroy": ([_vp], C.c_int),
     "tto_archive_export": ([_vp, _vp, _vp, _vp], C.c_int),
     "tto_archive_import": ([_vp, _vp, _vp, _vp], C.c_int),
@@ -230,6 +232,15 @@ def tto_worst_k(h, topo, n, timesteps, k, outage_out, energy_out, all_energy, st
         n_t = int(ts_arr.size)
     return check(lib().tto_worst_k(h, _dp(topo), int(n), ts, n_t, int(k), _dp(outage_out), _dp(energy_out),
                                    _dp(all_energy), _vp(stream)))
+
+
+def tto_epoch_export(a, k, fit, gen, filled, widx, wval, stream):
+    return check(lib().tto_epoch_export(a, int(k), _dp(fit), _dp(gen), _dp(filled), _dp(widx), _dp(wval),
+                                        _vp(stream)))
+
+
+def tto_epoch_export_wait(a):
+    return check(lib().tto_epoch_export_wait(a))
 
 
 def tto_grid_disc_info(h):

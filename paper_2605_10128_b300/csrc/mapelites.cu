@@ -502,6 +502,7 @@ int tto_archive_create_ex(tto_grid* g, int32_t d_split, int32_t d_moved, int32_t
 int tto_archive_destroy(tto_archive* a) {
   if (!a) return TTO_OK;
   cudaSetDevice(a->g->device);
+  free_epoch(a);
   void* ptrs[] = {a->d_fit, a->d_genome, a->d_filled, a->d_key, a->d_filled_list};
   for (void* p : ptrs)
     if (p) cudaFree(p);

@@ -99,8 +99,13 @@ struct tto_grid {
   std::vector<cudaEvent_t> prof_ev;  // 4 per recorded call
 };
 
+namespace tto {
+struct EpochSnap;  // epoch hand-over snapshot (epoch.cu)
+}
+
 struct tto_archive {
   tto_grid* g = nullptr;
+  tto::EpochSnap* epoch = nullptr;  // created by the first tto_epoch_export
   int d_split = 0, d_moved = 0, d_disc = 1, cells = 0;
   float* d_fit = nullptr;         // [cells]
   int32_t* d_genome = nullptr;    // [cells][gw]
@@ -127,4 +132,9 @@ int propose_impl(tto_archive* ar, uint64_t seed, uint64_t it, int B, const tto_m
                  int32_t* out, cudaStream_t s);
 int insert_impl(tto_archive* ar, const int32_t* topo, int B, const float* fit, const int32_t* cell,
                 cudaStream_t s);
+void free_epoch(tto_archive* a);  // waits for a pending epoch copy, frees the snapshot
+// tto_worst_k with an optional device mask: topologies with use[b] == 0 are
+// skipped (energies NaN, lists -1).
+int worst_k_impl(tto_grid* g, const int32_t* topo, int32_t n, const int32_t* timesteps, int32_t n_t, int32_t k,
+                 int32_t* outage_out, float* energy_out, float* all_energy, const uint8_t* use, cudaStream_t s);
 }  // namespace tto

@@ -32,13 +32,22 @@ constexpr int kEThreads = 128;  // outage columns per CTA
 constexpr int kERows = 32;     // monitored rows staged per tile
 
 template <int TT>
-__global__ void __launch_bounds__(kEThreads) outage_energy_kernel(EvalArgs a, float* energy) {
+__global__ void __launch_bounds__(kEThreads) outage_energy_kernel(EvalArgs a, float* energy, const uint8_t* use) {
   __shared__ __align__(16) float sU[kEG][kERows][8];
   __shared__ float sF[kEG][kERows][TT];
   __shared__ float sL[kERows];
   const int tid = threadIdx.x;
   const int c = blockIdx.x * kEThreads + tid;
   const int b0 = blockIdx.y * kEG;
+  const float qnan = __int_as_float(0x7fc00000);
+  if (use) {  // CTA-uniform: a group of topologies that are all unused writes NaN and leaves
+    bool any = false;
+    for (int gi = 0; gi < kEG && b0 + gi < a.B; ++gi) any = any || use[b0 + gi];
+    if (!any) {
+      for (int gi = 0; gi < kEG && b0 + gi < a.B && c < a.O; ++gi) energy[(size_t)(b0 + gi) * a.O + c] = qnan;
+      return;
+    }
+  }
   const int Ep = a.E_mon_pad, Op = a.O_pad;
   const int cc = c < Op ? c : Op - 1;  // idle columns still join the staging
   float v[kEG][8], g[kEG][TT], e[kEG];
@@ -81,11 +90,10 @@ __global__ void __launch_bounds__(kEThreads) outage_energy_kernel(EvalArgs a, fl
     }
   }
   if (c >= a.O) return;
-  const float qnan = __int_as_float(0x7fc00000);
 #pragma unroll
   for (int gi = 0; gi < kEG; ++gi) {
     const int b = b0 + gi;
-    if (b < a.B) energy[(size_t)b * a.O + c] = isnan(g[gi][0]) ? qnan : e[gi];
+    if (b < a.B) energy[(size_t)b * a.O + c] = (isnan(g[gi][0]) || (use && !use[b])) ? qnan : e[gi];
   }
 }
 
@@ -157,14 +165,19 @@ __global__ void __launch_bounds__(256) worst_k_kernel(const float* energy, int O
 }
 
 template <int TT>
-int launch_energy(const EvalArgs& a, float* energy, cudaStream_t s) {
+int launch_energy(const EvalArgs& a, float* energy, const uint8_t* use, cudaStream_t s) {
   const dim3 grid((unsigned)((a.O_pad + kEThreads - 1) / kEThreads), (unsigned)((a.B + kEG - 1) / kEG));
-  outage_energy_kernel<TT><<<grid, kEThreads, 0, s>>>(a, energy);
+  outage_energy_kernel<TT><<<grid, kEThreads, 0, s>>>(a, energy, use);
   TTO_CUDA_TRY(cudaGetLastError());
   return TTO_OK;
 }
 
 }  // namespace
+
+// use (device, may be NULL): topologies b with use[b] == 0 are skipped (their
+// energies NaN, their lists -1), as the epoch export does for empty cells.
+int worst_k_impl(tto_grid* g, const int32_t* topo, int32_t n, const int32_t* timesteps, int32_t n_t, int32_t k,
+                 int32_t* outage_out, float* energy_out, float* all_energy, const uint8_t* use, cudaStream_t s);
 
 }  // namespace tto
 
@@ -172,11 +185,17 @@ using namespace tto;
 
 extern "C" int tto_worst_k(tto_grid* g, const int32_t* topo, int32_t n, const int32_t* timesteps, int32_t n_t,
                            int32_t k, int32_t* outage_out, float* energy_out, float* all_energy, void* stream) {
+  return worst_k_impl(g, topo, n, timesteps, n_t, k, outage_out, energy_out, all_energy, nullptr,
+                      (cudaStream_t)stream);
+}
+
+int tto::worst_k_impl(tto_grid* g, const int32_t* topo, int32_t n, const int32_t* timesteps, int32_t n_t,
+                      int32_t k, int32_t* outage_out, float* energy_out, float* all_energy, const uint8_t* use,
+                      cudaStream_t s) {
   if (!g) return set_error(TTO_E_ARG, "null grid");
   if (n < 0 || k < 1 || k > 1024) return set_error(TTO_E_ARG, "need n >= 0 and 1 <= k <= 1024");
   if (n > 0 && (!topo || !outage_out || !energy_out)) return set_error(TTO_E_ARG, "null buffer");
   if (n == 0) return TTO_OK;
-  cudaStream_t s = (cudaStream_t)stream;
   TTO_CUDA_TRY(cudaSetDevice(g->device));
   const int TT = padded_T(timesteps ? n_t : g->T);
   if (TT < 0) return set_error(TTO_E_ARG, "at most %d timesteps", TTO_MAX_T);
@@ -194,13 +213,13 @@ extern "C" int tto_worst_k(tto_grid* g, const int32_t* topo, int32_t n, const in
   // staging buffer (B x O_pad x TT floats), which the FP32 split update leaves unused
   float* energy = all_energy ? all_energy : g->ws.gq;
   switch (a.TT) {
-    case 1: rc = launch_energy<1>(a, energy, s); break;
-    case 2: rc = launch_energy<2>(a, energy, s); break;
-    case 4: rc = launch_energy<4>(a, energy, s); break;
-    case 8: rc = launch_energy<8>(a, energy, s); break;
-    case 16: rc = launch_energy<16>(a, energy, s); break;
-    case 24: rc = launch_energy<24>(a, energy, s); break;
-    case 32: rc = launch_energy<32>(a, energy, s); break;
+    case 1: rc = launch_energy<1>(a, energy, use, s); break;
+    case 2: rc = launch_energy<2>(a, energy, use, s); break;
+    case 4: rc = launch_energy<4>(a, energy, use, s); break;
+    case 8: rc = launch_energy<8>(a, energy, use, s); break;
+    case 16: rc = launch_energy<16>(a, energy, use, s); break;
+    case 24: rc = launch_energy<24>(a, energy, use, s); break;
+    case 32: rc = launch_energy<32>(a, energy, use, s); break;
     default: return set_error(TTO_E_ARG, "unsupported timestep count %d", a.TT);
   }
   if (rc) return rc;

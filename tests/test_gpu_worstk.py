@@ -98,3 +98,39 @@ def test_worst_k_validation_and_large_k():
         n_ok = int((~np.isnan(E[i])).sum())
         assert sorted(sel[i][:n_ok].tolist()) == sorted(np.flatnonzero(~np.isnan(E[i])).tolist())
         assert np.all(sel[i][n_ok:] == -1)
+
+
+def test_epoch_export_snapshot_and_overlap():
+    """The end-of-epoch hand-over: the host copy equals the archive at the
+    export point although later iterations were queued behind it, its worst-k
+    lists equal tto_worst_k on the exported genomes, and a second export
+    orders itself after the first copy."""
+    from paper_2605_10128_b300 import Grid, Archive
+    sg = _grid("tto2k", 30)  # large enough that the archive keeps improving
+    g = Grid(sg)
+    A = Archive(g, 8, 8)
+    for it in range(3):
+        A.step(3, it, 512)
+    torch.cuda.synchronize()
+    ref_f, ref_g, ref_fl = A.export()
+    out = A.epoch_export(k=10)
+    for it in range(3, 6):
+        A.step(3, it, 512)
+    A.epoch_wait()
+    g.sync_status()
+    np.testing.assert_array_equal(out["fitness"].numpy(), ref_f)
+    np.testing.assert_array_equal(out["genome"].numpy(), ref_g)
+    np.testing.assert_array_equal(out["filled"].numpy(), ref_fl)
+    wk = g.worst_k(torch.tensor(ref_g, dtype=torch.int32, device="cuda"), k=10)
+    full = ref_fl.astype(bool)
+    assert full.sum() > 5
+    np.testing.assert_array_equal(out["worst_outage"].numpy()[full], wk["outage"].cpu().numpy()[full])
+    np.testing.assert_array_equal(out["worst_energy"].numpy()[full], wk["energy"].cpu().numpy()[full])
+    assert np.all(out["worst_outage"].numpy()[~full] == -1)  # empty cells are skipped
+    assert np.isnan(out["worst_energy"].numpy()[~full]).all()
+    f_now, g_now, fl_now = A.export()
+    assert not np.array_equal(f_now, ref_f)  # the later iterations moved on
+    out2 = A.epoch_export(k=10)
+    A.epoch_wait()
+    np.testing.assert_array_equal(out2["fitness"].numpy(), f_now)
+    np.testing.assert_array_equal(out2["genome"].numpy(), g_now)
