@@ -145,10 +145,11 @@ def post_split_graph(grid, genome):
     return n_node, fr, to, p, slots
 
 
-def solve_flows(n_node, fr, to, b, p, slack, skip=-1, keep=None):
+def solve_flows(n_node, fr, to, b, p, slack, skip=-1, keep=None, pin=()):
     """DC loadflow: branch flows [T][E] for injections p [T][n_node]; branch
     ``skip`` and the branches outside ``keep`` are out of service (flow 0).  The
-    slack angle is fixed at 0 and the slack absorbs any imbalance."""
+    slack angle is fixed at 0 and the slack absorbs any imbalance.  Nodes in
+    ``pin`` (isolated, without injection) get angle 0."""
     E = len(fr)
     keep = np.ones(E, dtype=bool) if keep is None else np.array(keep, dtype=bool)
     if skip >= 0:
@@ -157,7 +158,10 @@ def solve_flows(n_node, fr, to, b, p, slack, skip=-1, keep=None):
     rows = np.concatenate([f, t, f, t])
     cols = np.concatenate([f, t, t, f])
     vals = np.concatenate([w, w, -w, -w])
-    L = sp.coo_matrix((vals, (rows, cols)), shape=(n_node, n_node)).tocsc()
+    L = sp.coo_matrix((vals, (rows, cols)), shape=(n_node, n_node)).tolil()
+    for v in pin:
+        L[v, v] = L[v, v] + 1.0
+    L = L.tocsc()
     idx = np.array([i for i in range(n_node) if i != slack])
     Lr = L[idx][:, idx]
     rhs = p[:, idx].T
@@ -256,6 +260,67 @@ def evaluate(grid, genome, timesteps=None, outages=None, d_split=8, d_moved=8, w
     if want_energy:
         res["outage_energy"] = energy
     return res
+
+
+def busbar_nodes(grid, genome):
+    """The busbar outage set O_b of a topology (reading): every splittable
+    station's node, and for a split station both its nodes (busbar A keeps the
+    station bus, busbar B is the new node).  Returns (node, station, side)."""
+    _, _, _, _, slots = post_split_graph(grid, genome)
+    split_node = {s: grid.n_bus + j for j, (s, _, _) in enumerate(slots)}
+    out = []
+    for s in range(grid.n_station):
+        out.append((int(grid.station_bus[s]), s, 0))
+        if s in split_node:
+            out.append((split_node[s], s, 1))
+    return out
+
+
+def busbar_outages(grid, genome, timesteps=None):
+    """Busbar outages of one topology by brute force (Sec. "Fitness function
+    heuristics": lambda_b = sum_e Pi(max_b |f_e^(b)| - fbar_e)).  A busbar
+    outage takes its node out of service: every branch at the node opens and
+    its injection is lost (the slack balances).  When the rest of the grid
+    falls apart the outage islands: it is skipped and counted.  Returns bmax
+    [T][E_mon] (max over busbar outages of |flow|), the islanding count and
+    lambda_b (summed over timesteps like lambda_o); None for a topology that
+    islands the grid."""
+    tsel = np.arange(grid.T) if timesteps is None else np.asarray(timesteps)
+    n_node, fr, to, p, _ = post_split_graph(grid, genome)
+    opened = open_branches(grid, genome)
+    live = np.ones(len(fr), dtype=bool)
+    live[opened] = False
+    p = p[tsel]
+    if not _is_connected_cs(n_node, fr, to, live):
+        return None
+    mon = grid.monitored.astype(np.int64)
+    lim = grid.limit[mon]
+    bmax = np.zeros((len(tsel), mon.size))
+    n_isl = 0
+    for v, _, _ in busbar_nodes(grid, genome):
+        keep = live & (fr != v) & (to != v)
+        g = sp.coo_matrix((np.ones(int(keep.sum())), (fr[keep], to[keep])), shape=(n_node, n_node))
+        _, lab = csg.connected_components(g, directed=False)
+        rest = np.delete(lab, v)
+        if np.any(rest != rest[0]):
+            n_isl += 1
+            continue
+        pb = p.copy()
+        pb[:, v] = 0.0
+        F = solve_flows(n_node, fr, to, grid.b, pb, grid.slack, keep=keep, pin=(v,))
+        bmax = np.maximum(bmax, np.abs(F[:, mon]))
+    return dict(bmax=bmax, n_islanded_busbar=n_isl,
+                lambda_b=float(np.maximum(bmax - lim[None, :], 0.0).sum()))
+
+
+def lambda_f2(res, busbar, lambda_b_pre):
+    """lambda_f2 = -(lambda_o + 200 lambda_c0 + 50 lambda_c + Pi(lambda_b -
+    lambda_b^pre)) (Sec. "High-level Genetic Algorithm loop"); -inf for a
+    topology that islands the grid."""
+    if res["island_base"]:
+        return -np.inf
+    return -(res["lambda_o"] + 200.0 * res["lambda_c0"] + 50.0 * res["lambda_c"]
+             + max(busbar["lambda_b"] - lambda_b_pre, 0.0))
 
 
 def outage_energy(grid, genome, timesteps=None):

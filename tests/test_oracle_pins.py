@@ -369,3 +369,51 @@ def test_outage_energies_sum_like_the_definition(seed):
             lim = g.limit[g.monitored]
             ref = np.maximum(np.abs(F[:, g.monitored]) - lim[None, :], 0.0).sum()
             assert E[oi] == pytest.approx(ref, rel=1e-9, abs=1e-12)
+
+
+# ------------------------------------------------------------- busbar outages
+def test_busbar_outages_three_bus():
+    g, d = three_bus()
+    c = d["cases"]["base"]
+    r = dcflow.busbar_outages(g, [-1])
+    np.testing.assert_allclose(r["bmax"][0], c["busbar_bmax"], atol=1e-12)
+    assert r["lambda_b"] == pytest.approx(c["busbar_lambda_b"], abs=1e-12) and r["n_islanded_busbar"] == 0
+    c = d["cases"]["split_branch_and_injection"]
+    a = action_of(g, 0, c.get("mask", 6))
+    r = dcflow.busbar_outages(g, [a])
+    np.testing.assert_allclose(r["bmax"][0], c["busbar_bmax"], atol=1e-12)
+    assert r["lambda_b"] == pytest.approx(c["busbar_lambda_b"], abs=1e-12)
+    assert r["n_islanded_busbar"] == c["busbar_n_islanded"]
+    assert [n for n, _, _ in dcflow.busbar_nodes(g, [a])] == [1, 3]
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_busbar_outages_kirchhoff_and_articulation_points(seed):
+    """Every busbar outage state obeys KCL and KVL with its node out of
+    service, and a busbar outage islands exactly when networkx calls its node
+    an articulation point of the topology's graph."""
+    g = small_grid(seed)
+    g = g.with_limits(np.ones(g.n_branch))
+    topo = random_topologies(g, 5, seed=seed)
+    for gen in topo:
+        n_node, fr, to, p, _ = dcflow.post_split_graph(g, gen)
+        if not dcflow.is_connected_uf(n_node, fr, to):
+            assert dcflow.busbar_outages(g, gen) is None
+            continue
+        r = dcflow.busbar_outages(g, gen)
+        G = nx.MultiGraph()
+        G.add_nodes_from(range(n_node))
+        for l in range(len(fr)):
+            G.add_edge(int(fr[l]), int(to[l]), key=l)
+        art = set(nx.articulation_points(nx.Graph(G)))
+        nodes = dcflow.busbar_nodes(g, gen)
+        assert r["n_islanded_busbar"] == sum(1 for v, _, _ in nodes if v in art)
+        for v, _, _ in nodes:
+            if v in art:
+                continue
+            keep = (fr != v) & (to != v)
+            pb = p.copy()
+            pb[:, v] = 0.0
+            F = dcflow.solve_flows(n_node, fr, to, g.b, pb, g.slack, keep=keep, pin=(v,))
+            assert np.all(F[:, ~keep] == 0.0)
+            _kcl_kvl(n_node, fr, to, g.b, pb, g.slack, F, opened=list(np.flatnonzero(~keep)))
