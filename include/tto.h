@@ -50,6 +50,8 @@ extern "C" {
 
 #define TTO_FIT_WORKLOAD 0 /* fitness = -(lambda_o + max loading) */
 #define TTO_FIT_F1 1       /* fitness = lambda_f1 = -(lambda_o + 200 lambda_c0 + 50 lambda_c) */
+#define TTO_FIT_F2 2       /* fitness = lambda_f2 = lambda_f1 - Pi(lambda_b - lambda_b_pre): busbar outages too
+                              (call tto_grid_busbar_reference first, with the same timesteps) */
 
 typedef struct tto_grid tto_grid;
 typedef struct tto_archive tto_archive;
@@ -255,6 +257,27 @@ int tto_evaluate_batch_static(tto_grid* g, const int32_t* topo, int32_t B, const
                               int32_t n_t, const tto_eval_opts* opts, float* fitness, int32_t* desc,
                               int32_t* cell, uint8_t* island, float* metrics, float* fmax,
                               void* stream);
+
+/* tto_evaluate_busbar -- busbar outages (Sec. "Fitness function heuristics":
+ * lambda_b = sum_e Pi(max_{b in O_b} |f_e^(b)| - fbar_e), summed over the
+ * selected timesteps like lambda_o).  O_b holds every splittable station's
+ * node and both nodes of a split station; an outage takes its node out of
+ * service (every branch at it opens, its injection is lost and the slack
+ * balances).  One that leaves the rest of the grid in pieces islands: it is
+ * skipped and counted.  Per topology (device int32 [B][k_max + n_dslot]):
+ * the split update, a rank-(d - 1) outage of each busbar node with d live
+ * branches (FP64 setup, FP32 sweep over the monitored rows), then
+ *   lambda_b  device float [B] (NaN for a topology that islands the grid),
+ *   n_island  device int32 [B] islanding busbar outages (-1: the topology islands), or NULL,
+ *   bmax      device float [B][n_t][n_monitored] max over busbar outages of |flow|, or NULL.
+ * Asynchronous on stream; genome errors as for tto_evaluate_batch. */
+int tto_evaluate_busbar(tto_grid* g, const int32_t* topo, int32_t B, const int32_t* timesteps, int32_t n_t,
+                        float* lambda_b, int32_t* n_island, float* bmax, void* stream);
+
+/* lambda_b of the unsplit topology (lambda_b^pre) for these timesteps (host,
+ * NULL = all), kept on the device for TTO_FIT_F2 evaluations with the same
+ * timesteps; tto_grid_set_limits drops it.  Asynchronous on stream. */
+int tto_grid_busbar_reference(tto_grid* g, const int32_t* timesteps, int32_t n_t, void* stream);
 
 /* tto_worst_k -- worst-k N-1 export for AC validation (Sec. "AC-Validator":
  * the DC optimiser computes each N-1 case's overload energy and writes out the

@@ -11,7 +11,7 @@ import numpy as np
 
 from . import _lib
 from ._lib import (  # noqa: F401
-    TTOError, PREC_FP32, PREC_BF16X3, PREC_BF16, PREC_TF32X3, PREC_FP16X3, FIT_WORKLOAD, FIT_F1,
+    TTOError, PREC_FP32, PREC_BF16X3, PREC_BF16, PREC_TF32X3, PREC_FP16X3, FIT_WORKLOAD, FIT_F1, FIT_F2,
     SCREEN_SCORE, SCREEN_CELL_GAIN,
 )
 
@@ -121,6 +121,29 @@ class Grid:
         if allE is not None:
             out["all_energy"] = allE
         return out
+
+    def busbar(self, topo, timesteps=None, bmax=False, stream=None):
+        """Busbar outages of each topology: lambda_b [B] (NaN where the
+        topology islands), the islanding busbar outages [B] and, when asked,
+        bmax [B][n_t][n_monitored]."""
+        torch = _torch()
+        B = int(topo.shape[0])
+        if topo.dtype != torch.int32 or not topo.is_cuda or topo.shape[1] != self.genome_width:
+            raise TTOError(_lib.TTO_E_ARG, "topo must be a CUDA int32 tensor [B][k_max + n_dslot]")
+        topo = topo.contiguous()
+        dev = topo.device
+        n_t = self.n_time if timesteps is None else len(timesteps)
+        out = {"lambda_b": torch.empty(B, dtype=torch.float32, device=dev),
+               "n_island": torch.empty(B, dtype=torch.int32, device=dev)}
+        if bmax:
+            out["bmax"] = torch.empty(B, n_t, self.n_monitored, dtype=torch.float32, device=dev)
+        _lib.tto_evaluate_busbar(self._h, topo, B, timesteps, out["lambda_b"], out["n_island"], out.get("bmax"),
+                                 _stream(stream))
+        return out
+
+    def busbar_reference(self, timesteps=None, stream=None):
+        """Compute lambda_b of the unsplit topology for lambda_f2 evaluations."""
+        _lib.tto_grid_busbar_reference(self._h, timesteps, _stream(stream))
 
     def sync_status(self, stream=None):
         _lib.tto_grid_sync_status(self._h, _stream(stream))

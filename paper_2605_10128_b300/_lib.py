@@ -21,7 +21,7 @@ TTO_E_NOMEM = -4
 TTO_E_TOPOLOGY = -5
 TTO_E_TIMEOUT = -6
 PREC_FP32, PREC_BF16X3, PREC_BF16, PREC_TF32X3, PREC_FP16X3 = 0, 1, 2, 3, 4
-FIT_WORKLOAD, FIT_F1 = 0, 1
+FIT_WORKLOAD, FIT_F1, FIT_F2 = 0, 1, 2
 
 _i32p = C.POINTER(C.c_int32)
 _u32p = C.POINTER(C.c_uint32)
@@ -105,6 +105,8 @@ _SIGS = {
     "tto_worst_k": ([_vp, _vp, C.c_int32, _i32p, C.c_int32, C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
     "tto_epoch_export": ([_vp, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp], C.c_int),
     "tto_epoch_export_wait": ([_vp], C.c_int),
+    "tto_evaluate_busbar": ([_vp, _vp, C.c_int32, _i32p, C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
+    "tto_grid_busbar_reference": ([_vp, _i32p, C.c_int32, _vp], C.c_int),
     "tto_archive_destroy": ([_vp], C.c_int),
     "tto_archive_export": ([_vp, _vp, _vp, _vp], C.c_int),
     "tto_archive_import": ([_vp, _vp, _vp, _vp], C.c_int),
@@ -232,6 +234,24 @@ def tto_worst_k(h, topo, n, timesteps, k, outage_out, energy_out, all_energy, st
         n_t = int(ts_arr.size)
     return check(lib().tto_worst_k(h, _dp(topo), int(n), ts, n_t, int(k), _dp(outage_out), _dp(energy_out),
                                    _dp(all_energy), _vp(stream)))
+
+
+def _ts(timesteps):
+    if timesteps is None:
+        return None, 0, None
+    ts_arr = np.ascontiguousarray(timesteps, dtype=np.int32)
+    return _ptr(ts_arr, C.c_int32), int(ts_arr.size), ts_arr
+
+
+def tto_evaluate_busbar(h, topo, B, timesteps, lambda_b, n_island, bmax, stream):
+    ts, n_t, keep = _ts(timesteps)
+    return check(lib().tto_evaluate_busbar(h, _dp(topo), int(B), ts, n_t, _dp(lambda_b), _dp(n_island), _dp(bmax),
+                                           _vp(stream)))
+
+
+def tto_grid_busbar_reference(h, timesteps, stream):
+    ts, n_t, keep = _ts(timesteps)
+    return check(lib().tto_grid_busbar_reference(h, ts, n_t, _vp(stream)))
 
 
 def tto_epoch_export(a, k, fit, gen, filled, widx, wval, stream):

@@ -1,0 +1,261 @@
+// Busbar outage sweep (Sec. "Fitness function heuristics": lambda_b =
+// sum_e Pi(max_{b in O_b} |f_e^(b)| - fbar_e); lambda_f2 in Sec. "High-level
+// Genetic Algorithm loop").
+//
+// The split update writes one record per (topology, busbar node) (see
+// busbar_setup in evaluate.cu): station s, the N columns of the node's other
+// branches R', the node's injection p_v[t], and z[t], y[t] of
+//   F_l[t] = f'_l[t] - p_v[t] pi_s,l - sum_j N_{l r_j} z_j[t] - U_l . y[t].
+// This kernel evaluates F for every monitored row and keeps the running
+// maximum over the busbar outages per (row, timestep), on the CUDA cores in
+// FP32.  CTA = 128 monitored rows (thread = row) x G topologies; the records
+// are staged VB at a time in shared memory; the thread's U row and f' stay in
+// registers; N_{l r_j} and pi_s,l are read coalesced along the rows from
+// column-major FP32 tables.  Each CTA reduces its rows to one partial
+// lambda_b per topology in a fixed order (no atomics).
+#include <math.h>
+
+#include "sweep.cuh"
+#include "tto_internal.h"
+
+namespace tto {
+
+namespace {
+
+constexpr int kBRows = 128;
+constexpr int kBVB = 8;  // busbar records staged per round
+
+template <int TT, int G>
+__global__ void __launch_bounds__(kBRows) busbar_sweep_kernel(EvalArgs a) {
+  extern __shared__ float srec[];  // [G][kBVB][kRec]
+  __shared__ float sred[kBRows / 32][G];
+  const int tid = threadIdx.x, tile = blockIdx.x;
+  const int l = tile * kBRows + tid;
+  const int b0 = blockIdx.y * G;
+  const int Ep = a.E_mon_pad, kRec = a.kRec;
+  float u[G][8], fpv[G][TT], m[G][TT];
+#pragma unroll
+  for (int gi = 0; gi < G; ++gi) {
+    const int bb = min(b0 + gi, a.B - 1);
+    const float* ur = a.U + ((size_t)bb * Ep + l) * 8;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) u[gi][i] = ur[i];
+#pragma unroll
+    for (int t = 0; t < TT; ++t) {
+      fpv[gi][t] = a.fp[((size_t)bb * TT + t) * Ep + l];
+      m[gi][t] = 0.f;
+    }
+  }
+  for (int v0 = 0; v0 < a.NB; v0 += kBVB) {
+    const int nv = min(kBVB, a.NB - v0);
+    __syncthreads();
+    for (int i = tid; i < G * kBVB * kRec; i += kBRows) {
+      const int gi = i / (kBVB * kRec), r = i % (kBVB * kRec), vv = r / kRec;
+      const int bb = min(b0 + gi, a.B - 1);
+      float x = __int_as_float(-1);
+      if (vv < nv) x = a.bbrec[((size_t)bb * a.NB + v0 + vv) * kRec + r % kRec];
+      else if (r % kRec != 1) x = 0.f;  // slot past the end: |R'| = -1 marks it unused
+      srec[i] = x;
+    }
+    __syncthreads();
+    for (int vv = 0; vv < nv; ++vv) {
+#pragma unroll
+      for (int gi = 0; gi < G; ++gi) {
+        const float* rec = srec + (gi * kBVB + vv) * kRec;
+        const int* irec = reinterpret_cast<const int*>(rec);
+        const int nr = irec[1];
+        if (nr < 0) continue;
+        const float pi = a.Pm[(size_t)irec[0] * Ep + l];
+        const float* pr = rec + kBBHead;
+        const float* zr = pr + TT;
+        const float* yr = zr + kMaxBB * TT;
+        float F[TT];
+#pragma unroll
+        for (int t = 0; t < TT; ++t) {
+          float f = fmaf(-pr[t], pi, fpv[gi][t]);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) f = fmaf(-u[gi][i], yr[i * TT + t], f);
+          F[t] = f;
+        }
+        for (int jj = 0; jj < nr; ++jj) {
+          const float n = a.Nswm[(size_t)irec[2 + jj] * Ep + l];
+#pragma unroll
+          for (int t = 0; t < TT; ++t) F[t] = fmaf(-n, zr[jj * TT + t], F[t]);
+        }
+#pragma unroll
+        for (int t = 0; t < TT; ++t) m[gi][t] = fmaxf(m[gi][t], fabsf(F[t]));
+      }
+    }
+  }
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int gi = 0; gi < G; ++gi) {
+    const int bb = b0 + gi;
+    float over = 0.f;
+    if (l < a.E_mon && bb < a.B) {
+      const float lim = a.lim[l];
+      for (int t = 0; t < a.n_t; ++t) {
+        over += fmaxf(m[gi][t] - lim, 0.f);
+        if (a.bmax) a.bmax[((size_t)bb * a.n_t + t) * a.E_mon + l] = m[gi][t];
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) over += __shfl_xor_sync(0xffffffffu, over, o);
+    if (lane == 0) sred[warp][gi] = over;
+  }
+  __syncthreads();
+  if (tid < G && b0 + tid < a.B) {
+    float s = 0.f;
+    for (int w = 0; w < kBRows / 32; ++w) s += sred[w][tid];
+    a.bbpart[(size_t)(b0 + tid) * a.n_rowtiles + tile] = s;
+  }
+}
+
+__global__ void build_nswm_kernel(const double* Nsw, const int* mon, int E, int E_mon, int Ep, int n_sw, float* out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)n_sw * Ep) return;
+  const int q = (int)(i / Ep), l = (int)(i % Ep);
+  out[i] = l < E_mon ? (float)Nsw[(size_t)q * E + mon[l]] : 0.f;
+}
+
+// lambda_b and the islanding count per topology (fixed-order sum of the row tiles)
+__global__ void busbar_metrics_kernel(EvalArgs a, float* lambda_b, int32_t* n_island) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= a.B) return;
+  const TopoInfo inf = a.info[b];
+  double s = 0.0;
+  for (int r = 0; r < a.n_rowtiles; ++r) s += (double)a.bbpart[(size_t)b * a.n_rowtiles + r];
+  if (lambda_b) lambda_b[b] = inf.island_base ? __int_as_float(0x7fc00000) : (float)s;
+  if (n_island) n_island[b] = inf.island_base ? -1 : inf.nbisl;
+}
+
+template <int TT, int G>
+int launch_tt(const EvalArgs& a, cudaStream_t s) {
+  const size_t smem = (size_t)G * kBVB * a.kRec * sizeof(float);
+  static bool attr[64] = {};
+  int dev = 0;
+  TTO_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < 64 && !attr[dev]) {
+    TTO_CUDA_TRY(cudaFuncSetAttribute(busbar_sweep_kernel<TT, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    attr[dev] = true;
+  }
+  const dim3 grid((unsigned)(a.E_mon_pad / kBRows), (unsigned)((a.B + G - 1) / G));
+  busbar_sweep_kernel<TT, G><<<grid, kBRows, smem, s>>>(a);
+  TTO_CUDA_TRY(cudaGetLastError());
+  return TTO_OK;
+}
+
+}  // namespace
+
+int ensure_busbar(tto_grid* g, int B, int TT, cudaStream_t s) {
+  if (kRowTile != kBRows) return set_error(TTO_E_ARG, "busbar sweep tile mismatch");
+  if (!g->d_Nswm) {
+    const size_t n = (size_t)std::max(g->n_sw, 1) * g->E_mon_pad;
+    TTO_CUDA_TRY(cudaMalloc(&g->d_Nswm, n * sizeof(float)));
+    build_nswm_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g->d_Nsw, g->d_mon, g->E, g->E_mon, g->E_mon_pad,
+                                                                   g->n_sw, g->d_Nswm);
+    TTO_CUDA_TRY(cudaGetLastError());
+  }
+  const int NB = g->S + g->k_max;
+  if (B > g->bb_cap_B || TT > g->bb_cap_T) {
+    const int nB = std::max(B, g->bb_cap_B), nT = std::max(TT, g->bb_cap_T);
+    TTO_CUDA_TRY(cudaStreamSynchronize(s));
+    if (g->d_bbrec) cudaFree(g->d_bbrec);
+    if (g->d_bbpart) cudaFree(g->d_bbpart);
+    g->d_bbrec = nullptr;
+    g->d_bbpart = nullptr;
+    g->bb_cap_B = g->bb_cap_T = 0;
+    TTO_CUDA_TRY(cudaMalloc(&g->d_bbrec, (size_t)nB * NB * bb_record_floats(nT) * sizeof(float)));
+    TTO_CUDA_TRY(cudaMalloc(&g->d_bbpart, (size_t)nB * g->n_rowtiles * sizeof(float)));
+    g->bb_cap_B = nB;
+    g->bb_cap_T = nT;
+    forget_grid_graphs(g);
+    ++g->ws_epoch;
+  }
+  return TTO_OK;
+}
+
+void fill_busbar_args(tto_grid* g, EvalArgs& a) {
+  a.busbar = 1;
+  a.S = g->S;
+  a.NB = g->S + g->k_max;
+  a.kRec = bb_record_floats(a.TT);
+  a.Pst = g->d_Pst;
+  a.Pm = g->d_Pm;
+  a.Nswm = g->d_Nswm;
+  a.bbrec = g->d_bbrec;
+  a.bbpart = g->d_bbpart;
+  a.lbpre = g->d_lbpre;
+}
+
+int launch_busbar_sweep(const EvalArgs& a, cudaStream_t s) {
+  switch (a.TT) {
+    case 1: return launch_tt<1, 4>(a, s);
+    case 2: return launch_tt<2, 4>(a, s);
+    case 4: return launch_tt<4, 4>(a, s);
+    case 8: return launch_tt<8, 4>(a, s);
+    case 16: return launch_tt<16, 2>(a, s);
+    case 24: return launch_tt<24, 1>(a, s);
+    case 32: return launch_tt<32, 1>(a, s);
+    default: return set_error(TTO_E_ARG, "unsupported timestep count %d", a.TT);
+  }
+}
+
+int launch_busbar_metrics(const EvalArgs& a, float* lambda_b, int32_t* n_island, cudaStream_t s) {
+  busbar_metrics_kernel<<<(a.B + 127) / 128, 128, 0, s>>>(a, lambda_b, n_island);
+  TTO_CUDA_TRY(cudaGetLastError());
+  return TTO_OK;
+}
+
+}  // namespace tto
+
+using namespace tto;
+
+extern "C" int tto_evaluate_busbar(tto_grid* g, const int32_t* topo, int32_t B, const int32_t* timesteps, int32_t n_t,
+                                   float* lambda_b, int32_t* n_island, float* bmax, void* stream) {
+  if (!g || B < 0) return set_error(TTO_E_ARG, "bad busbar arguments");
+  if (B == 0) return TTO_OK;
+  if (!topo) return set_error(TTO_E_ARG, "null topology buffer");
+  if (g->S < 1) return set_error(TTO_E_ARG, "the grid has no stations, so no busbar outages");
+  cudaStream_t s = (cudaStream_t)stream;
+  TTO_CUDA_TRY(cudaSetDevice(g->device));
+  const int TT = padded_T(timesteps ? n_t : g->T);
+  if (TT < 0) return set_error(TTO_E_ARG, "at most %d timesteps", TTO_MAX_T);
+  int rc = ensure_workspace(g, B, TT);
+  if (rc) return rc;
+  rc = ensure_busbar(g, B, TT, s);
+  if (rc) return rc;
+  tto_eval_opts o{};
+  o.precision = TTO_PREC_FP32;
+  o.fitness_kind = TTO_FIT_WORKLOAD;
+  o.d_split = 1;
+  o.d_moved = 1;
+  EvalArgs a;
+  rc = evaluate_impl(g, topo, B, timesteps, n_t, &o, g->ws.fit, nullptr, nullptr, nullptr, nullptr, nullptr, s, &a,
+                     /*busbar_setup=*/true);
+  if (rc) return rc;
+  a.bmax = bmax;
+  rc = launch_busbar_sweep(a, s);
+  if (rc) return rc;
+  return launch_busbar_metrics(a, lambda_b, n_island, s);
+}
+
+extern "C" int tto_grid_busbar_reference(tto_grid* g, const int32_t* timesteps, int32_t n_t, void* stream) {
+  if (!g) return set_error(TTO_E_ARG, "null grid");
+  cudaStream_t s = (cudaStream_t)stream;
+  TTO_CUDA_TRY(cudaSetDevice(g->device));
+  const int nt = timesteps ? n_t : g->T;
+  if (nt < 1 || nt > TTO_MAX_T) return set_error(TTO_E_ARG, "n_t must be in [1, %d]", TTO_MAX_T);
+  if (!g->d_lbpre) TTO_CUDA_TRY(cudaMalloc(&g->d_lbpre, sizeof(float)));
+  if (!g->d_empty) {
+    TTO_CUDA_TRY(cudaMalloc(&g->d_empty, TTO_MAX_K * sizeof(int32_t)));
+    TTO_CUDA_TRY(cudaMemset(g->d_empty, 0xFF, TTO_MAX_K * sizeof(int32_t)));
+  }
+  const int rc = tto_evaluate_busbar(g, g->d_empty, 1, timesteps, n_t, g->d_lbpre, nullptr, nullptr, stream);
+  if (rc) return rc;
+  g->lbpre_nt = nt;
+  for (int t = 0; t < nt; ++t) g->lbpre_tsel[t] = timesteps ? timesteps[t] : t;
+  (void)s;
+  return TTO_OK;
+}

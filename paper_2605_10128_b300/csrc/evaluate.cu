@@ -47,8 +47,169 @@ __device__ __forceinline__ void store_col_factors(const EvalArgs& a, int b, int 
   for (int t = 0; t < a.TT; ++t) grow[t] = gv[t];
 }
 
+// ------------------------------------------------------ busbar outage setup
+// Busbar outages (Sec. "Fitness function heuristics": lambda_b over the
+// busbar outage set O_b): every splittable station's node, and both nodes of a
+// split station, taken out of service (branches opened, injection dropped, the
+// slack balances).  Per topology and busbar node v, with R_v its live branches
+// and p_v its injection, the post-outage flows on the post-topology grid are
+//   F = f' - p_v rho - N'[:, R'] z,   N'_{R'R'} z = f'_{R'} - p_v rho_{R'},
+// rho = pi_s + U kappa (the post-topology response to +1 at v, -1 at the
+// slack; pi_s the unsplit response at the station bus, kappa = dp_M - S^T pi_s
+// with dp_M = e_j for busbar B of split slot j) and R' = R_v without its first
+// branch: once p_v is gone, v hangs on that branch with no injection and
+// carries no flow.  N'_{R'R'} is singular exactly when the rest of the grid
+// falls apart without v (the busbar outage islands).  With N' = N - U V^T the
+// monitored rows need only
+//   F_l[t] = f'_l[t] - p_v[t] pi_s,l - sum_j N_{l r_j} z_j[t] - U_l . y[t],
+//   y[t] = p_v[t] kappa - sum_j z_j[t] V_{r_j},
+// so each (topology, busbar) record holds s, |R'|, the N columns of R', p_v,
+// z and y.  The small system is solved in FP64 as D^-1 N'_{R'R'} (symmetric:
+// D^-1 N and D^-1 U V^T = D^-1 W K^-1 W^T D^-1 are) by LDL^T, with the
+// islanding test pivot x b_r <= 1e-6 as for single outages.
+__device__ void busbar_setup(const EvalArgs& a, int b, int k, int ns, const int* s_st, const uint32_t* s_mask,
+                             const int* s_dis, int nd, const int* s_slot, const int* s_e, const double* s_sign,
+                             const double* s_coef, const double* const* s_col, const double (*s_Ki)[TTO_MAX_K],
+                             const double (*s_psi)[TTO_MAX_K], int* n_island) {
+  const int TT = a.TT, nt = a.n_t;
+  for (int v = threadIdx.x; v < a.NB; v += blockDim.x) {
+    float* rec = a.bbrec + ((size_t)b * a.NB + v) * a.kRec;
+    int* irec = reinterpret_cast<int*>(rec);
+    int s, side, js = -1;
+    if (v < a.S) {
+      s = v;
+      side = 0;
+    } else {
+      const int j = v - a.S;
+      if (j >= ns) {
+        irec[0] = 0;
+        irec[1] = -1;  // no such busbar in this topology
+        continue;
+      }
+      s = s_st[j];
+      side = 1;
+    }
+    for (int j = 0; j < ns; ++j)
+      if (s_st[j] == s) js = j;
+    const uint32_t mask = js >= 0 ? s_mask[js] : 0u;
+    const int a0 = a.asset_off[s], m = a.asset_off[s + 1] - a0, bus = a.station_bus[s];
+    int R[TTO_MAX_ASSETS], nrv = 0;
+    bool inj = false;
+    for (int i = 0; i < m; ++i) {
+      const bool on_b = (mask >> i) & 1u;
+      if (side == 1 ? !on_b : on_b) continue;  // the asset sits on the other node
+      const int e = a.asset_br[a0 + i];
+      if (e < 0) {
+        inj = true;
+        continue;
+      }
+      bool open = false;
+      for (int q = 0; q < nd; ++q) open = open || s_dis[q] == e;
+      if (!open) R[nrv++] = e;
+    }
+    irec[0] = s;
+    if (nrv == 0) {  // a node without live branches: the topology itself islands (not reached)
+      irec[1] = -2;
+      atomicAdd(n_island, 1);
+      continue;
+    }
+    float* prec = rec + kBBHead;
+    float* zrec = prec + TT;
+    float* yrec = zrec + kMaxBB * TT;
+    double pv[TTO_MAX_T];
+    for (int t = 0; t < TT; ++t) {
+      pv[t] = (inj && t < nt) ? a.p[(size_t)a.tsel[t] * a.n_bus + bus] : 0.0;
+      prec[t] = (float)pv[t];
+    }
+    double kap[TTO_MAX_K];
+    for (int i = 0; i < k; ++i) {
+      double st = 0.0;
+      for (int q = s_slot[i]; q < s_slot[i + 1]; ++q) st += s_sign[q] * a.Pst[(size_t)s * a.E + s_e[q]];
+      kap[i] = (side == 1 && i == js ? 1.0 : 0.0) - st;
+    }
+    const int nrp = nrv - 1;
+    double W[kMaxBB][TTO_MAX_K], U[kMaxBB][TTO_MAX_K], Q[kMaxBB][kMaxBB], rhs[kMaxBB][TTO_MAX_T];
+    for (int jj = 0; jj < nrp; ++jj) {
+      const int r = R[1 + jj];
+      for (int i = 0; i < k; ++i) {
+        double w = 0.0;
+        for (int q = s_slot[i]; q < s_slot[i + 1]; ++q) w += s_coef[q] * s_col[q][r];
+        W[jj][i] = w;
+      }
+      double rho = a.Pst[(size_t)s * a.E + r];
+      for (int i = 0; i < k; ++i) {
+        double u = 0.0;
+        for (int i2 = 0; i2 < k; ++i2) u += W[jj][i2] * s_Ki[i2][i];
+        U[jj][i] = u;
+        rho += u * kap[i];
+      }
+      const double br = a.b[r];
+      for (int t = 0; t < TT; ++t) {
+        double f = 0.0;
+        if (t < nt) {
+          f = a.f0[(size_t)a.tsel[t] * a.E + r];
+          for (int i = 0; i < k; ++i) f += W[jj][i] * s_psi[t][i];
+        }
+        rhs[jj][t] = (f - pv[t] * rho) / br;
+      }
+    }
+    // Q = D^-1 N'_{R'R'}, lower triangle
+    for (int ii = 0; ii < nrp; ++ii)
+      for (int jj = 0; jj <= ii; ++jj) {
+        const int ri = R[1 + ii], rj = R[1 + jj];
+        double uv = 0.0;
+        for (int i = 0; i < k; ++i) uv += U[ii][i] * W[jj][i];
+        Q[ii][jj] = (a.Nsw[(size_t)a.swcol[rj] * a.E + ri] - uv / a.b[rj]) / a.b[ri];
+      }
+    // LDL^T in place (L below the diagonal, D on it)
+    bool isl = false;
+    for (int j = 0; j < nrp && !isl; ++j) {
+      double dj = Q[j][j];
+      for (int q = 0; q < j; ++q) dj -= Q[j][q] * Q[j][q] * Q[q][q];
+      if (!(dj * a.b[R[1 + j]] > kIslandTol)) isl = true;
+      Q[j][j] = dj;
+      for (int i = j + 1; i < nrp && !isl; ++i) {
+        double x = Q[i][j];
+        for (int q = 0; q < j; ++q) x -= Q[i][q] * Q[j][q] * Q[q][q];
+        Q[i][j] = x / dj;
+      }
+    }
+    if (isl) {
+      irec[1] = -2;
+      atomicAdd(n_island, 1);
+      continue;
+    }
+    for (int t = 0; t < TT; ++t) {
+      double z[kMaxBB];
+      for (int i = 0; i < nrp; ++i) {
+        double x = rhs[i][t];
+        for (int q = 0; q < i; ++q) x -= Q[i][q] * z[q];
+        z[i] = x;
+      }
+      for (int i = 0; i < nrp; ++i) z[i] /= Q[i][i];
+      for (int i = nrp - 1; i >= 0; --i) {
+        double x = z[i];
+        for (int q = i + 1; q < nrp; ++q) x -= Q[q][i] * z[q];
+        z[i] = x;
+      }
+      for (int jj = 0; jj < kMaxBB; ++jj) zrec[jj * TT + t] = jj < nrp ? (float)z[jj] : 0.f;
+      for (int i = 0; i < TTO_MAX_K; ++i) {
+        double y = 0.0;
+        if (i < k) {
+          y = pv[t] * kap[i];
+          for (int jj = 0; jj < nrp; ++jj) y -= z[jj] * W[jj][i] / a.b[R[1 + jj]];
+        }
+        yrec[i * TT + t] = (float)y;
+      }
+    }
+    irec[1] = nrp;
+    for (int jj = 0; jj < kMaxBB; ++jj) irec[2 + jj] = jj < nrp ? a.swcol[R[1 + jj]] : 0;
+  }
+}
+
 // ---------------------------------------------------------------- split update
-__global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
+template <bool BB>
+__device__ __forceinline__ void split_update_body(const EvalArgs& a) {
   const int b = blockIdx.x;
   const int tid = threadIdx.x;
   __shared__ int s_k, s_island, s_ns, s_nm;
@@ -70,6 +231,9 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
   __shared__ int s_cnt_c0, s_cnt_isl;
   __shared__ float s_umax, s_vmax;
   __shared__ int s_dis[TTO_MAX_K], s_nd;  // branches the genome opens
+  __shared__ int s_st[TTO_MAX_K];          // station of each split slot
+  __shared__ uint32_t s_mk[TTO_MAX_K];     // its busbar-B mask
+  __shared__ int s_bbisl;
 
   if (tid == 0) {
     int k = 0, ne = 0, bad = 0, ns = 0, nm = 0, nd = 0;
@@ -103,6 +267,8 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
       if (bad) break;
       stations[k] = st;
       uint32_t mask = a.act_mask[act];
+      s_st[k] = st;
+      s_mk[k] = mask;
       int bus = a.station_bus[st];
       int a0 = a.asset_off[st], m = a.asset_off[st + 1] - a0;
       int onb = __popc(mask);
@@ -150,6 +316,7 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
     s_ns = ns;
     s_nm = nm;
     s_nd = bad ? 0 : nd;
+    s_bbisl = 0;
     s_island = bad;
     s_cnt_c0 = 0;
     s_cnt_isl = 0;
@@ -372,6 +539,18 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
   // magnitudes are >= 0, so the float bit patterns order like the values
   if (umax > 0.f) atomicMax(reinterpret_cast<int*>(&s_umax), __float_as_int(umax));
   if (vmax > 0.f) atomicMax(reinterpret_cast<int*>(&s_vmax), __float_as_int(vmax));
+  if constexpr (BB) {
+    if (dead) {
+      for (int v = tid; v < a.NB; v += blockDim.x) {
+        int* irec = reinterpret_cast<int*>(a.bbrec + ((size_t)b * a.NB + v) * a.kRec);
+        irec[0] = 0;
+        irec[1] = -1;
+      }
+    } else {
+      busbar_setup(a, b, k, s_ns, s_st, s_mk, s_dis, s_nd, s_slot, s_e, s_sign, s_coef, s_col, s_Ki, s_psi,
+                   &s_bbisl);
+    }
+  }
   __syncthreads();
   if (tid == 0) {
     TopoInfo inf;
@@ -383,9 +562,15 @@ __global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) {
     inf.umax = s_umax;
     inf.vmax = s_vmax;
     inf.nd = s_nd;
+    inf.nbisl = dead ? 0 : s_bbisl;
     a.info[b] = inf;
   }
 }
+
+// Two instantiations: the busbar-outage setup needs many more registers and a
+// large stack, which the plain split update should not pay for.
+__global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) { split_update_body<false>(a); }
+__global__ void __launch_bounds__(256) split_update_bb_kernel(EvalArgs a) { split_update_body<true>(a); }
 
 // ---------------------------------------------------------------- fitness
 __global__ void fitness_kernel(EvalArgs a) {
@@ -405,6 +590,10 @@ __global__ void fitness_kernel(EvalArgs a) {
     fit = -INFINITY;
   } else if (a.fitness_kind == TTO_FIT_F1) {
     fit = (float)(-(lo + 200.0 * inf.lambda_c0 + 50.0 * lc));
+  } else if (a.fitness_kind == TTO_FIT_F2) {
+    double lb = 0.0;
+    for (int r = 0; r < a.n_rowtiles; ++r) lb += (double)a.bbpart[(size_t)b * a.n_rowtiles + r];
+    fit = (float)(-(lo + 200.0 * inf.lambda_c0 + 50.0 * lc + fmax(lb - (double)*a.lbpre, 0.0)));
   } else {
     fit = (float)(-(lo + (double)ml));
   }
@@ -473,13 +662,15 @@ static int padded_K(int k) { return k <= 2 ? 2 : (k <= 4 ? 4 : 8); }
 
 int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, int n_t,
                   const tto_eval_opts* o, float* fitness, int32_t* desc, int32_t* cell,
-                  uint8_t* island, float* metrics, float* fmax, cudaStream_t s, EvalArgs* split_only) {
+                  uint8_t* island, float* metrics, float* fmax, cudaStream_t s, EvalArgs* split_only,
+                  bool busbar_setup) {
   if (!g || !o) return set_error(TTO_E_ARG, "null argument");
   if (B < 0) return set_error(TTO_E_ARG, "negative batch");
   if (B > 0 && (!topo || !fitness)) return set_error(TTO_E_ARG, "null topology or fitness buffer");
   if (o->d_split < 1 || o->d_moved < 1 || o->d_disc < 0) return set_error(TTO_E_ARG, "archive extents must be >= 1");
   if (o->precision < TTO_PREC_FP32 || o->precision > TTO_PREC_FP16X3) return set_error(TTO_E_ARG, "unknown precision");
-  if (o->fitness_kind != TTO_FIT_WORKLOAD && o->fitness_kind != TTO_FIT_F1) return set_error(TTO_E_ARG, "unknown fitness kind");
+  if (o->fitness_kind != TTO_FIT_WORKLOAD && o->fitness_kind != TTO_FIT_F1 && o->fitness_kind != TTO_FIT_F2)
+    return set_error(TTO_E_ARG, "unknown fitness kind");
   if (n_t < 0 || n_t > TTO_MAX_T || (tsel == nullptr && g->T > TTO_MAX_T))
     return set_error(TTO_E_ARG, "n_t must be in [1, %d]", TTO_MAX_T);
   EvalArgs a;
@@ -497,8 +688,20 @@ int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, 
   if (B == 0) return TTO_OK;
   const int TT = padded_T(n_t);
   TTO_CUDA_TRY(cudaSetDevice(g->device));
+  const bool bb = busbar_setup || o->fitness_kind == TTO_FIT_F2;
+  if (o->fitness_kind == TTO_FIT_F2 && !busbar_setup) {
+    bool same = g->d_lbpre && g->lbpre_nt == n_t;
+    for (int t = 0; same && t < n_t; ++t) same = g->lbpre_tsel[t] == a.tsel[t];
+    if (!same)
+      return set_error(TTO_E_ARG, "lambda_f2 needs tto_grid_busbar_reference for these timesteps and limits first");
+  }
   int rc = ensure_workspace(g, B, TT);
   if (rc) return rc;
+  if (bb) {
+    if (g->S < 1) return set_error(TTO_E_ARG, "the grid has no stations, so no busbar outages");
+    rc = ensure_busbar(g, B, TT, s);
+    if (rc) return rc;
+  }
   Workspace& w = g->ws;
   a.Nmo = g->d_Nmo;
   a.Nsw = g->d_Nsw;
@@ -560,13 +763,15 @@ int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, 
   a.precision = o->precision;
   a.shape = g->tuned_shape[o->precision] >= 0 ? g->tuned_shape[o->precision] : 0;
   a.from = g->d_from;
+  if (bb) fill_busbar_args(g, a);
   cudaEvent_t* ev = nullptr;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   TTO_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
   if (g->prof_on && !split_only && g->prof_n < kProfileCalls && cap == cudaStreamCaptureStatusNone)
     ev = &g->prof_ev[4 * g->prof_n++];
   if (ev) TTO_CUDA_TRY(cudaEventRecord(ev[0], s));
-  split_update_kernel<<<B, 256, 0, s>>>(a);
+  if (bb) split_update_bb_kernel<<<B, 256, 0, s>>>(a);
+  else split_update_kernel<<<B, 256, 0, s>>>(a);
   TTO_CUDA_TRY(cudaGetLastError());
   if (split_only) {
     *split_only = a;
@@ -580,6 +785,10 @@ int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, 
   }
   rc = launch_sweep(a, s);
   if (rc) return rc;
+  if (bb) {
+    rc = launch_busbar_sweep(a, s);
+    if (rc) return rc;
+  }
   if (ev) TTO_CUDA_TRY(cudaEventRecord(ev[2], s));
   fitness_kernel<<<(B + 127) / 128, 128, 0, s>>>(a);
   TTO_CUDA_TRY(cudaGetLastError());

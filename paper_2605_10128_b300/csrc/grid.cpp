@@ -343,10 +343,13 @@ static int build_grid(const tto_grid_desc* d, tto_grid* g) {
   std::vector<double> Nsw((size_t)std::max(g->n_sw, 1) * E);
   std::vector<double> Ncc(g->O);
   g->f0.assign((size_t)T * E, 0.0);
+  // injection responses of the station buses (busbar outages): flows for +1
+  // at the station bus, withdrawn at the slack
+  std::vector<double> Pst((size_t)std::max(g->S, 1) * E, 0.0);
 
   unsigned nthreads = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
   std::atomic<int> next(0);
-  const int njobs = (int)need.size() + T;
+  const int njobs = (int)need.size() + T + g->S;
   auto worker = [&]() {
     std::vector<double> x(nr), col(E);
     for (;;) {
@@ -358,10 +361,12 @@ static int build_grid(const tto_grid_desc* d, tto_grid* g) {
         c = need[job];
         if (g->from[c] != g->slack) x[red(g->from[c])] += 1.0;
         if (g->to[c] != g->slack) x[red(g->to[c])] -= 1.0;
-      } else {
+      } else if (job < (int)need.size() + T) {
         int t = job - (int)need.size();
         for (int i = 0; i < n; ++i)
           if (i != g->slack) x[red(i)] = g->p[(size_t)t * n + i];
+      } else {
+        x[red(g->station_bus[job - (int)need.size() - T])] = 1.0;  // stations never sit at the slack
       }
       ldl.solve(x.data());
       for (int l = 0; l < E; ++l) {
@@ -372,7 +377,8 @@ static int build_grid(const tto_grid_desc* d, tto_grid* g) {
       }
       if (c < 0) {
         int t = job - (int)need.size();
-        std::copy(col.begin(), col.end(), g->f0.begin() + (size_t)t * E);
+        if (t < T) std::copy(col.begin(), col.end(), g->f0.begin() + (size_t)t * E);
+        else std::copy(col.begin(), col.end(), Pst.begin() + (size_t)(t - T) * E);
         continue;
       }
       // col = M[:, c]; N[:, c] = e_c - M[:, c]
@@ -404,6 +410,14 @@ static int build_grid(const tto_grid_desc* d, tto_grid* g) {
     if ((rc = upload(&g->d_Nsw32, Nsw32.data(), Nsw32.size()))) return rc;
   }
   if ((rc = upload(&g->d_swcol, swcol.data(), swcol.size()))) return rc;
+  if ((rc = upload(&g->d_Pst, Pst.data(), Pst.size()))) return rc;
+  {
+    std::vector<float> Pm((size_t)std::max(g->S, 1) * g->E_mon_pad, 0.f);
+    for (int s = 0; s < g->S; ++s)
+      for (int l = 0; l < g->E_mon; ++l) Pm[(size_t)s * g->E_mon_pad + l] = (float)Pst[(size_t)s * E + g->mon[l]];
+    if ((rc = upload(&g->d_Pm, Pm.data(), Pm.size()))) return rc;
+  }
+  g->swlist = swlist;
   if ((rc = upload(&g->d_f0, g->f0.data(), g->f0.size()))) return rc;
   if ((rc = upload(&g->d_p, g->p.data(), g->p.size()))) return rc;
   if ((rc = upload(&g->d_b, g->b.data(), g->b.size()))) return rc;
@@ -431,7 +445,8 @@ static void release(tto_grid* g) {
   cudaSetDevice(g->device);
   forget_grid_graphs(g);
   free_workspace(g);
-  void* ptrs[] = {g->d_from, g->d_Nf, g->d_Nmo, g->d_Nsw, g->d_Nsw32, g->d_swcol, g->d_f0, g->d_p, g->d_b, g->d_lim,
+  void* ptrs[] = {g->d_from, g->d_Nf, g->d_Nmo, g->d_Nsw, g->d_Nsw32, g->d_swcol, g->d_Pst, g->d_Pm, g->d_Nswm,
+                  g->d_lbpre, g->d_empty, g->d_bbrec, g->d_bbpart, g->d_f0, g->d_p, g->d_b, g->d_lim,
                   g->d_mon, g->d_out, g->d_Ncc, g->d_station_bus, g->d_asset_off,
                   g->d_asset_br, g->d_act_st, g->d_act_off, g->d_act_mask, g->d_disc, g->d_status};
   for (void* p : ptrs)
@@ -511,6 +526,7 @@ int tto_grid_set_limits(tto_grid* g, const double* limit_host) {
   for (int l = 0; l < g->E_mon; ++l) lim[l] = (float)g->limit[g->mon[l]];
   TTO_CUDA_TRY(cudaSetDevice(g->device));
   TTO_CUDA_TRY(cudaMemcpy(g->d_lim, lim.data(), lim.size() * sizeof(float), cudaMemcpyHostToDevice));
+  g->lbpre_nt = 0;  // lambda_b of the unsplit topology depends on the limits: recompute it
   return TTO_OK;
 }
 

@@ -7,6 +7,12 @@
 
 namespace tto {
 
+// busbar outage records: [station, |R'|, N columns of R' x kMaxBB], then
+// p_v[TT], z[kMaxBB][TT], y[8][TT]
+constexpr int kMaxBB = TTO_MAX_ASSETS - 1;
+constexpr int kBBHead = 2 + kMaxBB;
+inline int bb_record_floats(int TT) { return kBBHead + TT * (1 + kMaxBB + 8); }
+
 struct EvalArgs {
   // grid (device)
   const float* Nmo;
@@ -35,6 +41,16 @@ struct EvalArgs {
   int TC, n_tch;  // tensor-core sweep: timesteps per pass and number of passes
   int tsel[TTO_MAX_T];
   int d_split, d_moved, d_disc;
+  // busbar outages (lambda_b, lambda_f2)
+  int busbar;            // compute them
+  int S, NB, kRec;       // stations, busbar slots per topology (S + k_max), record floats
+  const double* Pst;     // [S][E] unsplit responses to +1 at each station bus
+  const float* Pm;       // [S][E_mon_pad] the same at the monitored rows
+  const float* Nswm;     // [n_sw][E_mon_pad] switchable N columns at the monitored rows
+  float* bbrec;          // [B][NB][kRec]
+  float* bbpart;         // [B][n_rowtiles] partial lambda_b
+  float* bmax;           // [B][n_t][E_mon] max over busbar outages of |flow|, or NULL
+  const float* lbpre;    // lambda_b of the unsplit topology
   int precision;
   int fitness_kind;
   int n_rowtiles;

@@ -35,6 +35,7 @@ struct TopoInfo {
   float lambda_c0;   // N-0 critical branches (summed over timesteps)
   float umax, vmax;  // largest |U| (monitored rows) and |V| (outage columns)
   int nd;            // opened branches (disconnection slots in use)
+  int nbisl;         // busbar outages that island the topology
 };
 
 // Evaluation workspace, grown on demand (or once by tto_grid_reserve).
@@ -75,6 +76,17 @@ struct tto_grid {
   double* d_Nsw = nullptr;     // [n_sw][E] full N columns of movable branches, FP64
   float* d_Nsw32 = nullptr;    // [n_sw][E] FP32 copy (monitored rows of the split update)
   int* d_swcol = nullptr;      // [E] column of a movable branch in d_Nsw, else -1
+  std::vector<int> swlist;     // branch of each d_Nsw column
+  double* d_Pst = nullptr;     // [S][E] flows for +1 at station bus s, -1 at the slack (FP64)
+  float* d_Pm = nullptr;       // [S][E_mon_pad] the same at the monitored rows, FP32
+  float* d_Nswm = nullptr;     // [n_sw][E_mon_pad] d_Nsw at the monitored rows, FP32 (busbar outages; built on first use)
+  float* d_lbpre = nullptr;    // lambda_b of the unsplit topology (tto_grid_busbar_reference)
+  int lbpre_nt = 0;            // its timestep selection (lambda_f2 needs the same)
+  int lbpre_tsel[TTO_MAX_T] = {};
+  int32_t* d_empty = nullptr;  // one all-empty genome (the unsplit topology)
+  float* d_bbrec = nullptr;    // busbar outage records [B][S + k_max][record]
+  float* d_bbpart = nullptr;   // partial lambda_b [B][row tiles]
+  int bb_cap_B = 0, bb_cap_T = 0;
   double* d_f0 = nullptr;      // [T][E] base flows
   double* d_p = nullptr;       // [T][n_bus]
   double* d_b = nullptr;       // [E]
@@ -126,7 +138,12 @@ struct EvalArgs;
 int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, int n_t,
                   const tto_eval_opts* o, float* fitness, int32_t* desc, int32_t* cell,
                   uint8_t* island, float* metrics, float* fmax, cudaStream_t s,
-                  EvalArgs* split_only = nullptr);
+                  EvalArgs* split_only = nullptr, bool busbar_setup = false);
+// Busbar outages (busbar.cu): tables and record workspace, launch arguments,
+// the sweep and the per-topology lambda_b.
+int ensure_busbar(tto_grid* g, int B, int TT, cudaStream_t s);
+void fill_busbar_args(tto_grid* g, EvalArgs& a);
+int launch_busbar_sweep(const EvalArgs& a, cudaStream_t s);
 // MapElites building blocks shared by the plain and the surrogate-screened step.
 int propose_impl(tto_archive* ar, uint64_t seed, uint64_t it, int B, const tto_mut_params* mp,
                  int32_t* out, cudaStream_t s);
