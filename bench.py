@@ -399,6 +399,8 @@ def main():
     ap.add_argument("--ddisc", type=int, default=3, help="archive extent over opened branches when --dslots > 0")
     ap.add_argument("--crossover", action="store_true", help="Algorithm 3's mutation/crossover split of each batch")
     ap.add_argument("--p-c1", type=float, default=0.5, help="crossover bias toward the first parent")
+    ap.add_argument("--fitness", default="workload", choices=["workload", "f1", "f2"],
+                    help="f2: lambda_f2, which adds every busbar outage of each topology")
     ap.add_argument("--epoch", type=int, default=0,
                     help="iterations per epoch: export the archive and its worst-20 lists after each (0: never)")
     args = ap.parse_args()
@@ -444,11 +446,14 @@ def main():
     else:
         tuned_shape, tuned_ms = g.autotune(min(B, 512), precision=prec)
     A = Archive(g, ds, dm, dd)
+    fit_kind = {"workload": 0, "f1": 1, "f2": 2}[args.fitness]
+    if fit_kind == 2:
+        g.busbar_reference()  # lambda_b of the unsplit topology, for lambda_f2
     seed = rank_seed(rank)
     stream = torch.cuda.current_stream()
 
     for it in range(args.warmup):
-        A.step(seed, it, B, mutation=mut, precision=prec)
+        A.step(seed, it, B, mutation=mut, precision=prec, fitness_kind=fit_kind)
     g.sync_status()
 
     def barrier():
@@ -465,7 +470,7 @@ def main():
     t0.record(stream)
     n_export = 0
     for it in range(args.warmup, args.warmup + args.steps):
-        A.step(seed, it, B, mutation=mut, precision=prec)
+        A.step(seed, it, B, mutation=mut, precision=prec, fitness_kind=fit_kind)
         if args.epoch and (it - args.warmup + 1) % args.epoch == 0:
             # end-of-epoch hand-over: archive snapshot + worst-20 N-1 cases of
             # every cell, copied to the host while the next epoch runs
@@ -553,6 +558,7 @@ def main():
                        "precision": args.precision, "parallelism": f"independent searches x{world}",
                        "l2": "inputs larger than L2 (N tile 305 MB + per-batch workspace ~8 GB)",
                        "step": "one MapElites iteration: propose, exact N-1 evaluation, insert",
+                       "fitness": args.fitness,
                        "genome": {"split_slots": c["k_max"], "disconnection_slots": args.dslots,
                                   "disconnection_set": n_disc, "archive": [ds, dm, dd],
                                   "crossover": bool(args.crossover), "p_c1": args.p_c1},

@@ -27,7 +27,7 @@ constexpr int kBVB = 8;  // busbar records staged per round
 
 template <int TT, int G>
 __global__ void __launch_bounds__(kBRows) busbar_sweep_kernel(EvalArgs a) {
-  extern __shared__ float srec[];  // [G][kBVB][kRec]
+  extern __shared__ __align__(16) float srec[];  // [G][kBVB][kRec]
   __shared__ float sred[kBRows / 32][G];
   const int tid = threadIdx.x, tile = blockIdx.x;
   const int l = tile * kBRows + tid;
@@ -70,17 +70,47 @@ __global__ void __launch_bounds__(kBRows) busbar_sweep_kernel(EvalArgs a) {
         const float* zr = pr + TT;
         const float* yr = zr + kMaxBB * TT;
         float F[TT];
+        if constexpr (TT % 4 == 0) {  // records are 16-byte aligned: four timesteps per load
 #pragma unroll
-        for (int t = 0; t < TT; ++t) {
-          float f = fmaf(-pr[t], pi, fpv[gi][t]);
+          for (int t4 = 0; t4 < TT; t4 += 4) {
+            const float4 p4 = *reinterpret_cast<const float4*>(pr + t4);
+            F[t4] = fmaf(-p4.x, pi, fpv[gi][t4]);
+            F[t4 + 1] = fmaf(-p4.y, pi, fpv[gi][t4 + 1]);
+            F[t4 + 2] = fmaf(-p4.z, pi, fpv[gi][t4 + 2]);
+            F[t4 + 3] = fmaf(-p4.w, pi, fpv[gi][t4 + 3]);
 #pragma unroll
-          for (int i = 0; i < 8; ++i) f = fmaf(-u[gi][i], yr[i * TT + t], f);
-          F[t] = f;
-        }
-        for (int jj = 0; jj < nr; ++jj) {
-          const float n = a.Nswm[(size_t)irec[2 + jj] * Ep + l];
+            for (int i = 0; i < 8; ++i) {
+              const float4 y4 = *reinterpret_cast<const float4*>(yr + i * TT + t4);
+              F[t4] = fmaf(-u[gi][i], y4.x, F[t4]);
+              F[t4 + 1] = fmaf(-u[gi][i], y4.y, F[t4 + 1]);
+              F[t4 + 2] = fmaf(-u[gi][i], y4.z, F[t4 + 2]);
+              F[t4 + 3] = fmaf(-u[gi][i], y4.w, F[t4 + 3]);
+            }
+          }
+          for (int jj = 0; jj < nr; ++jj) {
+            const float n = a.Nswm[(size_t)irec[2 + jj] * Ep + l];
 #pragma unroll
-          for (int t = 0; t < TT; ++t) F[t] = fmaf(-n, zr[jj * TT + t], F[t]);
+            for (int t4 = 0; t4 < TT; t4 += 4) {
+              const float4 z4 = *reinterpret_cast<const float4*>(zr + jj * TT + t4);
+              F[t4] = fmaf(-n, z4.x, F[t4]);
+              F[t4 + 1] = fmaf(-n, z4.y, F[t4 + 1]);
+              F[t4 + 2] = fmaf(-n, z4.z, F[t4 + 2]);
+              F[t4 + 3] = fmaf(-n, z4.w, F[t4 + 3]);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int t = 0; t < TT; ++t) {
+            float f = fmaf(-pr[t], pi, fpv[gi][t]);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) f = fmaf(-u[gi][i], yr[i * TT + t], f);
+            F[t] = f;
+          }
+          for (int jj = 0; jj < nr; ++jj) {
+            const float n = a.Nswm[(size_t)irec[2 + jj] * Ep + l];
+#pragma unroll
+            for (int t = 0; t < TT; ++t) F[t] = fmaf(-n, zr[jj * TT + t], F[t]);
+          }
         }
 #pragma unroll
         for (int t = 0; t < TT; ++t) m[gi][t] = fmaxf(m[gi][t], fabsf(F[t]));

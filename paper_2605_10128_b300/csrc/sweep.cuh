@@ -7,10 +7,11 @@
 
 namespace tto {
 
-// busbar outage records: [station, |R'|, N columns of R' x kMaxBB], then
-// p_v[TT], z[kMaxBB][TT], y[8][TT]
+// busbar outage records: [station, |R'|, N columns of R' x kMaxBB, pad to a
+// multiple of 4 floats], then p_v[TT], z[kMaxBB][TT], y[8][TT] (16-byte
+// aligned rows, so timesteps load as float4)
 constexpr int kMaxBB = TTO_MAX_ASSETS - 1;
-constexpr int kBBHead = 2 + kMaxBB;
+constexpr int kBBHead = (2 + kMaxBB + 3) / 4 * 4;
 inline int bb_record_floats(int TT) { return kBBHead + TT * (1 + kMaxBB + 8); }
 
 struct EvalArgs {
