@@ -158,10 +158,11 @@ def solve_flows(n_node, fr, to, b, p, slack, skip=-1, keep=None, pin=()):
     rows = np.concatenate([f, t, f, t])
     cols = np.concatenate([f, t, t, f])
     vals = np.concatenate([w, w, -w, -w])
-    L = sp.coo_matrix((vals, (rows, cols)), shape=(n_node, n_node)).tolil()
-    for v in pin:
-        L[v, v] = L[v, v] + 1.0
-    L = L.tocsc()
+    if pin:
+        rows = np.concatenate([rows, np.asarray(pin, dtype=rows.dtype)])
+        cols = np.concatenate([cols, np.asarray(pin, dtype=cols.dtype)])
+        vals = np.concatenate([vals, np.ones(len(pin))])
+    L = sp.coo_matrix((vals, (rows, cols)), shape=(n_node, n_node)).tocsc()
     idx = np.array([i for i in range(n_node) if i != slack])
     Lr = L[idx][:, idx]
     rhs = p[:, idx].T
