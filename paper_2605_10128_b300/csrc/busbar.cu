@@ -8,7 +8,8 @@
 //   F_l[t] = f'_l[t] - p_v[t] pi_s,l - sum_j N_{l r_j} z_j[t] - U_l . y[t].
 // This kernel evaluates F for every monitored row and keeps the running
 // maximum over the busbar outages per (row, timestep), on the CUDA cores in
-// FP32.  CTA = 128 monitored rows (thread = row) x G topologies; the records
+// FP32.  CTA = 128 monitored rows (thread = row) x G topologies (2; 4 measured 1.46x slower:
+// the kernel is latency bound and fewer registers buy occupancy); the records
 // are staged VB at a time in shared memory; the thread's U row and f' stay in
 // registers; N_{l r_j} and pi_s,l are read coalesced along the rows from
 // column-major FP32 tables.  Each CTA reduces its rows to one partial
@@ -221,10 +222,10 @@ void fill_busbar_args(tto_grid* g, EvalArgs& a) {
 
 int launch_busbar_sweep(const EvalArgs& a, cudaStream_t s) {
   switch (a.TT) {
-    case 1: return launch_tt<1, 4>(a, s);
-    case 2: return launch_tt<2, 4>(a, s);
-    case 4: return launch_tt<4, 4>(a, s);
-    case 8: return launch_tt<8, 4>(a, s);
+    case 1: return launch_tt<1, 2>(a, s);
+    case 2: return launch_tt<2, 2>(a, s);
+    case 4: return launch_tt<4, 2>(a, s);
+    case 8: return launch_tt<8, 2>(a, s);
     case 16: return launch_tt<16, 2>(a, s);
     case 24: return launch_tt<24, 1>(a, s);
     case 32: return launch_tt<32, 1>(a, s);
