@@ -327,6 +327,8 @@ def evaluate_multi(jobs, precision=PREC_FP32, fitness_kind=FIT_WORKLOAD, d_split
         g, topo = j[0], j[1].contiguous()
         ts = j[2] if len(j) > 2 else None
         B = int(topo.shape[0])
+        if topo.dtype != torch.int32 or not topo.is_cuda or topo.dim() != 2 or topo.shape[1] != g.genome_width:
+            raise TTOError(_lib.TTO_E_ARG, "each job's topo must be a CUDA int32 tensor [B][k_max + n_dslot]")
         dev = topo.device
         o = dict(fitness=torch.empty(B, dtype=torch.float32, device=dev),
                  desc=torch.empty(B, 2, dtype=torch.int32, device=dev),

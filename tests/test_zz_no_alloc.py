@@ -29,7 +29,9 @@ def _grids():
     b = make_grid(300, 450, 24, assets=(4, 8), T=3, b_dist=("loguniform", 2.0, 200.0), noise=0.1,
                   seed=3, k_max=3, name="rag")
     b = b.with_limits(limits_from_flows(dcflow.base_flows(b)[0], 5, seed=3))
-    return [(a, 256), (b, 37)]
+    c = config_grid("tto30", n_disc=8, n_dslot=2)  # genomes with disconnection slots
+    c = c.with_limits(a.limit)
+    return [(a, 256), (b, 37), (c, 64)]
 
 
 def _outputs(B, n_t, E_mon):
@@ -41,7 +43,7 @@ def _outputs(B, n_t, E_mon):
                 fmax=torch.full((B, n_t, E_mon), np.nan, dtype=torch.float32, device="cuda"))
 
 
-@pytest.mark.parametrize("which", [0, 1])
+@pytest.mark.parametrize("which", [0, 1, 2])
 def test_static_scratch_matches_evaluate_batch_twice(which):
     from paper_2605_10128_b300 import Grid, _lib
     sg, B = _grids()[which]
