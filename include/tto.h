@@ -51,7 +51,9 @@ extern "C" {
 #define TTO_FIT_WORKLOAD 0 /* fitness = -(lambda_o + max loading) */
 #define TTO_FIT_F1 1       /* fitness = lambda_f1 = -(lambda_o + 200 lambda_c0 + 50 lambda_c) */
 #define TTO_FIT_F2 2       /* fitness = lambda_f2 = lambda_f1 - Pi(lambda_b - lambda_b_pre): busbar outages too
-                              (call tto_grid_busbar_reference first, with the same timesteps) */
+                              (call tto_grid_busbar_reference first, with the same timesteps; the
+                              busbar workspace is allocated on first use, so make one such call
+                              outside stream capture before recording graphs) */
 
 typedef struct tto_grid tto_grid;
 typedef struct tto_archive tto_archive;
