@@ -417,4 +417,10 @@ def evaluate_parallel_outages(grid, genome, processes=8, **kw):
     r.update(fmax=fmax, n_islanded=n_isl, island_any=n_isl > 0, lambda_o=lam_o, lambda_c=lam_c,
              lambda_c0=lam_c0, maxload=maxload, fitness=-(lam_o + maxload),
              lambda_f1=-(lam_o + 200.0 * lam_c0 + 50.0 * lam_c))
+    if kw.get("want_energy"):
+        energy = np.full(O, np.nan)
+        for q in parts:
+            e = q["outage_energy"]
+            energy[~np.isnan(e)] = e[~np.isnan(e)]
+        r["outage_energy"] = energy
     return r

@@ -134,3 +134,33 @@ def test_epoch_export_snapshot_and_overlap():
     A.epoch_wait()
     np.testing.assert_array_equal(out2["fitness"].numpy(), f_now)
     np.testing.assert_array_equal(out2["genome"].numpy(), g_now)
+
+
+@pytest.mark.slow
+def test_tto10k_full_batch_worst_k_and_busbar_sampled():
+    """The 10000-bus workload in the benchmark's batch (8192 topologies): the
+    worst-20 export and the busbar outages of the whole batch on the GPU, one
+    non-islanded topology re-solved by the oracle over every outage and every
+    busbar node."""
+    from paper_2605_10128_b300 import Grid
+    from synth import CONFIGS
+    c = CONFIGS["tto10k"]
+    sg = _grid("tto10k", c["n_tight"])
+    g = Grid(sg)
+    topo = random_topologies(sg, c["batch"], seed=1)
+    t = torch.tensor(topo, dtype=torch.int32, device="cuda")
+    wk = g.worst_k(t, k=20, all_energy=True)
+    bb = g.busbar(t, bmax=True)
+    g.sync_status()
+    i = next(j for j in range(64) if dcflow.is_connected_uf(*dcflow.post_split_graph(sg, topo[j])[:3]))
+    r = dcflow.evaluate_parallel_outages(sg, topo[i], processes=parity.n_procs(), want_energy=True)
+    out = {"all_energy": wk["all_energy"][i:i + 1].cpu().numpy(), "outage": wk["outage"][i:i + 1].cpu().numpy(),
+           "energy": wk["energy"][i:i + 1].cpu().numpy()}
+    _check(sg, out, [0], [r["outage_energy"]], 20)
+    rb = dcflow.busbar_outages(sg, topo[i])
+    lim = sg.limit[sg.monitored.astype(np.int64)]
+    bm = bb["bmax"][i].cpu().numpy().astype(np.float64)
+    err = np.abs(bm - rb["bmax"]) / lim[None, :]
+    allowed = parity.TOL_FP32 + parity.FLOW_ULPS * np.abs(rb["bmax"]) / lim[None, :]
+    assert np.all(err <= allowed), float(err.max())
+    assert int(bb["n_island"][i]) == rb["n_islanded_busbar"]
