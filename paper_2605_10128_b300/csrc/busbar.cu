@@ -33,7 +33,9 @@ __global__ void __launch_bounds__(kBRows) busbar_sweep_kernel(EvalArgs a) {
   const int tid = threadIdx.x, tile = blockIdx.x;
   const int l = tile * kBRows + tid;
   const int b0 = blockIdx.y * G;
-  const int Ep = a.E_mon_pad, kRec = a.kRec;
+  const int Ep = a.E_mon_pad;
+  constexpr int kRec = bb_record_floats(TT), kRec4 = kRec / 4;  // records are whole float4s
+  static_assert(kRec % 4 == 0, "busbar records must be 16-byte multiples");
   float u[G][8], fpv[G][TT], m[G][TT];
 #pragma unroll
   for (int gi = 0; gi < G; ++gi) {
@@ -50,13 +52,14 @@ __global__ void __launch_bounds__(kBRows) busbar_sweep_kernel(EvalArgs a) {
   for (int v0 = 0; v0 < a.NB; v0 += kBVB) {
     const int nv = min(kBVB, a.NB - v0);
     __syncthreads();
-    for (int i = tid; i < G * kBVB * kRec; i += kBRows) {
-      const int gi = i / (kBVB * kRec), r = i % (kBVB * kRec), vv = r / kRec;
+    // a topology's records v0 .. v0 + nv - 1 are contiguous: float4 copies with
+    // compile-time divisors
+    for (int i = tid; i < G * kBVB * kRec4; i += kBRows) {
+      const int gi = i / (kBVB * kRec4), r = i % (kBVB * kRec4);
       const int bb = min(b0 + gi, a.B - 1);
-      float x = __int_as_float(-1);
-      if (vv < nv) x = a.bbrec[((size_t)bb * a.NB + v0 + vv) * kRec + r % kRec];
-      else if (r % kRec != 1) x = 0.f;  // slot past the end: |R'| = -1 marks it unused
-      srec[i] = x;
+      float4 x = make_float4(0.f, __int_as_float(-1), 0.f, 0.f);  // slot past the end: |R'| = -1 marks it unused
+      if (r < nv * kRec4) x = reinterpret_cast<const float4*>(a.bbrec + ((size_t)bb * a.NB + v0) * kRec)[r];
+      reinterpret_cast<float4*>(srec)[i] = x;
     }
     __syncthreads();
     for (int vv = 0; vv < nv; ++vv) {
@@ -125,7 +128,9 @@ __global__ void __launch_bounds__(kBRows) busbar_sweep_kernel(EvalArgs a) {
     float over = 0.f;
     if (l < a.E_mon && bb < a.B) {
       const float lim = a.lim[l];
-      for (int t = 0; t < a.n_t; ++t) {
+#pragma unroll
+      for (int t = 0; t < TT; ++t) {  // fixed trip count: m stays in registers
+        if (t >= a.n_t) break;
         over += fmaxf(m[gi][t] - lim, 0.f);
         if (a.bmax) a.bmax[((size_t)bb * a.n_t + t) * a.E_mon + l] = m[gi][t];
       }
@@ -162,6 +167,7 @@ __global__ void busbar_metrics_kernel(EvalArgs a, float* lambda_b, int32_t* n_is
 
 template <int TT, int G>
 int launch_tt(const EvalArgs& a, cudaStream_t s) {
+  if (a.kRec != bb_record_floats(TT)) return set_error(TTO_E_ARG, "busbar record size mismatch");
   const size_t smem = (size_t)G * kBVB * a.kRec * sizeof(float);
   static bool attr[64] = {};
   int dev = 0;

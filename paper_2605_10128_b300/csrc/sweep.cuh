@@ -12,7 +12,7 @@ namespace tto {
 // aligned rows, so timesteps load as float4)
 constexpr int kMaxBB = TTO_MAX_ASSETS - 1;
 constexpr int kBBHead = (2 + kMaxBB + 3) / 4 * 4;
-inline int bb_record_floats(int TT) { return kBBHead + TT * (1 + kMaxBB + 8); }
+constexpr int bb_record_floats(int TT) { return kBBHead + TT * (1 + kMaxBB + 8); }
 
 struct EvalArgs {
   // grid (device)
