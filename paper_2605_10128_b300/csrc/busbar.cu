@@ -24,29 +24,68 @@ namespace tto {
 namespace {
 
 constexpr int kBRows = 128;
-constexpr int kBVB = 8;  // busbar records staged per round
+constexpr int kBVB = 16;  // busbar records staged per round
 
-template <int TT, int G>
-__global__ void __launch_bounds__(kBRows) busbar_sweep_kernel(EvalArgs a) {
+// R adjacent monitored rows per thread (R = 1, 2 or 4): the per-record shared
+// loads (indices, p_v, z, y) serve R rows, and the N and pi reads become
+// R-wide vector loads.
+template <int R>
+struct RowVec;
+template <>
+struct RowVec<1> {
+  __device__ static void load(const float* p, float* x) { x[0] = *p; }
+  __device__ static void store(float* p, const float* x) { *p = x[0]; }
+};
+template <>
+struct RowVec<2> {
+  __device__ static void load(const float* p, float* x) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    x[0] = v.x;
+    x[1] = v.y;
+  }
+  __device__ static void store(float* p, const float* x) { *reinterpret_cast<float2*>(p) = make_float2(x[0], x[1]); }
+};
+template <>
+struct RowVec<4> {
+  __device__ static void load(const float* p, float* x) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    x[0] = v.x;
+    x[1] = v.y;
+    x[2] = v.z;
+    x[3] = v.w;
+  }
+  __device__ static void store(float* p, const float* x) {
+    *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+  }
+};
+
+template <int TT, int G, int R>
+__global__ void __launch_bounds__(kBRows / R) busbar_sweep_kernel(EvalArgs a) {
+  constexpr int kThreads = kBRows / R, kWarps = kThreads / 32;
   extern __shared__ __align__(16) float srec[];  // [G][kBVB][kRec]
-  __shared__ float sred[kBRows / 32][G];
+  __shared__ float sred[kWarps][G];
   const int tid = threadIdx.x, tile = blockIdx.x;
-  const int l = tile * kBRows + tid;
+  const int l = tile * kBRows + tid * R;  // rows l .. l + R - 1 (the padded row count is a multiple of 128)
   const int b0 = blockIdx.y * G;
   const int Ep = a.E_mon_pad;
   constexpr int kRec = bb_record_floats(TT), kRec4 = kRec / 4;  // records are whole float4s
   static_assert(kRec % 4 == 0, "busbar records must be 16-byte multiples");
-  float u[G][8], fpv[G][TT], m[G][TT];
+  float u[G][R][8], fpv[G][TT][R], m[G][TT][R];
 #pragma unroll
   for (int gi = 0; gi < G; ++gi) {
     const int bb = min(b0 + gi, a.B - 1);
-    const float* ur = a.U + ((size_t)bb * Ep + l) * 8;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) u[gi][i] = ur[i];
+    for (int r = 0; r < R; ++r) {
+      const float4* ur = reinterpret_cast<const float4*>(a.U + ((size_t)bb * Ep + l + r) * 8);
+      const float4 u0 = ur[0], u1 = ur[1];
+      u[gi][r][0] = u0.x, u[gi][r][1] = u0.y, u[gi][r][2] = u0.z, u[gi][r][3] = u0.w;
+      u[gi][r][4] = u1.x, u[gi][r][5] = u1.y, u[gi][r][6] = u1.z, u[gi][r][7] = u1.w;
+    }
 #pragma unroll
     for (int t = 0; t < TT; ++t) {
-      fpv[gi][t] = a.fp[((size_t)bb * TT + t) * Ep + l];
-      m[gi][t] = 0.f;
+      RowVec<R>::load(a.fp + ((size_t)bb * TT + t) * Ep + l, fpv[gi][t]);
+#pragma unroll
+      for (int r = 0; r < R; ++r) m[gi][t][r] = 0.f;
     }
   }
   for (int v0 = 0; v0 < a.NB; v0 += kBVB) {
@@ -54,11 +93,11 @@ __global__ void __launch_bounds__(kBRows) busbar_sweep_kernel(EvalArgs a) {
     __syncthreads();
     // a topology's records v0 .. v0 + nv - 1 are contiguous: float4 copies with
     // compile-time divisors
-    for (int i = tid; i < G * kBVB * kRec4; i += kBRows) {
-      const int gi = i / (kBVB * kRec4), r = i % (kBVB * kRec4);
+    for (int i = tid; i < G * kBVB * kRec4; i += kThreads) {
+      const int gi = i / (kBVB * kRec4), q = i % (kBVB * kRec4);
       const int bb = min(b0 + gi, a.B - 1);
       float4 x = make_float4(0.f, __int_as_float(-1), 0.f, 0.f);  // slot past the end: |R'| = -1 marks it unused
-      if (r < nv * kRec4) x = reinterpret_cast<const float4*>(a.bbrec + ((size_t)bb * a.NB + v0) * kRec)[r];
+      if (q < nv * kRec4) x = reinterpret_cast<const float4*>(a.bbrec + ((size_t)bb * a.NB + v0) * kRec)[q];
       reinterpret_cast<float4*>(srec)[i] = x;
     }
     __syncthreads();
@@ -69,55 +108,72 @@ __global__ void __launch_bounds__(kBRows) busbar_sweep_kernel(EvalArgs a) {
         const int* irec = reinterpret_cast<const int*>(rec);
         const int nr = irec[1];
         if (nr < 0) continue;
-        const float pi = a.Pm[(size_t)irec[0] * Ep + l];
+        float pi[R];
+        RowVec<R>::load(a.Pm + (size_t)irec[0] * Ep + l, pi);
         const float* pr = rec + kBBHead;
         const float* zr = pr + TT;
         const float* yr = zr + kMaxBB * TT;
-        float F[TT];
+        float F[TT][R];
         if constexpr (TT % 4 == 0) {  // records are 16-byte aligned: four timesteps per load
 #pragma unroll
           for (int t4 = 0; t4 < TT; t4 += 4) {
             const float4 p4 = *reinterpret_cast<const float4*>(pr + t4);
-            F[t4] = fmaf(-p4.x, pi, fpv[gi][t4]);
-            F[t4 + 1] = fmaf(-p4.y, pi, fpv[gi][t4 + 1]);
-            F[t4 + 2] = fmaf(-p4.z, pi, fpv[gi][t4 + 2]);
-            F[t4 + 3] = fmaf(-p4.w, pi, fpv[gi][t4 + 3]);
+            const float pv[4] = {p4.x, p4.y, p4.z, p4.w};
+#pragma unroll
+            for (int d = 0; d < 4; ++d)
+#pragma unroll
+              for (int r = 0; r < R; ++r) F[t4 + d][r] = fmaf(-pv[d], pi[r], fpv[gi][t4 + d][r]);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
               const float4 y4 = *reinterpret_cast<const float4*>(yr + i * TT + t4);
-              F[t4] = fmaf(-u[gi][i], y4.x, F[t4]);
-              F[t4 + 1] = fmaf(-u[gi][i], y4.y, F[t4 + 1]);
-              F[t4 + 2] = fmaf(-u[gi][i], y4.z, F[t4 + 2]);
-              F[t4 + 3] = fmaf(-u[gi][i], y4.w, F[t4 + 3]);
+              const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+              for (int d = 0; d < 4; ++d)
+#pragma unroll
+                for (int r = 0; r < R; ++r) F[t4 + d][r] = fmaf(-u[gi][r][i], yv[d], F[t4 + d][r]);
             }
           }
           for (int jj = 0; jj < nr; ++jj) {
-            const float n = a.Nswm[(size_t)irec[2 + jj] * Ep + l];
+            float n[R];
+            RowVec<R>::load(a.Nswm + (size_t)irec[2 + jj] * Ep + l, n);
 #pragma unroll
             for (int t4 = 0; t4 < TT; t4 += 4) {
               const float4 z4 = *reinterpret_cast<const float4*>(zr + jj * TT + t4);
-              F[t4] = fmaf(-n, z4.x, F[t4]);
-              F[t4 + 1] = fmaf(-n, z4.y, F[t4 + 1]);
-              F[t4 + 2] = fmaf(-n, z4.z, F[t4 + 2]);
-              F[t4 + 3] = fmaf(-n, z4.w, F[t4 + 3]);
+              const float zv[4] = {z4.x, z4.y, z4.z, z4.w};
+#pragma unroll
+              for (int d = 0; d < 4; ++d)
+#pragma unroll
+                for (int r = 0; r < R; ++r) F[t4 + d][r] = fmaf(-n[r], zv[d], F[t4 + d][r]);
             }
           }
         } else {
 #pragma unroll
           for (int t = 0; t < TT; ++t) {
-            float f = fmaf(-pr[t], pi, fpv[gi][t]);
+            const float pt = pr[t];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) f = fmaf(-u[gi][i], yr[i * TT + t], f);
-            F[t] = f;
+            for (int r = 0; r < R; ++r) F[t][r] = fmaf(-pt, pi[r], fpv[gi][t][r]);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const float yt = yr[i * TT + t];
+#pragma unroll
+              for (int r = 0; r < R; ++r) F[t][r] = fmaf(-u[gi][r][i], yt, F[t][r]);
+            }
           }
           for (int jj = 0; jj < nr; ++jj) {
-            const float n = a.Nswm[(size_t)irec[2 + jj] * Ep + l];
+            float n[R];
+            RowVec<R>::load(a.Nswm + (size_t)irec[2 + jj] * Ep + l, n);
 #pragma unroll
-            for (int t = 0; t < TT; ++t) F[t] = fmaf(-n, zr[jj * TT + t], F[t]);
+            for (int t = 0; t < TT; ++t) {
+              const float zt = zr[jj * TT + t];
+#pragma unroll
+              for (int r = 0; r < R; ++r) F[t][r] = fmaf(-n[r], zt, F[t][r]);
+            }
           }
         }
 #pragma unroll
-        for (int t = 0; t < TT; ++t) m[gi][t] = fmaxf(m[gi][t], fabsf(F[t]));
+        for (int t = 0; t < TT; ++t)
+#pragma unroll
+          for (int r = 0; r < R; ++r) m[gi][t][r] = fmaxf(m[gi][t][r], fabsf(F[t][r]));
       }
     }
   }
@@ -126,13 +182,23 @@ __global__ void __launch_bounds__(kBRows) busbar_sweep_kernel(EvalArgs a) {
   for (int gi = 0; gi < G; ++gi) {
     const int bb = b0 + gi;
     float over = 0.f;
-    if (l < a.E_mon && bb < a.B) {
-      const float lim = a.lim[l];
+    if (bb < a.B) {
 #pragma unroll
       for (int t = 0; t < TT; ++t) {  // fixed trip count: m stays in registers
         if (t >= a.n_t) break;
-        over += fmaxf(m[gi][t] - lim, 0.f);
-        if (a.bmax) a.bmax[((size_t)bb * a.n_t + t) * a.E_mon + l] = m[gi][t];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (l + r < a.E_mon) over += fmaxf(m[gi][t][r] - a.lim[l + r], 0.f);
+        if (a.bmax) {
+          float* out = a.bmax + ((size_t)bb * a.n_t + t) * a.E_mon + l;
+          if (R > 1 && l + R - 1 < a.E_mon && a.E_mon % R == 0 && (reinterpret_cast<uintptr_t>(a.bmax) & (4 * R - 1)) == 0) {
+            RowVec<R>::store(out, m[gi][t]);
+          } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+              if (l + r < a.E_mon) out[r] = m[gi][t][r];
+          }
+        }
       }
     }
 #pragma unroll
@@ -142,7 +208,7 @@ __global__ void __launch_bounds__(kBRows) busbar_sweep_kernel(EvalArgs a) {
   __syncthreads();
   if (tid < G && b0 + tid < a.B) {
     float s = 0.f;
-    for (int w = 0; w < kBRows / 32; ++w) s += sred[w][tid];
+    for (int w = 0; w < kWarps; ++w) s += sred[w][tid];
     a.bbpart[(size_t)(b0 + tid) * a.n_rowtiles + tile] = s;
   }
 }
@@ -165,7 +231,7 @@ __global__ void busbar_metrics_kernel(EvalArgs a, float* lambda_b, int32_t* n_is
   if (n_island) n_island[b] = inf.island_base ? -1 : inf.nbisl;
 }
 
-template <int TT, int G>
+template <int TT, int G, int R>
 int launch_tt(const EvalArgs& a, cudaStream_t s) {
   if (a.kRec != bb_record_floats(TT)) return set_error(TTO_E_ARG, "busbar record size mismatch");
   const size_t smem = (size_t)G * kBVB * a.kRec * sizeof(float);
@@ -173,12 +239,12 @@ int launch_tt(const EvalArgs& a, cudaStream_t s) {
   int dev = 0;
   TTO_CUDA_TRY(cudaGetDevice(&dev));
   if (dev >= 0 && dev < 64 && !attr[dev]) {
-    TTO_CUDA_TRY(cudaFuncSetAttribute(busbar_sweep_kernel<TT, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    TTO_CUDA_TRY(cudaFuncSetAttribute(busbar_sweep_kernel<TT, G, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
     attr[dev] = true;
   }
   const dim3 grid((unsigned)(a.E_mon_pad / kBRows), (unsigned)((a.B + G - 1) / G));
-  busbar_sweep_kernel<TT, G><<<grid, kBRows, smem, s>>>(a);
+  busbar_sweep_kernel<TT, G, R><<<grid, kBRows / R, smem, s>>>(a);
   TTO_CUDA_TRY(cudaGetLastError());
   return TTO_OK;
 }
@@ -228,13 +294,13 @@ void fill_busbar_args(tto_grid* g, EvalArgs& a) {
 
 int launch_busbar_sweep(const EvalArgs& a, cudaStream_t s) {
   switch (a.TT) {
-    case 1: return launch_tt<1, 2>(a, s);
-    case 2: return launch_tt<2, 2>(a, s);
-    case 4: return launch_tt<4, 2>(a, s);
-    case 8: return launch_tt<8, 2>(a, s);
-    case 16: return launch_tt<16, 2>(a, s);
-    case 24: return launch_tt<24, 1>(a, s);
-    case 32: return launch_tt<32, 1>(a, s);
+    case 1: return launch_tt<1, 1, 2>(a, s);
+    case 2: return launch_tt<2, 1, 2>(a, s);
+    case 4: return launch_tt<4, 1, 2>(a, s);
+    case 8: return launch_tt<8, 1, 2>(a, s);
+    case 16: return launch_tt<16, 2, 1>(a, s);
+    case 24: return launch_tt<24, 1, 1>(a, s);
+    case 32: return launch_tt<32, 1, 1>(a, s);
     default: return set_error(TTO_E_ARG, "unsupported timestep count %d", a.TT);
   }
 }
