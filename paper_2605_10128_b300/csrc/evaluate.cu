@@ -116,11 +116,6 @@ __device__ void busbar_setup(const EvalArgs& a, int b, int k, int ns, const int*
     float* prec = rec + kBBHead;
     float* zrec = prec + TT;
     float* yrec = zrec + kMaxBB * TT;
-    double pv[TTO_MAX_T];
-    for (int t = 0; t < TT; ++t) {
-      pv[t] = (inj && t < nt) ? a.p[(size_t)a.tsel[t] * a.n_bus + bus] : 0.0;
-      prec[t] = (float)pv[t];
-    }
     double kap[TTO_MAX_K];
     for (int i = 0; i < k; ++i) {
       double st = 0.0;
@@ -128,50 +123,47 @@ __device__ void busbar_setup(const EvalArgs& a, int b, int k, int ns, const int*
       kap[i] = (side == 1 && i == js ? 1.0 : 0.0) - st;
     }
     const int nrp = nrv - 1;
-    double W[kMaxBB][TTO_MAX_K], U[kMaxBB][TTO_MAX_K], Q[kMaxBB][kMaxBB], rhs[kMaxBB][TTO_MAX_T];
-    for (int jj = 0; jj < nrp; ++jj) {
-      const int r = R[1 + jj];
+    // Per branch r_j of R': its W row, 1 / b_r, rho_r, and row j of
+    // Q = D^-1 N'_{R'R'} (lower triangle, packed by rows: Q(i, j) at
+    // i (i + 1) / 2 + j) from the branch's U row, which is not kept.
+    double W[kMaxBB][TTO_MAX_K], Q[kMaxBB * (kMaxBB + 1) / 2], rho[kMaxBB], ib[kMaxBB];
+    for (int ii = 0; ii < nrp; ++ii) {
+      const int r = R[1 + ii];
+      ib[ii] = 1.0 / a.b[r];
       for (int i = 0; i < k; ++i) {
         double w = 0.0;
         for (int q = s_slot[i]; q < s_slot[i + 1]; ++q) w += s_coef[q] * s_col[q][r];
-        W[jj][i] = w;
+        W[ii][i] = w;
       }
-      double rho = a.Pst[(size_t)s * a.E + r];
+      double U[TTO_MAX_K], rh = a.Pst[(size_t)s * a.E + r];
       for (int i = 0; i < k; ++i) {
         double u = 0.0;
-        for (int i2 = 0; i2 < k; ++i2) u += W[jj][i2] * s_Ki[i2][i];
-        U[jj][i] = u;
-        rho += u * kap[i];
+        for (int i2 = 0; i2 < k; ++i2) u += W[ii][i2] * s_Ki[i2][i];
+        U[i] = u;
+        rh += u * kap[i];
       }
-      const double br = a.b[r];
-      for (int t = 0; t < TT; ++t) {
-        double f = 0.0;
-        if (t < nt) {
-          f = a.f0[(size_t)a.tsel[t] * a.E + r];
-          for (int i = 0; i < k; ++i) f += W[jj][i] * s_psi[t][i];
-        }
-        rhs[jj][t] = (f - pv[t] * rho) / br;
+      rho[ii] = rh;
+      for (int jj = 0; jj <= ii; ++jj) {
+        double uv = 0.0;
+        for (int i = 0; i < k; ++i) uv += U[i] * W[jj][i];
+        Q[ii * (ii + 1) / 2 + jj] = (a.Nsw[(size_t)a.swcol[R[1 + jj]] * a.E + r] - uv * ib[jj]) * ib[ii];
       }
     }
-    // Q = D^-1 N'_{R'R'}, lower triangle
-    for (int ii = 0; ii < nrp; ++ii)
-      for (int jj = 0; jj <= ii; ++jj) {
-        const int ri = R[1 + ii], rj = R[1 + jj];
-        double uv = 0.0;
-        for (int i = 0; i < k; ++i) uv += U[ii][i] * W[jj][i];
-        Q[ii][jj] = (a.Nsw[(size_t)a.swcol[rj] * a.E + ri] - uv / a.b[rj]) / a.b[ri];
-      }
-    // LDL^T in place (L below the diagonal, D on it)
+    // LDL^T in place (L below the diagonal, D on it); idg = 1 / D
     bool isl = false;
+    double idg[kMaxBB];
     for (int j = 0; j < nrp && !isl; ++j) {
-      double dj = Q[j][j];
-      for (int q = 0; q < j; ++q) dj -= Q[j][q] * Q[j][q] * Q[q][q];
+      const int jr = j * (j + 1) / 2;
+      double dj = Q[jr + j];
+      for (int q = 0; q < j; ++q) dj -= Q[jr + q] * Q[jr + q] * Q[q * (q + 1) / 2 + q];
       if (!(dj * a.b[R[1 + j]] > kIslandTol)) isl = true;
-      Q[j][j] = dj;
+      Q[jr + j] = dj;
+      idg[j] = 1.0 / dj;
       for (int i = j + 1; i < nrp && !isl; ++i) {
-        double x = Q[i][j];
-        for (int q = 0; q < j; ++q) x -= Q[i][q] * Q[j][q] * Q[q][q];
-        Q[i][j] = x / dj;
+        const int ir = i * (i + 1) / 2;
+        double x = Q[ir + j];
+        for (int q = 0; q < j; ++q) x -= Q[ir + q] * Q[jr + q] * Q[q * (q + 1) / 2 + q];
+        Q[ir + j] = x * idg[j];
       }
     }
     if (isl) {
@@ -179,25 +171,35 @@ __device__ void busbar_setup(const EvalArgs& a, int b, int k, int ns, const int*
       atomicAdd(n_island, 1);
       continue;
     }
+    // per timestep: rhs_j = (f'_{r_j} - p_v rho_j) / b_j, z from L D L^T, then y
     for (int t = 0; t < TT; ++t) {
+      const double pvt = (inj && t < nt) ? a.p[(size_t)a.tsel[t] * a.n_bus + bus] : 0.0;
+      prec[t] = (float)pvt;
       double z[kMaxBB];
       for (int i = 0; i < nrp; ++i) {
-        double x = rhs[i][t];
-        for (int q = 0; q < i; ++q) x -= Q[i][q] * z[q];
+        double f = 0.0;
+        if (t < nt) {
+          f = a.f0[(size_t)a.tsel[t] * a.E + R[1 + i]];
+          for (int q = 0; q < k; ++q) f += W[i][q] * s_psi[t][q];
+        }
+        const int ir = i * (i + 1) / 2;
+        double x = (f - pvt * rho[i]) * ib[i];
+        for (int q = 0; q < i; ++q) x -= Q[ir + q] * z[q];
         z[i] = x;
       }
-      for (int i = 0; i < nrp; ++i) z[i] /= Q[i][i];
+      for (int i = 0; i < nrp; ++i) z[i] *= idg[i];
       for (int i = nrp - 1; i >= 0; --i) {
         double x = z[i];
-        for (int q = i + 1; q < nrp; ++q) x -= Q[q][i] * z[q];
+        for (int q = i + 1; q < nrp; ++q) x -= Q[q * (q + 1) / 2 + i] * z[q];
         z[i] = x;
       }
       for (int jj = 0; jj < kMaxBB; ++jj) zrec[jj * TT + t] = jj < nrp ? (float)z[jj] : 0.f;
+      for (int jj = 0; jj < nrp; ++jj) z[jj] *= ib[jj];  // z_j / b_j for y
       for (int i = 0; i < TTO_MAX_K; ++i) {
         double y = 0.0;
         if (i < k) {
-          y = pv[t] * kap[i];
-          for (int jj = 0; jj < nrp; ++jj) y -= z[jj] * W[jj][i] / a.b[R[1 + jj]];
+          y = pvt * kap[i];
+          for (int jj = 0; jj < nrp; ++jj) y -= z[jj] * W[jj][i];
         }
         yrec[i * TT + t] = (float)y;
       }
