@@ -64,9 +64,12 @@ __global__ void __launch_bounds__(kBRows / R) busbar_sweep_kernel(EvalArgs a) {
   constexpr int kThreads = kBRows / R, kWarps = kThreads / 32;
   extern __shared__ __align__(16) float srec[];  // [G][kBVB][kRec]
   __shared__ float sred[kWarps][G];
-  const int tid = threadIdx.x, tile = blockIdx.x;
+  // topology groups vary fastest along the grid: the CTAs resident at one time
+  // share a row tile, so the N and pi_s segments that their records name
+  // (mostly the same stations in every topology) are re-read from L1 and L2
+  const int tid = threadIdx.x, tile = blockIdx.y;
   const int l = tile * kBRows + tid * R;  // rows l .. l + R - 1 (the padded row count is a multiple of 128)
-  const int b0 = blockIdx.y * G;
+  const int b0 = blockIdx.x * G;
   const int Ep = a.E_mon_pad;
   constexpr int kRec = bb_record_floats(TT), kRec4 = kRec / 4;  // records are whole float4s
   static_assert(kRec % 4 == 0, "busbar records must be 16-byte multiples");
@@ -243,7 +246,8 @@ int launch_tt(const EvalArgs& a, cudaStream_t s) {
                                       (int)smem));
     attr[dev] = true;
   }
-  const dim3 grid((unsigned)(a.E_mon_pad / kBRows), (unsigned)((a.B + G - 1) / G));
+  if (a.E_mon_pad / kBRows > 65535) return set_error(TTO_E_ARG, "too many monitored rows for the busbar sweep");
+  const dim3 grid((unsigned)((a.B + G - 1) / G), (unsigned)(a.E_mon_pad / kBRows));
   busbar_sweep_kernel<TT, G, R><<<grid, kBRows / R, smem, s>>>(a);
   TTO_CUDA_TRY(cudaGetLastError());
   return TTO_OK;
