@@ -137,6 +137,7 @@ __global__ void __launch_bounds__(kRowTile) sweep_fp32_kernel(EvalArgs a) {
 
 template <int TT, int KP, int G>
 static int launch_fp32_g(const EvalArgs& a, cudaStream_t s) {
+  if ((a.B + G - 1) / G > 65535) return set_error(TTO_E_ARG, "batch too large for one FP32 sweep launch");
   dim3 grid(a.n_rowtiles, (a.B + G - 1) / G);
   sweep_fp32_kernel<TT, G, KP><<<grid, kRowTile, 0, s>>>(a);
   TTO_CUDA_TRY(cudaGetLastError());

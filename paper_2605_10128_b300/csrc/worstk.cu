@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(256) worst_k_kernel(const float* energy, int O
 
 template <int TT>
 int launch_energy(const EvalArgs& a, float* energy, const uint8_t* use, cudaStream_t s) {
+  if ((a.B + kEG - 1) / kEG > 65535) return set_error(TTO_E_ARG, "at most %d topologies per worst-k call", 65535 * kEG);
   const dim3 grid((unsigned)((a.O_pad + kEThreads - 1) / kEThreads), (unsigned)((a.B + kEG - 1) / kEG));
   outage_energy_kernel<TT><<<grid, kEThreads, 0, s>>>(a, energy, use);
   TTO_CUDA_TRY(cudaGetLastError());
