@@ -111,3 +111,43 @@ def test_lambda_f2_fitness():
     g.set_limits(sg.limit * 1.01)
     with pytest.raises(TTOError):
         g.evaluate(t, fitness_kind=FIT_F2)
+
+
+@pytest.mark.parametrize("T", [2, 5, 24, 32])
+def test_busbar_outages_every_timestep_shape(T):
+    """Timestep counts that pad to 2, 8 (5 real), 24 and 32: the kernels that
+    take two rows per thread, with paired bmax stores, and the one-row kernels
+    of long horizons."""
+    from paper_2605_10128_b300 import Grid
+    from synth import make_grid
+    sg = make_grid(120, 180, 10, assets=(4, 8), T=T, b_dist=("loguniform", 2.0, 200.0), noise=0.1,
+                   seed=40 + T, k_max=4, name="busbar_T")
+    sg = sg.with_limits(limits_from_flows(dcflow.base_flows(sg)[0], 3, seed=T))
+    g = Grid(sg)
+    topo = random_topologies(sg, 24, seed=T)
+    idx = list(range(len(topo)))
+    assert _check(sg, _run(g, topo), idx, _oracle(sg, topo, idx)) > 10
+
+
+def test_busbar_timestep_subset_and_empty_batch():
+    """A reordered subset of the timesteps (3 of 24, padded to 4) against the
+    oracle on the same subset, and an empty batch."""
+    from paper_2605_10128_b300 import Grid
+    from synth import make_grid
+    sg = make_grid(120, 180, 10, assets=(4, 8), T=24, b_dist=("loguniform", 2.0, 200.0), noise=0.1,
+                   seed=64, k_max=4, name="busbar_T")
+    sg = sg.with_limits(limits_from_flows(dcflow.base_flows(sg)[0], 3, seed=1))
+    g = Grid(sg)
+    topo = random_topologies(sg, 24, seed=3)
+    ts = [23, 0, 7]
+    out = g.busbar(torch.tensor(topo, dtype=torch.int32, device="cuda"), timesteps=ts, bmax=True)
+    g.sync_status()
+    out = {k: v.cpu().numpy() for k, v in out.items()}
+    assert out["bmax"].shape == (24, 3, len(sg.monitored))
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(parity.n_procs(), 8)) as pool:
+        refs = pool.starmap(dcflow.busbar_outages, [(sg, topo[i], ts) for i in range(24)])
+    assert _check(sg, out, list(range(24)), refs) > 10
+    empty = g.busbar(torch.empty((0, sg.genome_width), dtype=torch.int32, device="cuda"), bmax=True)
+    g.sync_status()
+    assert empty["lambda_b"].shape == (0,) and empty["bmax"].shape == (0, sg.T, len(sg.monitored))
