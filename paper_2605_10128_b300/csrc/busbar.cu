@@ -8,12 +8,14 @@
 //   F_l[t] = f'_l[t] - p_v[t] pi_s,l - sum_j N_{l r_j} z_j[t] - U_l . y[t].
 // This kernel evaluates F for every monitored row and keeps the running
 // maximum over the busbar outages per (row, timestep), on the CUDA cores in
-// FP32.  CTA = 128 monitored rows (thread = row) x G topologies (2; 4 measured 1.46x slower:
-// the kernel is latency bound and fewer registers buy occupancy); the records
-// are staged VB at a time in shared memory; the thread's U row and f' stay in
-// registers; N_{l r_j} and pi_s,l are read coalesced along the rows from
-// column-major FP32 tables.  Each CTA reduces its rows to one partial
-// lambda_b per topology in a fixed order (no atomics).
+// FP32.  A thread takes R adjacent rows of G topologies (R = 2, G = 1 up to 8
+// timesteps: CTA = 64 threads = 128 rows x 1 topology).  The records are
+// staged kBVB at a time in shared memory as float4s, and each record's
+// broadcast loads (indices, p_v, z, y) then serve the thread's R rows.  The
+// thread's U rows and f' stay in registers.  N_{l r_j} and pi_s,l are read
+// R rows at a time from column-major FP32 tables, coalesced along the rows.
+// Each CTA reduces its rows to one partial lambda_b per topology in a fixed
+// order (no atomics).
 #include <math.h>
 
 #include "sweep.cuh"
@@ -26,7 +28,7 @@ namespace {
 constexpr int kBRows = 128;
 constexpr int kBVB = 16;  // busbar records staged per round
 
-// R adjacent monitored rows per thread (R = 1, 2 or 4): the per-record shared
+// R adjacent monitored rows per thread (R = 1 or 2): the per-record shared
 // loads (indices, p_v, z, y) serve R rows, and the N and pi reads become
 // R-wide vector loads.
 template <int R>
@@ -44,19 +46,6 @@ struct RowVec<2> {
     x[1] = v.y;
   }
   __device__ static void store(float* p, const float* x) { *reinterpret_cast<float2*>(p) = make_float2(x[0], x[1]); }
-};
-template <>
-struct RowVec<4> {
-  __device__ static void load(const float* p, float* x) {
-    const float4 v = *reinterpret_cast<const float4*>(p);
-    x[0] = v.x;
-    x[1] = v.y;
-    x[2] = v.z;
-    x[3] = v.w;
-  }
-  __device__ static void store(float* p, const float* x) {
-    *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
-  }
 };
 
 template <int TT, int G, int R>
