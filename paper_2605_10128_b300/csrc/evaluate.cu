@@ -129,7 +129,7 @@ __device__ void busbar_setup(const EvalArgs& a, int b, int k, int ns, const int*
     double W[kMaxBB][TTO_MAX_K], Q[kMaxBB * (kMaxBB + 1) / 2], rho[kMaxBB], ib[kMaxBB];
     for (int ii = 0; ii < nrp; ++ii) {
       const int r = R[1 + ii];
-      ib[ii] = 1.0 / a.b[r];
+      ib[ii] = a.invb[r];
       for (int i = 0; i < k; ++i) {
         double w = 0.0;
         for (int q = s_slot[i]; q < s_slot[i + 1]; ++q) w += s_coef[q] * s_col[q][r];
@@ -225,6 +225,7 @@ __device__ __forceinline__ void split_update_body(const EvalArgs& a) {
   __shared__ int s_injbus[TTO_MAX_K];
   __shared__ double s_K[TTO_MAX_K][TTO_MAX_K];
   __shared__ double s_Ki[TTO_MAX_K][TTO_MAX_K];
+  __shared__ double s_Ki2[TTO_MAX_K][TTO_MAX_K];  // Ki_ji + Ki_ij for i > j
   __shared__ float s_Kif[TTO_MAX_K][TTO_MAX_K];  // FP32 copy for the monitored rows' U
   __shared__ double s_rhs[TTO_MAX_T][TTO_MAX_K];
   __shared__ double s_psi[TTO_MAX_T][TTO_MAX_K];
@@ -393,6 +394,8 @@ __device__ __forceinline__ void split_update_body(const EvalArgs& a) {
           s_Kif[i][c] = (float)x[i];
         }
       }
+      for (int j = 0; j < k; ++j)  // off-diagonal pair sums for the outage rows' W^T K^-1 W
+        for (int i = j + 1; i < k; ++i) s_Ki2[j][i] = s_Ki[j][i] + s_Ki[i][j];
     }
   }
   __syncthreads();
@@ -502,14 +505,15 @@ __device__ __forceinline__ void split_update_body(const EvalArgs& a) {
       W[j] = w;
     }
     // N'_cc = N_cc - U_c . V_c = N_cc - (W^T K^-1 W) / b_c.  FP64 division is
-    // a long instruction sequence on this part, so each row divides twice
-    // (1 / b_c, 1 / N'_cc) and multiplies elsewhere.
-    const double inv_be = 1.0 / a.b[e];
+    // a long instruction sequence on this part: 1 / b_c comes from the grid's
+    // table, each row divides once (1 / N'_cc) and multiplies elsewhere.
+    // W^T K^-1 W = sum_j W_j (Ki_jj W_j + sum_{i>j} (Ki_ji + Ki_ij) W_i).
+    const double inv_be = a.invb[e];
     double q = 0.0;
-    for (int jj = 0; jj < k; ++jj) {
-      double uu = 0.0;
-      for (int j = 0; j < k; ++j) uu += W[j] * s_Ki[j][jj];
-      q += uu * W[jj];
+    for (int j = 0; j < k; ++j) {
+      double uu = s_Ki[j][j] * W[j];
+      for (int i = j + 1; i < k; ++i) uu += s_Ki2[j][i] * W[i];
+      q += uu * W[j];
     }
     const double npcc = a.Ncc[cr] - q * inv_be;
     for (int jj = 0; jj < TTO_MAX_K; ++jj) {
@@ -712,6 +716,7 @@ int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, 
   a.f0 = g->d_f0;
   a.p = g->d_p;
   a.b = g->d_b;
+  a.invb = g->d_invb;
   a.lim = g->d_lim;
   a.mon = g->d_mon;
   a.out = g->d_out;

@@ -110,6 +110,7 @@ extern "C" int tto_evaluate_batch_static(tto_grid* g, const int32_t* topo, int32
   a.f0 = g->d_f0;
   a.p = g->d_p;
   a.b = g->d_b;
+  a.invb = g->d_invb;
   a.lim = g->d_lim;
   a.mon = g->d_mon;
   a.out = g->d_out;

@@ -24,6 +24,7 @@ struct EvalArgs {
   const double* f0;
   const double* p;
   const double* b;
+  const double* invb;  // 1 / b
   const float* lim;
   const int* mon;
   const int* out;

@@ -90,6 +90,7 @@ struct tto_grid {
   double* d_f0 = nullptr;      // [T][E] base flows
   double* d_p = nullptr;       // [T][n_bus]
   double* d_b = nullptr;       // [E]
+  double* d_invb = nullptr;    // [E] 1 / b (IEEE division, the same bits as on the device)
   float* d_lim = nullptr;      // [E_mon] limits of monitored branches
   int* d_mon = nullptr;        // [E_mon]
   int* d_out = nullptr;        // [O]
