@@ -93,6 +93,9 @@ __global__ void __launch_bounds__(kBRows / R) busbar_sweep_kernel(EvalArgs a) {
       reinterpret_cast<float4*>(srec)[i] = x;
     }
     __syncthreads();
+    // unrolled so that later records' gathers of N and pi_s are issued while
+    // earlier records' arithmetic runs (the loop is bound by their latency)
+#pragma unroll 4
     for (int vv = 0; vv < nv; ++vv) {
 #pragma unroll
       for (int gi = 0; gi < G; ++gi) {
