@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(kEThreads) outage_energy_kernel(EvalArgs a, fl
     }
     if (tid < kERows) sL[tid] = tid < nr ? a.lim[l0 + tid] : 1.f;
     __syncthreads();
+#pragma unroll 4  // several rows' N loads in flight at once
     for (int r = 0; r < nr; ++r) {
       const float n = a.Nmo[(size_t)(l0 + r) * Op + cc];
       const float lim = sL[r];
