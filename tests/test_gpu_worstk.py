@@ -83,6 +83,24 @@ def test_worst_k_tto2k_sampled():
     _check(sg, out, idx, _energies(sg, topo, idx), 20)
 
 
+@pytest.mark.parametrize("T", [2, 5, 24, 32])
+def test_worst_k_every_timestep_shape(T):
+    """Timestep counts that pad to 2, 8 (5 real), 24 and 32 in the energy
+    kernel, whose row loop is unrolled."""
+    from paper_2605_10128_b300 import Grid
+    from synth import make_grid
+    sg = make_grid(120, 180, 10, assets=(4, 8), T=T, b_dist=("loguniform", 2.0, 200.0), noise=0.1,
+                   seed=50 + T, k_max=4, name="worstk_T")
+    sg = sg.with_limits(limits_from_flows(dcflow.base_flows(sg)[0], 3, seed=T))
+    g = Grid(sg)
+    topo = random_topologies(sg, 24, seed=T)
+    out = g.worst_k(torch.tensor(topo, dtype=torch.int32, device="cuda"), k=20, all_energy=True)
+    g.sync_status()
+    out = {k_: v.cpu().numpy() for k_, v in out.items()}
+    idx = list(range(len(topo)))
+    _check(sg, out, idx, _energies(sg, topo, idx), 20)
+
+
 def test_worst_k_validation_and_large_k():
     from paper_2605_10128_b300 import Grid, TTOError
     sg = _grid("tto30", 5)
