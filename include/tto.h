@@ -292,7 +292,8 @@ int tto_grid_busbar_reference(tto_grid* g, const int32_t* timesteps, int32_t n_t
  * [n][k] (NaN with -1).  An outage that islands the topology, or whose branch
  * the topology opened, never qualifies (its all_energy entry is NaN); a
  * topology that islands the grid yields -1 throughout.  all_energy (device
- * float [n][n_outage], may be NULL) receives every E_c.  1 <= k <= 1024.
+ * float [n][n_outage], may be NULL) receives every E_c.  1 <= k <= 1024 and
+ * n <= 262140 (TTO_E_ARG otherwise).
  * Shares the evaluation workspace with the other calls on this grid.
  * Asynchronous on stream; genome errors as for tto_evaluate_batch. */
 int tto_worst_k(tto_grid* g, const int32_t* topo, int32_t n, const int32_t* timesteps, int32_t n_t, int32_t k,
