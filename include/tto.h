@@ -180,7 +180,10 @@ int tto_grid_reserve(tto_grid* g, int32_t max_batch, int32_t n_t);
  * busbar B keeps only opened branches islands the grid.
  * Asynchronous on stream.  A genome with an unknown action or disconnection
  * id, a repeated station or a repeated disconnection is reported by the
- * device; read it with tto_grid_sync_status. */
+ * device; read it with tto_grid_sync_status.  With TTO_PREC_FP32 one call
+ * takes at most 65535 x G topologies (G = 8, 4, 2, 1 up to 4, 8, 16, 32
+ * timesteps, halved by the autotuner's shape 1); larger batches return
+ * TTO_E_ARG. */
 int tto_evaluate_batch(tto_grid* g, const int32_t* topo, int32_t B, const int32_t* timesteps,
                        int32_t n_t, const tto_eval_opts* opts, float* fitness, int32_t* desc,
                        int32_t* cell, uint8_t* island, float* metrics, float* fmax, void* stream);
