@@ -417,3 +417,99 @@ def test_busbar_outages_kirchhoff_and_articulation_points(seed):
             F = dcflow.solve_flows(n_node, fr, to, g.b, pb, g.slack, keep=keep, pin=(v,))
             assert np.all(F[:, ~keep] == 0.0)
             _kcl_kvl(n_node, fr, to, g.b, pb, g.slack, F, opened=list(np.flatnonzero(~keep)))
+
+
+# ------------------------------------------------------------- lambda_f2 and the lambda_d cell
+def _triangle_topology(g, d, name):
+    """Genome of a named triangle topology of the golden fixture, on the
+    triangle extended with the disconnection set [0, 1, 2] and two slots."""
+    gd = _with_disc(g, [0, 1, 2], 2)
+    if name.startswith("mask"):
+        return gd, [action_of(g, 0, int(name.split()[1])), -1, -1]
+    if name == "open 0->2":
+        return gd, [-1, 2, -1]
+    raise KeyError(name)
+
+
+def test_lambda_f2_three_bus_hand_values():
+    """lambda_f2 with a nonzero busbar penalty Pi(lambda_b - lambda_b^pre) and
+    with the penalty clamped at zero, against values derived by hand from the
+    triangle's busbar outages (fixture block lambda_f2)."""
+    g, d = three_bus()
+    for c in d["lambda_f2"]["cases"]:
+        gl, gen = _triangle_topology(g.with_limits(np.array(c["limit"])), d, c["topology"])
+        pre = dcflow.busbar_outages(gl, [-1, -1, -1])["lambda_b"]
+        assert pre == pytest.approx(c["lambda_b_pre"], abs=1e-12)
+        r = dcflow.evaluate(gl, gen)
+        bb = dcflow.busbar_outages(gl, gen)
+        assert bb["lambda_b"] == pytest.approx(c["lambda_b"], abs=1e-12), c
+        assert r["lambda_o"] == pytest.approx(c["lambda_o"], abs=1e-12)
+        assert (r["lambda_c0"], r["lambda_c"]) == (c["lambda_c0"], c["lambda_c"])
+        assert dcflow.lambda_f2(r, bb, pre) == pytest.approx(c["lambda_f2"], abs=1e-12), c
+    # a topology that islands the grid has lambda_f2 = -inf
+    gl, _ = _triangle_topology(g, d, "mask 6")
+    r = dcflow.evaluate(gl, [-1, 0, 2])
+    assert r["island_base"] and dcflow.lambda_f2(r, None, 0.0) == -np.inf
+
+
+def test_cells_with_disconnection_axis_hand_values():
+    """Cells of the three-axis archive (split stations, moved assets, opened
+    branches), including every clamp at the archive's edge, against values
+    derived by hand (fixture block cells_with_disconnections)."""
+    g, d = three_bus()
+    gd = _with_disc(g, [0, 1, 2], 2)
+    for c in d["cells_with_disconnections"]["cases"]:
+        split = -1 if c["split"] == "none" else action_of(g, 0, int(c["split"].split()[1]))
+        disc = list(c["disc"]) + [-1] * (2 - len(c["disc"]))
+        ds, dm, dd = c["extent"]
+        ns, nm, cell = dcflow.descriptors(gd, [split] + disc, ds, dm, dd)
+        assert (ns, nm, cell) == (c["ns"], c["nm"], c["cell"]), c
+        assert len(dcflow.open_branches(gd, [split] + disc)) == c["nd"]
+        r = dcflow.evaluate(gd, [split] + disc, d_split=ds, d_moved=dm, d_disc=dd)
+        assert r["cell"] == c["cell"] and r["nd"] == c["nd"]
+
+
+# ------------------------------------------------------------- process-parallel oracle
+def _parallel_case(name):
+    from dataclasses import replace
+    from synth.grids import make_grid
+    if name == "300":
+        g = make_grid(300, 450, 20, assets=(4, 10), T=3, b_dist=("loguniform", 2.0, 200.0),
+                      noise=0.1, seed=11, k_max=4, name="ragged300")
+    else:
+        from synth import config_grid
+        g = config_grid("tto2k")
+        # 160 outages, every eighth of them a bridge of the unsplit grid, so that
+        # islanding outages fall into several process chunks
+        rng = np.random.default_rng(5)
+        g = replace(g, outages=np.sort(rng.choice(g.n_branch, 160, replace=False)).astype(np.int32))
+    g = g.with_limits(limits_from_flows(dcflow.base_flows(g)[0], max(2, g.n_branch // 100)))
+    return g
+
+
+@pytest.mark.parametrize("name", ["300", "2k"])
+def test_parallel_outage_merge_equals_serial(name):
+    """The process-parallel oracle (outages split into chunks, maxima merged)
+    equals the serial oracle exactly at 2, 3 and 8 processes: the same f^max
+    array, islanding count, metrics and per-outage energies, on topologies
+    with islanding outages."""
+    g = _parallel_case(name)
+    topo = random_topologies(g, 6, seed=21)
+    seen_isl = 0
+    for gen in topo[:3] if name == "2k" else topo:
+        ref = dcflow.evaluate(g, gen, want_energy=True)
+        for procs in (2, 3, 8):
+            r = dcflow.evaluate_parallel_outages(g, gen, processes=procs, want_energy=True)
+            assert r["island_base"] == ref["island_base"]
+            if ref["island_base"]:
+                continue
+            assert np.array_equal(r["fmax"], ref["fmax"])
+            assert np.array_equal(r["fprime"], ref["fprime"])
+            for k in ["n_islanded", "island_any", "lambda_o", "lambda_c", "lambda_c0", "maxload",
+                      "fitness", "lambda_f1", "cell"]:
+                assert r[k] == ref[k], (k, procs)
+            e, e0 = r["outage_energy"], ref["outage_energy"]
+            assert np.array_equal(np.isnan(e), np.isnan(e0))
+            assert np.array_equal(e[~np.isnan(e)], e0[~np.isnan(e0)])
+        seen_isl += int(not ref["island_base"] and ref["n_islanded"] > 0)
+    assert seen_isl >= 1
