@@ -254,7 +254,11 @@ int tto_grid_profile_read(tto_grid* g, float* ms_stage, int32_t* n_calls);
  * workspace exceeds 64 MiB is rejected with TTO_E_ARG and a message giving the
  * bytes it needs (about 7 KB per topology on the 30-bus workload, 1 MB on the
  * 10000-bus one).  The first call on a device looks up the array's address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress) and keeps it for the life of the process; make that
+ * first call before any stream capture, and do not use the entry point across
+ * a cudaDeviceReset of the device.  The FP32 sweep runs in the variant that
+ * tto_grid_autotune chose for the grid (the default variant otherwise), as in
+ * tto_evaluate_batch.
  * All calls share the one array: calls that overlap on the GPU (other streams,
  * other threads) race and corrupt each other's results; serialise them.
  * Arguments, outputs and status reporting are those of tto_evaluate_batch. */
@@ -447,6 +451,17 @@ int tto_surrogate_score(tto_surrogate* s, const int32_t* topo, int32_t B, float*
  * be NULL.  Synchronises the device. */
 int tto_surrogate_features(tto_surrogate* s, int32_t B, int32_t* si, float* sf, float* xd,
                            int32_t* valid);
+
+/* Host copies of the network's intermediate values for the first B rows of the
+ * last batch (for element-wise checks of each layer): hidden activations
+ * h [3][B][H] (after the ReLU), output y [B] (the scores after
+ * tto_surrogate_score, the unscaled network output after tto_surrogate_grad),
+ * and, after tto_surrogate_grad, the training targets t [B]
+ * (standardised), the output gradient dy [B] and the backward signals
+ * dh [3][B][H] (dL/dz of hidden layers 1..3, ReLU mask applied).  Any pointer
+ * may be NULL; values the last call did not compute are unspecified.
+ * Synchronises the device.  TTO_E_ARG when B exceeds the last batch. */
+int tto_surrogate_trace(tto_surrogate* s, int32_t B, float* h, float* y, float* t, float* dy, float* dh);
 
 /* Append B exact pairs (device genomes [B][k_max], device fitness [B] from
  * tto_evaluate_batch) to the replay ring; non-finite fitness is kept without a

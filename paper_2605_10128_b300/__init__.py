@@ -302,6 +302,13 @@ class Surrogate:
         last processed batch, as numpy arrays."""
         return _lib.tto_surrogate_features(self._h, B, self.grid.k_max, self.n_load)
 
+    def trace(self, B):
+        """Intermediate values of the last batch (first B rows) as numpy
+        arrays: h [3][B][H] hidden activations, y [B] raw output, and after
+        :meth:`grad` the targets t, output gradient dy and backward signals
+        dh [3][B][H]."""
+        return _lib.tto_surrogate_trace(self._h, B, self.hidden)
+
     def add(self, topo, fitness, stream=None):
         _lib.tto_surrogate_add(self._h, topo.contiguous(), int(topo.shape[0]), fitness.contiguous(),
                                _stream(stream))

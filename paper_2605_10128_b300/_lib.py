@@ -123,6 +123,7 @@ _SIGS = {
     "tto_surrogate_params": ([_vp, _vp, _vp], C.c_int),
     "tto_surrogate_score": ([_vp, _vp, C.c_int32, _vp, _vp], C.c_int),
     "tto_surrogate_features": ([_vp, C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
+    "tto_surrogate_trace": ([_vp, C.c_int32, _vp, _vp, _vp, _vp, _vp], C.c_int),
     "tto_surrogate_add": ([_vp, _vp, C.c_int32, _vp, _vp], C.c_int),
     "tto_surrogate_train": ([_vp, C.c_int32, C.POINTER(C.c_float), _vp], C.c_int),
     "tto_surrogate_grad": ([_vp, _vp, C.c_int32, _vp, C.POINTER(C.c_float), _vp, _vp], C.c_int),
@@ -485,6 +486,17 @@ def tto_surrogate_features(h, B, k_max, n_load):
     check(lib().tto_surrogate_features(h, int(B), si.ctypes.data, sf.ctypes.data, xd.ctypes.data,
                                        valid.ctypes.data))
     return si, sf, xd, valid
+
+
+def tto_surrogate_trace(h, B, hidden):
+    hs = np.zeros((3, B, hidden), dtype=np.float32)
+    dh = np.zeros((3, B, hidden), dtype=np.float32)
+    y = np.zeros(B, dtype=np.float32)
+    t = np.zeros(B, dtype=np.float32)
+    dy = np.zeros(B, dtype=np.float32)
+    check(lib().tto_surrogate_trace(h, int(B), hs.ctypes.data, y.ctypes.data, t.ctypes.data, dy.ctypes.data,
+                                    dh.ctypes.data))
+    return dict(h=hs, y=y, t=t, dy=dy, dh=dh)
 
 
 def tto_surrogate_add(h, topo, B, fitness, stream):

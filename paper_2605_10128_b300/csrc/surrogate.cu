@@ -1285,6 +1285,23 @@ int tto_surrogate_features(tto_surrogate* s, int32_t B, int32_t* si, float* sf, 
   return TTO_OK;
 }
 
+int tto_surrogate_trace(tto_surrogate* s, int32_t B, float* h, float* y, float* t, float* dy, float* dh) {
+  if (!s || B < 0 || B > s->bcap) return set_error(TTO_E_ARG, "B exceeds the last batch");
+  TTO_CUDA_TRY(cudaSetDevice(s->g->device));
+  TTO_CUDA_TRY(cudaDeviceSynchronize());
+  const size_t bh = (size_t)B * s->H * sizeof(float);
+  const float* hs[3] = {s->H1, s->H2, s->H3};
+  const float* ds[3] = {s->dH1, s->dH2, s->dH3};
+  for (int l = 0; l < 3; ++l) {
+    if (h) TTO_CUDA_TRY(cudaMemcpy((char*)h + l * bh, hs[l], bh, cudaMemcpyDeviceToHost));
+    if (dh) TTO_CUDA_TRY(cudaMemcpy((char*)dh + l * bh, ds[l], bh, cudaMemcpyDeviceToHost));
+  }
+  if (y) TTO_CUDA_TRY(cudaMemcpy(y, s->Y, (size_t)B * sizeof(float), cudaMemcpyDeviceToHost));
+  if (t) TTO_CUDA_TRY(cudaMemcpy(t, s->T, (size_t)B * sizeof(float), cudaMemcpyDeviceToHost));
+  if (dy) TTO_CUDA_TRY(cudaMemcpy(dy, s->dY, (size_t)B * sizeof(float), cudaMemcpyDeviceToHost));
+  return TTO_OK;
+}
+
 int tto_surrogate_add(tto_surrogate* s, const int32_t* topo, int32_t B, const float* fitness, void* stream) {
   if (!s || B < 0 || (B > 0 && (!topo || !fitness))) return set_error(TTO_E_ARG, "bad add arguments");
   if (B == 0) return TTO_OK;
