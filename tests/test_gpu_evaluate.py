@@ -78,8 +78,10 @@ def check_all_precisions(label, sg, g, topo, idx, refs, plain_bf16=True, **kw):
         finally:
             if shape is not None:
                 g.set_sweep_shape(prec, -1)
-        worst = parity.compare(sg, out, idx, refs, tol=tol)
-        print(f"{label} {name} worst loading error {worst:.2e} of limit")
+        split = {}
+        worst = parity.compare(sg, out, idx, refs, tol=tol, split=split)
+        print(f"{label} {name} worst loading error {worst:.2e} of limit; "
+              + parity.split_report(split, tol if np.isfinite(tol) else parity.TOL_BF16))
     if plain_bf16:
         out = run(g, topo, precision=2, **kw)
         worst = parity.compare(sg, out, idx, refs, tol=np.inf)
@@ -233,3 +235,46 @@ def test_empty_batch_and_validation():
     g.sync_status()
     with pytest.raises(TTOError):
         g.evaluate(torch.zeros(4, sg.k_max, dtype=torch.int32, device="cuda"), timesteps=[5])
+
+
+@pytest.mark.slow
+def test_tto10k_full_rows_sampled_outages_many_topologies():
+    """The 10000-bus grid with all 15000 monitored branches and 4 timesteps
+    but 120 sampled non-bridge outages, so that the oracle can re-solve many
+    topologies: 40 topologies of an 8192 batch (every split count 1 to 6, and
+    4 that island the grid) in FP32, the tcgen05 TF32X3 sweep, every mma.sync
+    variant and the BF16 split, with the error split into near-limit and
+    far-above-limit parts."""
+    from dataclasses import replace
+    c = CONFIGS["tto10k"]
+    full = with_limits(config_grid("tto10k"), c["n_tight"])
+    rng = np.random.default_rng(12)
+    sg = replace(full, outages=np.sort(rng.choice(full.outages, 120, replace=False)).astype(np.int32))
+    topo = random_topologies(sg, c["batch"], seed=3)
+    per_k = {k: [] for k in range(1, 7)}
+    isl = []
+    for i in range(c["batch"]):
+        n_node, fr, to, _, _ = dcflow.post_split_graph(sg, topo[i])
+        if not dcflow.is_connected_uf(n_node, fr, to):
+            if len(isl) < 4:
+                isl.append(i)
+            continue
+        k = int((topo[i] >= 0).sum())
+        if len(per_k[k]) < 6:
+            per_k[k].append(i)
+        if len(isl) == 4 and all(len(v) == 6 for v in per_k.values()):
+            break
+    idx = sorted(isl + [i for v in per_k.values() for i in v])
+    assert len(isl) == 4 and len(idx) == 40
+    refs = parity.oracle_eval(sg, topo, idx, d_split=20, d_moved=20)
+    g = lib_grid(sg)
+    check_all_precisions("tto10k rows x 120 outages", sg, g, topo, idx, refs, plain_bf16=False,
+                         d_split=20, d_moved=20)
+    for variant in range(4):  # every mma.sync tile variant of TF32X3
+        g.set_sweep_shape(3, variant)
+        out = run(g, topo, precision=3, d_split=20, d_moved=20)
+        split = {}
+        worst = parity.compare(sg, out, idx, refs, tol=parity.TOL_FP32, split=split)
+        print(f"tto10k rows x 120 outages tf32x3 mma.sync variant {variant}: worst {worst:.2e}; "
+              + parity.split_report(split, parity.TOL_FP32))
+    g.set_sweep_shape(3, -1)
