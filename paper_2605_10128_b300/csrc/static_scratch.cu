@@ -11,7 +11,9 @@
 // which exists on every device that loads this library until the process
 // exits.  The array's device address is looked up once per device with
 // cudaGetSymbolAddress (host code must not use the array's name as a device
-// pointer); the first call on a device does that lookup.
+// pointer); the first call on a device does that lookup and caches it for the
+// life of the process, so the entry point must not be used across a
+// cudaDeviceReset of that device (the cached address would be stale).
 #include <string.h>
 
 #include <mutex>
@@ -143,6 +145,7 @@ extern "C" int tto_evaluate_batch_static(tto_grid* g, const int32_t* topo, int32
   a.d_moved = o->d_moved;
   a.d_disc = o->d_disc > 1 ? o->d_disc : 1;
   a.precision = TTO_PREC_FP32;
+  a.shape = g->tuned_shape[TTO_PREC_FP32] >= 0 ? g->tuned_shape[TTO_PREC_FP32] : 0;  // the autotuned variant
   a.fitness_kind = o->fitness_kind;
   a.n_rowtiles = g->n_rowtiles;
   a.n_parts = g->n_rowtiles;
