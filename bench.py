@@ -7,7 +7,8 @@ iteration (propose, split update, fused N-1 sweep, metrics, insert) per step.
 python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 Under torchrun each rank runs its own independent search on its own GPU (the
 topologies of different ranks are independent; no collective on the data path)
-and rank 0 prints one JSON line.
+and rank 0 prints one JSON line; with --shared-archive the ranks keep one
+archive instead (one all-gather of the step's candidates per step).
 """
 from __future__ import annotations
 
@@ -401,6 +402,9 @@ def main():
     ap.add_argument("--p-c1", type=float, default=0.5, help="crossover bias toward the first parent")
     ap.add_argument("--fitness", default="workload", choices=["workload", "f1", "f2"],
                     help="f2: lambda_f2, which adds every busbar outage of each topology")
+    ap.add_argument("--shared-archive", action="store_true",
+                    help="under torchrun: one archive shared by all ranks (one all-gather of the step's "
+                         "(genome, fitness, cell) rows, the same insert on every rank) instead of independent searches")
     ap.add_argument("--epoch", type=int, default=0,
                     help="iterations per epoch: export the archive and its worst-20 lists after each (0: never)")
     args = ap.parse_args()
@@ -451,9 +455,21 @@ def main():
         g.busbar_reference()  # lambda_b of the unsplit topology, for lambda_f2
     seed = rank_seed(rank)
     stream = torch.cuda.current_stream()
+    if args.shared_archive:
+        # one repertoire for all ranks: each rank's proposals use its own key
+        # derived from the shared seed; the step's rows are all-gathered and
+        # inserted on every rank
+        from paper_2605_10128_b300.shared_archive import SharedArchive
+        shared = SharedArchive(A)
+
+        def step(it):
+            shared.step(rank_seed(0), it, B, mutation=mut, precision=prec, fitness_kind=fit_kind)
+    else:
+        def step(it):
+            A.step(seed, it, B, mutation=mut, precision=prec, fitness_kind=fit_kind)
 
     for it in range(args.warmup):
-        A.step(seed, it, B, mutation=mut, precision=prec, fitness_kind=fit_kind)
+        step(it)
     g.sync_status()
 
     def barrier():
@@ -470,7 +486,7 @@ def main():
     t0.record(stream)
     n_export = 0
     for it in range(args.warmup, args.warmup + args.steps):
-        A.step(seed, it, B, mutation=mut, precision=prec, fitness_kind=fit_kind)
+        step(it)
         if args.epoch and (it - args.warmup + 1) % args.epoch == 0:
             # end-of-epoch hand-over: archive snapshot + worst-20 N-1 cases of
             # every cell, copied to the host while the next epoch runs
@@ -555,7 +571,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_desc(args.config, B, args.dslots, n_disc), "batch": B, "timesteps": T,
-                       "precision": args.precision, "parallelism": f"independent searches x{world}",
+                       "precision": args.precision, "parallelism": (f"shared archive x{world} (all-gather per step)" if args.shared_archive
+                                       else f"independent searches x{world}"),
                        "l2": "inputs larger than L2 (N tile 305 MB + per-batch workspace ~8 GB)",
                        "step": "one MapElites iteration: propose, exact N-1 evaluation, insert",
                        "fitness": args.fitness,
