@@ -222,6 +222,8 @@ typedef struct {
 #define TTO_MULTI_SEQUENTIAL 0 /* one grid after another on the stream */
 #define TTO_MULTI_STREAMS 1    /* grids on forked streams, joined back into the stream */
 #define TTO_MULTI_GRAPH 2      /* as STREAMS, recorded once as a CUDA graph and replayed */
+#define TTO_MULTI_PERSISTENT 3 /* one launch per stage for all jobs: split update, persistent sweep, metrics */
+#define TTO_MULTI_PERSISTENT_GRAPH 4 /* as PERSISTENT, recorded once as a CUDA graph and replayed */
 
 /* tto_evaluate_multi -- evaluate n (1..16) jobs on grids of one device as one
  * unit of work (mixed grid sizes, timestep counts and batch sizes; each grid at
@@ -229,7 +231,18 @@ typedef struct {
  * (same grids, buffers, sizes, options and stream) runs them eagerly and
  * records the launch sequence as a CUDA graph; later identical calls replay it
  * with one graph launch.  Recorded graphs are dropped when a grid is destroyed
- * or its workspace is reallocated.  Asynchronous on stream. */
+ * or its workspace is reallocated.
+ * TTO_MULTI_PERSISTENT (TTO_PREC_FP32, fitness kinds WORKLOAD and F1) runs all
+ * jobs with one launch per stage: one split update over every job's
+ * topologies, one persistent FP32 sweep whose CTAs (a few per SM) take
+ * (job, 128-row tile, topology group) items from a shared work-list counter
+ * until none is left (jobs with the largest items first; each job's items use
+ * its autotuned FP32 variant's group size), and one metric reduction (batching
+ * row of the workload: mixed grids in one persistent launch).  Eager calls in
+ * this mode share one counter per device, so such calls must not overlap on
+ * the GPU; TTO_MULTI_PERSISTENT_GRAPH records the same launches as a graph
+ * with a counter of its own.  Results equal the other modes bit for bit.
+ * Asynchronous on stream. */
 int tto_evaluate_multi(const tto_eval_job* jobs, int32_t n, const tto_eval_opts* opts, int32_t mode,
                        void* stream);
 

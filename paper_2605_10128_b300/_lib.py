@@ -56,7 +56,7 @@ class EvalJob(C.Structure):
                 ("fitness", _vp), ("desc", _vp), ("cell", _vp), ("island", _vp), ("metrics", _vp)]
 
 
-MULTI_SEQUENTIAL, MULTI_STREAMS, MULTI_GRAPH = 0, 1, 2
+MULTI_SEQUENTIAL, MULTI_STREAMS, MULTI_GRAPH, MULTI_PERSISTENT, MULTI_PERSISTENT_GRAPH = 0, 1, 2, 3, 4
 SCREEN_SCORE, SCREEN_CELL_GAIN = 0, 1
 
 

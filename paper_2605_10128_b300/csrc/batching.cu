@@ -13,8 +13,10 @@
 // fill the SMs that large ones leave idle.
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <map>
+#include <new>
 #include <mutex>
 #include <vector>
 
@@ -24,7 +26,7 @@
 namespace tto {
 namespace {
 
-constexpr int kMaxJobs = 16;
+constexpr int kMaxJobs = kMaxMultiJobs;
 
 struct StreamPool {
   std::vector<cudaStream_t> side;
@@ -68,12 +70,19 @@ struct GraphKey {
 struct GraphEntry {
   cudaGraphExec_t exec;
   std::vector<uint64_t> grids;  // uids of the grids the graph reads and writes
+  unsigned int* counter = nullptr;  // persistent mode: the graph's own work-list counter
 };
+
+void drop_entry(GraphEntry& e) {
+  cudaGraphExecDestroy(e.exec);
+  if (e.counter) cudaFree(e.counter);
+}
 
 std::map<GraphKey, GraphEntry> g_graphs;
 
-GraphKey make_key(const tto_eval_job* jobs, int n, const tto_eval_opts* o) {
+GraphKey make_key(const tto_eval_job* jobs, int n, const tto_eval_opts* o, int mode) {
   GraphKey k;
+  k.words.push_back((uint64_t)mode);
   k.words.push_back(((uint64_t)o->precision << 48) | ((uint64_t)o->fitness_kind << 32) |
                     ((uint64_t)o->d_split << 16) | (uint64_t)o->d_moved);
   k.words.push_back((uint64_t)(uint32_t)o->d_disc);
@@ -113,6 +122,62 @@ int run_forked(const tto_eval_job* jobs, int n, const tto_eval_opts* o, cudaStre
   return TTO_OK;
 }
 
+// ------------------------------------------------------- persistent work list
+unsigned int* g_counter[64] = {};  // per device: the eager persistent mode's work-list counter
+
+// Arguments of the one-launch-per-stage evaluation of jobs (FP32 only): every
+// job's evaluation arguments (no launches), its sweep items of G topologies x
+// one 128-row tile, the jobs ordered by the cost of one item (largest first).
+int build_multi(const tto_eval_job* jobs, int n, const tto_eval_opts* o, cudaStream_t s, unsigned int* counter,
+                MultiArgs* m) {
+  if (o->precision != TTO_PREC_FP32)
+    return set_error(TTO_E_ARG, "the persistent work list runs the FP32 sweep (TTO_PREC_FP32) only");
+  if (o->fitness_kind == TTO_FIT_F2) return set_error(TTO_E_ARG, "the persistent work list has no busbar outages");
+  std::vector<EvalArgs> args(n);
+  std::vector<double> cost(n);
+  std::vector<unsigned long long> items(n);
+  for (int i = 0; i < n; ++i) {
+    const tto_eval_job& j = jobs[i];
+    memset(&args[i], 0, sizeof(EvalArgs));
+    int rc = evaluate_impl(j.grid, j.topo, j.B, j.timesteps, j.n_t, o, j.fitness, j.desc, j.cell, j.island,
+                           j.metrics, nullptr, s, &args[i], false, true);
+    if (rc) return rc;
+    EvalArgs& a = args[i];
+    a.n_parts = a.n_rowtiles;  // as the FP32 sweep launcher sets it
+    const int G = fp32_item_group(a.TT);
+    items[i] = (unsigned long long)a.n_rowtiles * ((a.B + G - 1) / G);
+    cost[i] = (double)G * a.O_pad * ((a.KP <= 4 ? 4 : 8) + 2.0 * a.TT);
+  }
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  memset(m, 0, sizeof(MultiArgs));
+  m->n = n;
+  m->counter = counter;
+  unsigned long long it = 0;
+  long long blk = 0;
+  for (int k = 0; k < n; ++k) {
+    const int i = order[k];
+    m->job[k] = args[i];
+    m->item_start[k] = (unsigned int)it;
+    m->blk_start[k] = (int)blk;
+    it += items[i];
+    blk += args[i].B;
+    if (it >= 0xFFFFFFFFull || blk > 0x7FFFFFFFll) return set_error(TTO_E_ARG, "mixed batch too large for one work list");
+  }
+  m->item_start[n] = (unsigned int)it;
+  m->blk_start[n] = (int)blk;
+  m->n_items = (unsigned int)it;
+  return TTO_OK;
+}
+
+int run_persistent(const MultiArgs& m, int dev, cudaStream_t s) {
+  int rc = launch_split_update_multi(m, s);
+  if (rc) return rc;
+  if ((rc = launch_sweep_persistent(m, dev, s))) return rc;
+  return launch_fitness_multi(m, s);
+}
+
 }  // namespace
 
 void forget_grid_graphs(const tto_grid* g) {
@@ -121,7 +186,7 @@ void forget_grid_graphs(const tto_grid* g) {
     bool uses = false;
     for (uint64_t u : it->second.grids) uses = uses || u == g->uid;
     if (uses) {
-      cudaGraphExecDestroy(it->second.exec);
+      drop_entry(it->second);
       it = g_graphs.erase(it);
     } else {
       ++it;
@@ -197,7 +262,7 @@ extern "C" int tto_grid_set_sweep_shape(tto_grid* g, int32_t precision, int32_t 
 extern "C" int tto_evaluate_multi(const tto_eval_job* jobs, int32_t n, const tto_eval_opts* opts,
                                   int32_t mode, void* stream) {
   if (!jobs || !opts || n < 1 || n > kMaxJobs) return set_error(TTO_E_ARG, "need 1..%d jobs", kMaxJobs);
-  if (mode < TTO_MULTI_SEQUENTIAL || mode > TTO_MULTI_GRAPH) return set_error(TTO_E_ARG, "unknown multi mode");
+  if (mode < TTO_MULTI_SEQUENTIAL || mode > TTO_MULTI_PERSISTENT_GRAPH) return set_error(TTO_E_ARG, "unknown multi mode");
   const int dev = jobs[0].grid ? jobs[0].grid->device : -1;
   for (int i = 0; i < n; ++i) {
     const tto_eval_job& j = jobs[i];
@@ -216,6 +281,16 @@ extern "C" int tto_evaluate_multi(const tto_eval_job* jobs, int32_t n, const tto
     return TTO_OK;
   }
   std::lock_guard<std::recursive_mutex> lock(g_mu);
+  if (mode == TTO_MULTI_PERSISTENT) {
+    if (dev < 0 || dev >= 64) return set_error(TTO_E_ARG, "device %d out of range", dev);
+    if (!g_counter[dev]) TTO_CUDA_TRY(cudaMalloc(&g_counter[dev], sizeof(unsigned int)));
+    MultiArgs* m = new (std::nothrow) MultiArgs;
+    if (!m) return set_error(TTO_E_NOMEM, "host allocation");
+    int rc = build_multi(jobs, n, opts, s, g_counter[dev], m);
+    if (rc == TTO_OK) rc = run_persistent(*m, dev, s);
+    delete m;
+    return rc;
+  }
   StreamPool* pool = nullptr;
   int rc = stream_pool(dev, n, &pool);
   if (rc) return rc;
@@ -234,7 +309,7 @@ extern "C" int tto_evaluate_multi(const tto_eval_job* jobs, int32_t n, const tto
       if (rc) return rc;
     }
   }
-  GraphKey key = make_key(jobs, n, opts);
+  GraphKey key = make_key(jobs, n, opts, mode);
   cudaStream_t cs = pool->cap;
   TTO_CUDA_TRY(cudaEventRecord(pool->cap_in, s));
   TTO_CUDA_TRY(cudaStreamWaitEvent(cs, pool->cap_in, 0));
@@ -245,24 +320,37 @@ extern "C" int tto_evaluate_multi(const tto_eval_job* jobs, int32_t n, const tto
     TTO_CUDA_TRY(cudaStreamWaitEvent(s, pool->cap_out, 0));
     return TTO_OK;
   }
-  rc = run_forked(jobs, n, opts, cs, pool);
-  if (rc) return rc;
-  TTO_CUDA_TRY(cudaEventRecord(pool->cap_out, cs));
-  TTO_CUDA_TRY(cudaStreamWaitEvent(s, pool->cap_out, 0));
-  TTO_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  rc = run_forked(jobs, n, opts, cs, pool);
-  cudaGraph_t graph = nullptr;
-  cudaError_t e = cudaStreamEndCapture(cs, &graph);
-  if (rc) {
-    if (graph) cudaGraphDestroy(graph);
-    return rc;
-  }
-  if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
-  cudaGraphExec_t exec = nullptr;
-  e = cudaGraphInstantiate(&exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return cuda_error(e, "cudaGraphInstantiate");
+  // the launch sequence of these jobs: per-grid launches on forked streams,
+  // or the persistent work list (which owns a counter of its own)
   GraphEntry entry;
+  MultiArgs* m = nullptr;
+  if (mode == TTO_MULTI_PERSISTENT_GRAPH) {
+    TTO_CUDA_TRY(cudaMalloc(&entry.counter, sizeof(unsigned int)));
+    m = new (std::nothrow) MultiArgs;
+    if (!m) rc = set_error(TTO_E_NOMEM, "host allocation");
+    if (rc == TTO_OK) rc = build_multi(jobs, n, opts, cs, entry.counter, m);
+  }
+  auto record = [&]() { return m ? run_persistent(*m, dev, cs) : run_forked(jobs, n, opts, cs, pool); };
+  if (rc == TTO_OK) rc = record();  // this call's results, run eagerly
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (rc == TTO_OK) {
+    e = cudaEventRecord(pool->cap_out, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, pool->cap_out, 0);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      rc = record();
+      e = cudaStreamEndCapture(cs, &graph);
+    }
+  }
+  delete m;
+  cudaGraphExec_t exec = nullptr;
+  if (rc == TTO_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (rc != TTO_OK || e != cudaSuccess) {
+    if (entry.counter) cudaFree(entry.counter);
+    return rc != TTO_OK ? rc : cuda_error(e, "recording the mixed batch as a graph");
+  }
   entry.exec = exec;
   for (int i = 0; i < n; ++i) entry.grids.push_back(jobs[i].grid->uid);
   g_graphs[key] = entry;

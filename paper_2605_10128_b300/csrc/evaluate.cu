@@ -211,8 +211,7 @@ __device__ void busbar_setup(const EvalArgs& a, int b, int k, int ns, const int*
 
 // ---------------------------------------------------------------- split update
 template <bool BB>
-__device__ __forceinline__ void split_update_body(const EvalArgs& a) {
-  const int b = blockIdx.x;
+__device__ __forceinline__ void split_update_body(const EvalArgs& a, const int b) {
   const int tid = threadIdx.x;
   __shared__ int s_k, s_island, s_ns, s_nm;
   __shared__ int s_slot[TTO_MAX_K + 1];
@@ -575,13 +574,25 @@ __device__ __forceinline__ void split_update_body(const EvalArgs& a) {
 
 // Two instantiations: the busbar-outage setup needs many more registers and a
 // large stack, which the plain split update should not pay for.
-__global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) { split_update_body<false>(a); }
-__global__ void __launch_bounds__(256) split_update_bb_kernel(EvalArgs a) { split_update_body<true>(a); }
+__global__ void __launch_bounds__(256) split_update_kernel(EvalArgs a) { split_update_body<false>(a, blockIdx.x); }
+__global__ void __launch_bounds__(256) split_update_bb_kernel(EvalArgs a) { split_update_body<true>(a, blockIdx.x); }
+
+// Job of topology i counted over all jobs of a mixed batch.
+__device__ __forceinline__ int multi_job(const MultiArgs& m, int i) {
+  int j = 0;
+  for (int q = 1; q < m.n; ++q)
+    if (i >= m.blk_start[q]) j = q;
+  return j;
+}
+
+// The split update of every job of a mixed batch, one CTA per topology.
+__global__ void __launch_bounds__(256) split_update_multi_kernel(const __grid_constant__ MultiArgs m) {
+  const int j = multi_job(m, blockIdx.x);
+  split_update_body<false>(m.job[j], blockIdx.x - m.blk_start[j]);
+}
 
 // ---------------------------------------------------------------- fitness
-__global__ void fitness_kernel(EvalArgs a) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= a.B) return;
+__device__ __forceinline__ void fitness_one(const EvalArgs& a, int b) {
   const TopoInfo inf = a.info[b];
   double lo = 0.0;
   float lc = 0.f, ml = 0.f;
@@ -618,6 +629,33 @@ __global__ void fitness_kernel(EvalArgs a) {
     m[2] = inf.island_base ? 0.f : lc;
     m[3] = inf.lambda_c0;
   }
+}
+
+__global__ void fitness_kernel(EvalArgs a) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < a.B) fitness_one(a, b);
+}
+
+__global__ void fitness_multi_kernel(const __grid_constant__ MultiArgs m) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.blk_start[m.n]) return;
+  const int j = multi_job(m, i);
+  fitness_one(m.job[j], i - m.blk_start[j]);
+}
+
+int launch_split_update_multi(const MultiArgs& m, cudaStream_t s) {
+  if (m.blk_start[m.n] == 0) return TTO_OK;
+  split_update_multi_kernel<<<m.blk_start[m.n], 256, 0, s>>>(m);
+  TTO_CUDA_TRY(cudaGetLastError());
+  return TTO_OK;
+}
+
+int launch_fitness_multi(const MultiArgs& m, cudaStream_t s) {
+  const int n = m.blk_start[m.n];
+  if (n == 0) return TTO_OK;
+  fitness_multi_kernel<<<(n + 127) / 128, 128, 0, s>>>(m);
+  TTO_CUDA_TRY(cudaGetLastError());
+  return TTO_OK;
 }
 
 // ---------------------------------------------------------------- workspace
@@ -669,7 +707,7 @@ static int padded_K(int k) { return k <= 2 ? 2 : (k <= 4 ? 4 : 8); }
 int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, int n_t,
                   const tto_eval_opts* o, float* fitness, int32_t* desc, int32_t* cell,
                   uint8_t* island, float* metrics, float* fmax, cudaStream_t s, EvalArgs* split_only,
-                  bool busbar_setup) {
+                  bool busbar_setup, bool prepare_only) {
   if (!g || !o) return set_error(TTO_E_ARG, "null argument");
   if (B < 0) return set_error(TTO_E_ARG, "negative batch");
   if (B > 0 && (!topo || !fitness)) return set_error(TTO_E_ARG, "null topology or fitness buffer");
@@ -771,6 +809,10 @@ int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, 
   a.shape = g->tuned_shape[o->precision] >= 0 ? g->tuned_shape[o->precision] : 0;
   a.from = g->d_from;
   if (bb) fill_busbar_args(g, a);
+  if (prepare_only) {  // arguments only: the caller launches (mixed-grid batches)
+    *split_only = a;
+    return TTO_OK;
+  }
   cudaEvent_t* ev = nullptr;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   TTO_CUDA_TRY(cudaStreamIsCapturing(s, &cap));

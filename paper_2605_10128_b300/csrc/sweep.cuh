@@ -80,6 +80,27 @@ struct EvalArgs {
   float* fmax;
 };
 
+// Topologies per CTA of the FP32 sweep at padded timestep count TT (the
+// running maxima of G topologies x TT timesteps stay in registers).
+constexpr int fp32_group(int TT) { return TT <= 4 ? 8 : (TT <= 8 ? 4 : (TT <= 16 ? 2 : 1)); }
+// Topologies per item of the persistent work-list sweep: the smaller group of
+// the FP32 sweep's two tile variants.
+constexpr int fp32_item_group(int TT) { return fp32_group(TT) > 1 ? fp32_group(TT) / 2 : 1; }
+
+// Several jobs (grid, topology batch) evaluated by one launch per stage:
+// the split update over all jobs' topologies, the persistent FP32 sweep over
+// (job, row tile, topology group) items, and the metric reduction.  Passed by
+// value as a kernel parameter.
+constexpr int kMaxMultiJobs = 16;
+struct MultiArgs {
+  int n;                                        // jobs
+  unsigned int n_items;                         // sweep items in all
+  unsigned int item_start[kMaxMultiJobs + 1];   // first sweep item of each job
+  int blk_start[kMaxMultiJobs + 1];             // first topology of each job, counted over all jobs
+  unsigned int* counter;                        // next sweep item (zeroed before the launch)
+  EvalArgs job[kMaxMultiJobs];
+};
+
 // Launch the fused N-1 sweep for the precision in a.precision; sets a.n_parts.
 int launch_sweep(EvalArgs& a, cudaStream_t s);
 int launch_sweep_fp32(const EvalArgs& a, cudaStream_t s);
@@ -92,6 +113,11 @@ size_t max_parts(const tto_grid* g);
 int ensure_fragment_N(tto_grid* g, cudaStream_t s);
 // One bounded wait on an mbarrier nothing completes (timeout-path test).
 int bounded_wait_probe(int* status, long long cycles, cudaStream_t s);
+// Mixed-grid batches: the persistent FP32 sweep over m's work list, and the
+// split update and metric reduction of all of m's jobs in one launch each.
+int launch_sweep_persistent(const MultiArgs& m, int device, cudaStream_t s);
+int launch_split_update_multi(const MultiArgs& m, cudaStream_t s);
+int launch_fitness_multi(const MultiArgs& m, cudaStream_t s);
 // The tcgen05 sweep (TF32X3 only); sets a.n_parts.
 int launch_sweep_umma(EvalArgs& a, cudaStream_t s);
 // Sweep tile variant of TF32X3 that runs the tcgen05 kernel.

@@ -9,22 +9,54 @@
 // maxima live in registers for the whole column walk, so each CTA owns complete
 // rows and reduces them straight to per-row-tile partial metrics (no atomics,
 // fixed reduction order).
+//
+// The same tile body serves the persistent work-list sweep of mixed-grid
+// batches (sweep_fp32_persistent_kernel): there each CTA takes (job, row tile,
+// topology group) items from a shared counter until the list is exhausted.
 #include "sweep.cuh"
 
 namespace tto {
 
 constexpr int kCC = 32;  // outage columns per staged chunk
 
+// The grid and batch fields one CTA of the FP32 sweep reads, copied out of the
+// job's arguments once per tile.
+struct Fp32Tile {
+  const float* U;
+  const float* V;
+  const float* gg;
+  const float* fp;
+  const float* Nmo;
+  const float* lim;
+  float* fmax;
+  float* part;
+  int B, E_mon, E_mon_pad, O_pad, n_t, n_parts;
+};
+
+__device__ __forceinline__ Fp32Tile fp32_tile(const EvalArgs& a) {
+  return Fp32Tile{a.U, a.V, a.gg, a.fp, a.Nmo, a.lim, a.fmax, a.part, a.B, a.E_mon, a.E_mon_pad, a.O_pad, a.n_t,
+                  a.n_parts};
+}
+
 template <int TT, int G, int KP>
-__global__ void __launch_bounds__(kRowTile) sweep_fp32_kernel(EvalArgs a) {
-  __shared__ __align__(16) float sU[G][kRowTile][KP];
-  __shared__ __align__(16) float sV[G][kCC][KP];
-  __shared__ __align__(16) float sg[G][kCC][TT];
-  __shared__ float sred[kRowTile / 32][G][3];
+struct Fp32Smem {
+  float sU[G][kRowTile][KP];
+  float sV[G][kCC][KP];
+  float sg[G][kCC][TT];
+  float sred[kRowTile / 32][G][3];
+};
+
+// One CTA's share of the sweep: row tile `tile` (128 rows) x topologies
+// G grp .. G grp + G - 1, all outage columns.
+template <int TT, int G, int KP>
+__device__ __forceinline__ void fp32_sweep_tile(const Fp32Tile& a, int tile, int grp, Fp32Smem<TT, G, KP>& sm) {
+  auto& sU = sm.sU;
+  auto& sV = sm.sV;
+  auto& sg = sm.sg;
+  auto& sred = sm.sred;
   const int tid = threadIdx.x;
-  const int tile = blockIdx.x;
   const int l = tile * kRowTile + tid;
-  const int b0 = blockIdx.y * G;
+  const int b0 = grp * G;
   const int nG = min(G, a.B - b0);
   const int Ep = a.E_mon_pad, Op = a.O_pad;
 
@@ -135,6 +167,12 @@ __global__ void __launch_bounds__(kRowTile) sweep_fp32_kernel(EvalArgs a) {
   }
 }
 
+template <int TT, int G, int KP>
+__global__ void __launch_bounds__(kRowTile) sweep_fp32_kernel(EvalArgs a) {
+  __shared__ __align__(16) Fp32Smem<TT, G, KP> sm;
+  fp32_sweep_tile<TT, G, KP>(fp32_tile(a), blockIdx.x, blockIdx.y, sm);
+}
+
 template <int TT, int KP, int G>
 static int launch_fp32_g(const EvalArgs& a, cudaStream_t s) {
   if ((a.B + G - 1) / G > 65535) return set_error(TTO_E_ARG, "batch too large for one FP32 sweep launch");
@@ -148,7 +186,7 @@ static int launch_fp32_g(const EvalArgs& a, cudaStream_t s) {
 // running maxima), shape 1 halves G (more CTAs, fewer registers).
 template <int TT, int KP>
 static int launch_fp32_tt(const EvalArgs& a, cudaStream_t s) {
-  constexpr int G = TT <= 4 ? 8 : (TT <= 8 ? 4 : (TT <= 16 ? 2 : 1));
+  constexpr int G = fp32_group(TT);
   constexpr int G2 = G > 1 ? G / 2 : 1;
   return a.shape == 1 ? launch_fp32_g<TT, KP, G2>(a, s) : launch_fp32_g<TT, KP, G>(a, s);
 }
@@ -187,6 +225,102 @@ int launch_sweep(EvalArgs& a, cudaStream_t s) {
     return launch_sweep_fp32(a, s);
   }
   return launch_sweep_tc(a, s);
+}
+
+// ------------------------------------------------------- persistent work list
+// Mixed-grid batches (tto_evaluate_multi, TTO_MULTI_PERSISTENT): one launch of
+// four CTAs per SM; every CTA takes the next (job, row tile, topology group)
+// item from a shared counter and runs the FP32 tile body above for it, until
+// the list is exhausted.  One kernel holds the bodies of every timestep count
+// and rank, so it needs the registers of the largest; items therefore take the
+// smaller topology group of the two FP32 tile variants (fp32_item_group),
+// which keeps every body within 128 registers at four CTAs per SM.  Items are
+// numbered job by job, the jobs ordered by the cost of one item (largest
+// first), so the large items start first and the small ones fill the tail.
+// Each item writes its own partial metrics, so the result does not depend on
+// which CTA took it.  Rank 2 genomes run the rank-4 body (U and V are stored
+// 8 wide, zero beyond the genome's rank).
+template <int TT, int G, int KP>
+__device__ __forceinline__ void persistent_item(const EvalArgs& a, int tile, int grp, unsigned char* dsm) {
+  fp32_sweep_tile<TT, G, KP>(fp32_tile(a), tile, grp, *reinterpret_cast<Fp32Smem<TT, G, KP>*>(dsm));
+}
+
+template <int TT, int KP>
+__device__ __forceinline__ void persistent_tt(const EvalArgs& a, int tile, int grp, unsigned char* dsm) {
+  persistent_item<TT, fp32_item_group(TT), KP>(a, tile, grp, dsm);
+}
+
+template <int KP>
+__device__ __forceinline__ void persistent_kp(const EvalArgs& a, int tile, int grp, unsigned char* dsm) {
+  switch (a.TT) {
+    case 1: persistent_tt<1, KP>(a, tile, grp, dsm); break;
+    case 2: persistent_tt<2, KP>(a, tile, grp, dsm); break;
+    case 4: persistent_tt<4, KP>(a, tile, grp, dsm); break;
+    case 8: persistent_tt<8, KP>(a, tile, grp, dsm); break;
+    case 16: persistent_tt<16, KP>(a, tile, grp, dsm); break;
+    case 24: persistent_tt<24, KP>(a, tile, grp, dsm); break;
+    case 32: persistent_tt<32, KP>(a, tile, grp, dsm); break;
+  }
+}
+
+__global__ void __launch_bounds__(kRowTile, 4) sweep_fp32_persistent_kernel(const __grid_constant__ MultiArgs m) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ unsigned int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(m.counter, 1u);
+    __syncthreads();
+    const unsigned int it = s_item;
+    if (it >= m.n_items) break;  // the same for every thread of the CTA
+    int j = 0;
+    for (int q = 1; q < m.n; ++q)
+      if (it >= m.item_start[q]) j = q;
+    const EvalArgs& a = m.job[j];
+    const int r = (int)(it - m.item_start[j]);
+    const int tile = r % a.n_rowtiles, grp = r / a.n_rowtiles;
+    if (a.KP <= 4)
+      persistent_kp<4>(a, tile, grp, dsm);
+    else
+      persistent_kp<8>(a, tile, grp, dsm);
+    __syncthreads();  // shared memory and s_item are reused by the next item
+  }
+}
+
+template <int TT, int KP>
+constexpr size_t fp32_smem_tt() {
+  return sizeof(Fp32Smem<TT, fp32_item_group(TT), KP>);
+}
+
+template <int KP>
+constexpr size_t fp32_smem_kp() {
+  size_t m = 0;
+  const size_t v[] = {fp32_smem_tt<1, KP>(),  fp32_smem_tt<2, KP>(),  fp32_smem_tt<4, KP>(), fp32_smem_tt<8, KP>(),
+                      fp32_smem_tt<16, KP>(), fp32_smem_tt<24, KP>(), fp32_smem_tt<32, KP>()};
+  for (size_t x : v) m = x > m ? x : m;
+  return m;
+}
+
+constexpr size_t kPersistentSmem = fp32_smem_kp<4>() > fp32_smem_kp<8>() ? fp32_smem_kp<4>() : fp32_smem_kp<8>();
+
+int launch_sweep_persistent(const MultiArgs& m, int device, cudaStream_t s) {
+  static int blocks_per_sm[64] = {};
+  if (device < 0 || device >= 64) return set_error(TTO_E_ARG, "device %d out of range", device);
+  if (blocks_per_sm[device] == 0) {
+    TTO_CUDA_TRY(cudaFuncSetAttribute(sweep_fp32_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kPersistentSmem));
+    int nb = 0;
+    TTO_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_fp32_persistent_kernel, kRowTile,
+                                                               kPersistentSmem));
+    blocks_per_sm[device] = nb > 0 ? nb : 1;
+  }
+  int sms = 0;
+  TTO_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  const unsigned int slots = (unsigned int)(sms * blocks_per_sm[device]);
+  const unsigned int grid = m.n_items < slots ? m.n_items : slots;
+  if (grid == 0) return TTO_OK;
+  TTO_CUDA_TRY(cudaMemsetAsync(m.counter, 0, sizeof(unsigned int), s));
+  sweep_fp32_persistent_kernel<<<grid, kRowTile, kPersistentSmem, s>>>(m);
+  TTO_CUDA_TRY(cudaGetLastError());
+  return TTO_OK;
 }
 
 }  // namespace tto

@@ -135,11 +135,13 @@ void free_workspace(tto_grid* g);
 void forget_grid_graphs(const tto_grid* g);
 struct EvalArgs;
 // Exact evaluation; with split_only set, stop after the split update (U, V,
-// f', g in the workspace) and return the launch arguments there.
+// f', g in the workspace) and return the launch arguments there; with
+// prepare_only as well, launch nothing (validation, workspace and arguments
+// only; a batch of 0 topologies leaves *split_only untouched).
 int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, int n_t,
                   const tto_eval_opts* o, float* fitness, int32_t* desc, int32_t* cell,
                   uint8_t* island, float* metrics, float* fmax, cudaStream_t s,
-                  EvalArgs* split_only = nullptr, bool busbar_setup = false);
+                  EvalArgs* split_only = nullptr, bool busbar_setup = false, bool prepare_only = false);
 // Busbar outages (busbar.cu): tables and record workspace, launch arguments,
 // the sweep and the per-topology lambda_b.
 int ensure_busbar(tto_grid* g, int B, int TT, cudaStream_t s);

@@ -50,7 +50,11 @@ def test_multi_equals_per_grid_in_every_mode(prec):
         r = g.evaluate(topo, precision=prec, metrics=True)
         g.sync_status()
         ref.append(_np(r))
-    for mode in [_lib.MULTI_SEQUENTIAL, _lib.MULTI_STREAMS, _lib.MULTI_GRAPH, _lib.MULTI_GRAPH]:
+    modes = [_lib.MULTI_SEQUENTIAL, _lib.MULTI_STREAMS, _lib.MULTI_GRAPH, _lib.MULTI_GRAPH]
+    if prec == 0:  # the persistent work list (FP32), eager and recorded (first call records, second replays)
+        modes += [_lib.MULTI_PERSISTENT, _lib.MULTI_PERSISTENT_GRAPH, _lib.MULTI_PERSISTENT_GRAPH,
+                  _lib.MULTI_PERSISTENT]
+    for mode in modes:
         outs = evaluate_multi([(g, topo) for _, g, topo in grids], precision=prec, mode=mode)
         torch.cuda.synchronize()
         for (sg, g, _), o, r in zip(grids, outs, ref):
@@ -113,3 +117,36 @@ def test_multi_rejects_bad_jobs():
     t = torch.tensor(random_topologies(sg, 8, seed=1), dtype=torch.int32, device="cuda")
     with pytest.raises(TTOError):
         evaluate_multi([(g, t), (g, t)])  # one grid twice
+
+
+@pytest.mark.parametrize("fitness_kind", [0, 1])
+def test_persistent_work_list_mixed_ranks_and_subsets(fitness_kind):
+    """The persistent work list over grids of genome rank 2, 3, 6 and 8 (the
+    rank-4 and rank-8 bodies), a reordered timestep subset and both fitness
+    kinds, equal bit for bit to per-grid evaluation; the tuned FP32 variant of
+    a grid does not change the results.  TF32X3 is refused in this mode."""
+    from paper_2605_10128_b300 import Grid, TTOError, evaluate_multi, _lib
+    specs = [(60, 90, 5, 1, 2, 33), (120, 180, 8, 3, 3, 70), (200, 300, 12, 5, 6, 19), (150, 225, 12, 8, 8, 9)]
+    jobs, ref = [], []
+    for i, (n, e, st, T, k, B) in enumerate(specs):
+        sg = _limited(make_grid(n, e, st, assets=(4, 8), T=T, b_dist=("loguniform", 2.0, 200.0),
+                                noise=0.1 if T > 1 else 0.0, seed=60 + i, k_max=k, name=f"rank{k}"))
+        g = Grid(sg)
+        if i == 1:
+            g.set_sweep_shape(0, 1)  # the other FP32 tile variant for the per-grid reference
+        topo = torch.tensor(random_topologies(sg, B, seed=3 + i), dtype=torch.int32, device="cuda")
+        ts = [2, 0] if T == 3 else None
+        jobs.append((g, topo, ts) if ts else (g, topo))
+        r = g.evaluate(topo, timesteps=ts, fitness_kind=fitness_kind, metrics=True)
+        g.sync_status()
+        ref.append(_np(r))
+    for mode in [_lib.MULTI_PERSISTENT, _lib.MULTI_PERSISTENT_GRAPH, _lib.MULTI_PERSISTENT_GRAPH]:
+        outs = evaluate_multi(jobs, fitness_kind=fitness_kind, mode=mode)
+        torch.cuda.synchronize()
+        for j, o, r in zip(jobs, outs, ref):
+            j[0].sync_status()
+            o = _np(o)
+            for k in ["fitness", "desc", "cell", "island", "metrics"]:
+                np.testing.assert_array_equal(o[k], r[k], err_msg=f"mode {mode} {k}")
+    with pytest.raises(TTOError):
+        evaluate_multi(jobs, precision=3, mode=_lib.MULTI_PERSISTENT)
