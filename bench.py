@@ -213,20 +213,23 @@ def run_reference(args, rank, world):
 
 
 MIX = ["mix500", "mix2k", "mix5k", "mix10k"]
+# a mix where small grids dominate the work: the 500- and 2000-bus grids at
+# 8192 topologies each, the 10000-bus grid at 512
+MIX_SMALL = {"mix500": 8192, "mix2k": 8192, "mix10k": 512}
 
 
 def run_mixed(args, prec, pk, pk_kind):
-    """Mixed-grid batching: the four grids of different size, timestep count and
-    batch size evaluated as one unit, per-grid launches vs one recorded graph;
-    each grid's sweep tile variant comes from the autotuner."""
+    """Mixed-grid batching: grids of different size, timestep count and batch
+    size evaluated as one unit, per-grid launches, one recorded graph of them,
+    and the persistent work list (one launch per stage, eager and recorded);
+    each grid's sweep tile variant comes from the autotuner (per-grid modes)."""
     import torch
     from paper_2605_10128_b300 import evaluate_multi, _lib
+    mix = MIX_SMALL if args.config == "mixsmall" else {n: CONFIGS[n]["batch"] for n in MIX}
     grids, topos, total = [], [], 0
     tune = {}
-    for i, name in enumerate(MIX):
-        c = CONFIGS[name]
+    for i, (name, B) in enumerate(mix.items()):
         sg, g, _ = make_grid(name, 0, seed=0)
-        B = c["batch"]
         g.reserve(B)
         tune[name] = g.autotune(min(B, 512), precision=prec)
         topo = torch.from_numpy(random_topologies(sg, B, seed=11 + i)).cuda()
@@ -235,7 +238,10 @@ def run_mixed(args, prec, pk, pk_kind):
         total += B
     jobs = list(zip(grids, topos))
     res = {}
-    for label, mode in [("per_grid_launches", _lib.MULTI_SEQUENTIAL), ("one_graph", _lib.MULTI_GRAPH)]:
+    modes = [("per_grid_launches", _lib.MULTI_SEQUENTIAL), ("one_graph", _lib.MULTI_GRAPH)]
+    if prec == 0:
+        modes += [("persistent", _lib.MULTI_PERSISTENT), ("persistent_graph", _lib.MULTI_PERSISTENT_GRAPH)]
+    for label, mode in modes:
         for _ in range(max(1, args.warmup)):
             evaluate_multi(jobs, precision=prec, mode=mode)
         torch.cuda.synchronize()
@@ -248,16 +254,16 @@ def run_mixed(args, prec, pk, pk_kind):
         res[label] = e0.elapsed_time(e1) / args.steps
     for g in grids:
         g.sync_status()
-    line = {"metric": "N-1 topology evals/s (mixed 500/2000/5000/10000-bus batch)",
-            "value": total / (res["one_graph"] / 1000.0), "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["one_graph"],
+    best = min(res, key=res.get)
+    line = {"metric": f"N-1 topology evals/s (mixed {'/'.join(n[3:] for n in mix)}-bus batch)",
+            "value": total / (res[best] / 1000.0), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res[best],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "mix: " + ", ".join(workload_desc(n, CONFIGS[n]["batch"]) for n in MIX),
-                       "precision": args.precision,
-                       "tile_variants": {n: {"chosen": tune[n][0], "ms_per_variant_at_B512": tune[n][1]} for n in MIX}},
-            "per_grid_launches": {"value": total / (res["per_grid_launches"] / 1000.0), "unit": UNIT,
-                                  "ms_per_step": res["per_grid_launches"]},
+            "config": {"workload": "mix: " + ", ".join(workload_desc(n, B) for n, B in mix.items()),
+                       "precision": args.precision, "mode": best,
+                       "tile_variants": {n: {"chosen": tune[n][0], "ms_per_variant_at_B512": tune[n][1]} for n in mix}},
+            "modes": {k: {"value": total / (v / 1000.0), "unit": UNIT, "ms_per_step": v} for k, v in res.items()},
             "gpu_launches": None}
     print(json.dumps(line), flush=True)
 
@@ -267,31 +273,27 @@ def _best(archive):
     return float(fit[filled.astype(bool)].max()) if filled.any() else -np.inf
 
 
-def run_surrogate(args, prec):
+def time_to_target(g, prec, variants_spec, seeds, iters, train_steps, stop_at_target=False):
     """Time to target on the 10000-bus workload: surrogate-screened MapElites
     against plain MapElites (8192 proposals evaluated exactly per iteration),
     same seeds, same precision.  A screened variant "rank:n" proposes n
     candidates per iteration, scores them, evaluates the best-ranked 8192
     exactly (rank "score": by predicted fitness; "gain": by predicted gain over
-    the cell's elite, empty cells first), then runs --train-steps training
+    the cell's elite, empty cells first), then runs train_steps training
     steps; "rank:n@w" runs plain iterations (whose exact pairs still train
     the surrogate) before screening from iteration w on.  The target of a
-    seed is the best fitness its plain run reaches in --iters iterations;
+    seed is the best fitness its plain run reaches in `iters` iterations;
     each arm's time to target is the wall time of the first iteration whose
-    archive holds a fitness at least as good."""
+    archive holds a fitness at least as good.  Returns (summary, runs)."""
     import torch
     from scipy.stats import spearmanr
     from paper_2605_10128_b300 import Archive, Surrogate, SCREEN_SCORE, SCREEN_CELL_GAIN
-    cfg = "tto10k"
-    c = CONFIGS[cfg]
+    c = CONFIGS["tto10k"]
     B = c["batch"]
     ds, dm = c["archive"]
-    sg, g, _ = make_grid(cfg, 0, seed=0)
-    g.reserve(B)
-    g.autotune(512, precision=prec)
     sur_kw = dict(hidden=512, n_load=256, replay=262144, minibatch=8192, lr=1e-3)
     variants = []
-    for v in args.variants.split(","):
+    for v in variants_spec.split(","):
         mode, rest = v.split(":")
         n, _, w = rest.partition("@")
         variants.append((v, {"score": SCREEN_SCORE, "gain": SCREEN_CELL_GAIN}[mode], int(n), int(w or 0)))
@@ -305,7 +307,7 @@ def run_surrogate(args, prec):
     wa.close()
     ws.close()
 
-    def run_arm(seed, variant):
+    def run_arm(seed, variant, target=None):
         A = Archive(g, ds, dm)
         S = Surrogate(g, seed=seed, **sur_kw) if variant else None
         torch.cuda.synchronize()
@@ -313,23 +315,25 @@ def run_surrogate(args, prec):
         curve = []
         topo_o = torch.empty(B, g.k_max, dtype=torch.int32, device="cuda")
         fit_o = torch.empty(B, dtype=torch.float32, device="cuda")
-        for it in range(args.iters):
+        for it in range(iters):
             if S is None:
                 A.step(seed, it, B, precision=prec)
             elif it < variant[3]:
                 # warm start: plain iteration whose exact pairs train the surrogate
                 A.step(seed, it, B, precision=prec, topo_out=topo_o, fitness_out=fit_o)
                 S.add(topo_o, fit_o)
-                S.train(args.train_steps, want_loss=False)
+                S.train(train_steps, want_loss=False)
             else:
                 A.step_screened(S, seed, it, variant[2], B, rank_by=variant[1], precision=prec,
-                                train_steps=args.train_steps)
+                                train_steps=train_steps)
             curve.append((time.perf_counter() - t0, _best(A)))
+            if target is not None and curve[-1][1] >= target:
+                break
         g.sync_status()
         rho = None
         if S is not None:
             # rank correlation on fresh proposals of the final archive
-            prop = A.propose(seed, args.iters + 1, B)
+            prop = A.propose(seed, iters + 1, B)
             sc = S.score(prop).cpu().numpy().astype(np.float64)
             fit = g.evaluate(prop, precision=prec, d_split=ds, d_moved=dm)["fitness"].cpu().numpy()
             ok = np.isfinite(sc) & np.isfinite(fit)
@@ -339,39 +343,57 @@ def run_surrogate(args, prec):
         return curve, rho
 
     runs = []
-    for k in range(args.seeds):
+    for k in range(seeds):
         seed = 2000 + k
         plain, _ = run_arm(seed, None)
         target = plain[-1][1]
         t_plain = next(t for t, b in plain if b >= target)
         rec = {"seed": seed, "target_fitness": target, "plain_s": t_plain,
-               "plain_s_per_iter": plain[-1][0] / args.iters,
+               "plain_s_per_iter": plain[-1][0] / iters,
                "plain_best_by_iter": [round(b, 3) for _, b in plain], "screened": {}}
         for v in variants:
-            curve, rho = run_arm(seed, v)
+            curve, rho = run_arm(seed, v, target if stop_at_target else None)
             hit = [t for t, b in curve if b >= target]
             rec["screened"][v[0]] = {"time_s": hit[0] if hit else None,
                                      "speedup": (t_plain / hit[0]) if hit else None,
-                                     "final_best": curve[-1][1], "s_per_iter": curve[-1][0] / args.iters,
+                                     "iterations_run": len(curve),
+                                     "final_best": curve[-1][1], "s_per_iter": curve[-1][0] / len(curve),
                                      "spearman_rho": rho, "best_by_iter": [round(b, 3) for _, b in curve]}
         runs.append(rec)
     summary = {}
     for v in variants:
         sp = [r["screened"][v[0]]["speedup"] for r in runs]
         reached = sum(x is not None for x in sp)
+        rhos = [r["screened"][v[0]]["spearman_rho"] for r in runs]
         summary[v[0]] = {"reached": f"{reached}/{len(runs)}",
                          "median_speedup": float(np.median(sp)) if reached == len(runs) else None,
+                         "speedups": sp,
+                         "spearman_rho": rhos, "median_spearman_rho": float(np.median(rhos)),
                          "final_best_minus_target": [r["screened"][v[0]]["final_best"] - r["target_fitness"]
                                                      for r in runs]}
-    head = summary[variants[0][0]]["median_speedup"]
+    return summary, runs
+
+
+def run_surrogate(args, prec):
+    """The time-to-target comparison (see time_to_target) as its own JSON line,
+    every arm's best-fitness curve included."""
+    cfg = "tto10k"
+    c = CONFIGS[cfg]
+    B = c["batch"]
+    sg, g, _ = make_grid(cfg, 0, seed=0)
+    g.reserve(B)
+    g.autotune(512, precision=prec)
+    summary, runs = time_to_target(g, prec, args.variants, args.seeds, args.iters, args.train_steps,
+                                   args.stop_at_target)
+    head = summary[args.variants.split(",")[0]]["median_speedup"]
     line = {"metric": "time-to-target best fitness (10k-bus), surrogate-screened vs plain MapElites",
             "value": head, "unit": "x (plain s / screened s)",
             "n_gpus": 1, "steps": args.iters, "warmup": 2, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_desc(cfg, B), "precision": args.precision,
                        "variants": args.variants, "exact_per_iter": B,
-                       "train_steps_per_iter": args.train_steps, "surrogate": sur_kw,
-                       "seeds": args.seeds, "iterations": args.iters},
+                       "train_steps_per_iter": args.train_steps,
+                       "seeds": args.seeds, "iterations": args.iters, "stop_at_target": args.stop_at_target},
             "summary": summary, "runs": runs, "gpu_launches": None}
     print(json.dumps(line), flush=True)
 
@@ -395,6 +417,12 @@ def main():
                     help="--config surrogate: screened variants rank:proposals[@first screened iteration] "
                          "(rank = score or gain)")
     ap.add_argument("--train-steps", type=int, default=8, help="--config surrogate: training steps per iteration")
+    ap.add_argument("--stop-at-target", action="store_true",
+                    help="--config surrogate: end a screened arm once it reaches its seed's target")
+    ap.add_argument("--ttt-seeds", type=int, default=3,
+                    help="default line: seeds of the time-to-target comparison (0: leave it out)")
+    ap.add_argument("--ttt-iters", type=int, default=60, help="default line: plain iterations that set the target")
+    ap.add_argument("--ttt-variant", default="score:65536@16", help="default line: the screened arm")
     ap.add_argument("--dslots", type=int, default=0, help="branch-disconnection slots per genome (0: splits only)")
     ap.add_argument("--ndisc", type=int, default=0, help="disconnection set size (default: a hundredth of the branches)")
     ap.add_argument("--ddisc", type=int, default=3, help="archive extent over opened branches when --dslots > 0")
@@ -425,7 +453,7 @@ def main():
         dist.init_process_group("nccl")
     prec = {"fp32": PREC_FP32, "fp16x3": PREC_FP16X3, "tf32x3": PREC_TF32X3, "bf16x3": PREC_BF16X3,
             "bf16": PREC_BF16}[args.precision]
-    if args.config == "mix":
+    if args.config in ("mix", "mixsmall"):
         if rank == 0:
             pk, pk_kind = peaks()
             run_mixed(args, prec, pk, pk_kind)
@@ -545,6 +573,21 @@ def main():
         wk = {"topologies": int(elites.shape[0]), "k": 20, "ms": wk_ms,
               "ms_per_topology": wk_ms / int(elites.shape[0])}
 
+    # time to target, surrogate-screened against plain MapElites, on this grid
+    # (one GPU: the comparison is per search, not per job)
+    ttt = None
+    if world == 1 and args.config == "tto10k" and args.ttt_seeds > 0 and not args.dslots and fit_kind == 0:
+        t_ttt = time.perf_counter()
+        summary, runs = time_to_target(g, prec, args.ttt_variant, args.ttt_seeds, args.ttt_iters, args.train_steps,
+                                       stop_at_target=True)
+        s_v = summary[args.ttt_variant]
+        ttt = {"variant": args.ttt_variant, "seeds": args.ttt_seeds, "target": f"plain best after {args.ttt_iters} "
+               "iterations", "reached": s_v["reached"], "median_speedup": s_v["median_speedup"],
+               "speedups": s_v["speedups"], "spearman_rho": s_v["spearman_rho"],
+               "plain_s": [r["plain_s"] for r in runs],
+               "screened_s": [r["screened"][args.ttt_variant]["time_s"] for r in runs],
+               "wall_s": round(time.perf_counter() - t_ttt, 1)}
+
     if rank == 0:
         pk, pk_kind = peaks()
         props = torch.cuda.get_device_properties(local)
@@ -590,6 +633,7 @@ def main():
             "stage_ms_per_step": {"split_update": stage_ms[0] / max(ncalls, 1), "sweep": sweep_ms,
                                   "metrics": stage_ms[2] / max(ncalls, 1)},
             "worst_k_export": wk,
+            "time_to_target": ttt,
             "epoch_export": ({"every_steps": args.epoch, "exports_in_timed_region": n_export, "k": 20,
                               "cells": A.cells} if args.epoch else None),
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(B * g.genome_width * 4),
