@@ -344,13 +344,15 @@ __global__ void __launch_bounds__(kUThreads, 1)
         const uint64_t a_d0 = smem_desc(smA, 128, 256), v_d0 = smem_desc(smS + kUN, 128, 256);
         constexpr uint32_t kDA = kUA >> 4, kDAlo = (kUA / 2) >> 4, kDV = C::kTopoBytes >> 4, kDVlo = (kUV / 2) >> 4,
                            kDS = C::kStage >> 4;
+        int slot = 0;
+        uint32_t ring_ph = 0;
+        uint64_t v_ds = v_d0;
         for (int s = 0; s < n_chunks; ++s) {
-          const int slot = s % kUStages, buf = s & 1;
-          if (!bar_wait(&full[slot], (uint32_t)(s / kUStages) & 1u, abort_flag, a.status)) {
+          const int buf = s & 1;
+          if (!bar_wait(&full[slot], ring_ph, abort_flag, a.status)) {
             give_up();
             break;
           }
-          const uint64_t v_ds = v_d0 + (uint64_t)(slot * kDS);
           bool ok = true;
           for (int b = 0; b < n_topo; ++b) {
             if (s >= 2 && !bar_wait(&tempty[b][buf], (uint32_t)((s >> 1) - 1) & 1u, abort_flag, a.status)) {
@@ -367,6 +369,13 @@ __global__ void __launch_bounds__(kUThreads, 1)
             umma_commit(&tfull[b][buf]);
           }
           if (!ok) break;
+          if (++slot == kUStages) {
+            slot = 0;
+            ring_ph ^= 1u;
+            v_ds = v_d0;
+          } else {
+            v_ds += kDS;
+          }
         }
       }
     }
@@ -389,18 +398,23 @@ __global__ void __launch_bounds__(kUThreads, 1)
           m[r][t] = 0.f;
         }
       bool ok = true;
+      // ring slot, its phase and the slot's shared-memory base advance
+      // incrementally; the tensor-memory base of the topology is fixed
+      int slot = 0;
+      uint32_t ring_ph = 0;
+      const unsigned char* st = smS;
+      const uint32_t lo_base = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 2 * kUNC);
+      const int noff = (2 * q) * 8 * 32 + lane;         // this lane's fragment, 16-row tile 2 q, block 0
+      const int goff = kUN + b * C::kTopoBytes + kUV;   // g of this topology within a slot
       for (int s = 0; s < n_chunks && ok; ++s) {
-        const int slot = s % kUStages, buf = s & 1;
-        ok = __all_sync(0xffffffffu, bar_wait(&full[slot], (uint32_t)(s / kUStages) & 1u, abort_flag, a.status) &&
+        const int buf = s & 1;
+        ok = __all_sync(0xffffffffu, bar_wait(&full[slot], ring_ph, abort_flag, a.status) &&
                                          bar_wait(&tfull[b][buf], (uint32_t)(s >> 1) & 1u, abort_flag, a.status));
         if (!ok) break;
         tc_fence_after();
-        const unsigned char* st = smS + (size_t)slot * C::kStage;
-        const float* gs = reinterpret_cast<const float*>(st + kUN + b * C::kTopoBytes + kUV);
-        // this lane's fragment of 16-row tile 2 q (rows 32 q .. 32 q + 15), block 0
-        const float4* nf = reinterpret_cast<const float4*>(st) + (2 * q) * 8 * 32 + lane;
-        const uint32_t col = (uint32_t)(b * 2 * kUNC + buf * kUNC);
-        const uint32_t lo = tmem + ((uint32_t)(32 * q) << 16) + col, hi = lo + (16u << 16);
+        const float* gs = reinterpret_cast<const float*>(st + goff);
+        const float4* nf = reinterpret_cast<const float4*>(st) + noff;
+        const uint32_t lo = lo_base + (uint32_t)(buf * kUNC), hi = lo + (16u << 16);
         uint32_t A0[8], B0[8], A1[8], B1[8];
         tmem_ld_2blk(lo, A0);
         tmem_ld_2blk(hi, B0);
@@ -423,6 +437,13 @@ __global__ void __launch_bounds__(kUThreads, 1)
         if (lane == 0) {
           bar_arrive(&tempty[b][buf]);
           bar_arrive(&empty[slot]);
+        }
+        if (++slot == kUStages) {
+          slot = 0;
+          ring_ph ^= 1u;
+          st = smS;
+        } else {
+          st += C::kStage;
         }
       }
       if (!ok) {
