@@ -421,7 +421,7 @@ def main():
                     help="--config surrogate: end a screened arm once it reaches its seed's target")
     ap.add_argument("--ttt-seeds", type=int, default=3,
                     help="default line: seeds of the time-to-target comparison (0: leave it out)")
-    ap.add_argument("--ttt-iters", type=int, default=60, help="default line: plain iterations that set the target")
+    ap.add_argument("--ttt-iters", type=int, default=100, help="default line: plain iterations that set the target")
     ap.add_argument("--ttt-variant", default="score:65536@16", help="default line: the screened arm")
     ap.add_argument("--dslots", type=int, default=0, help="branch-disconnection slots per genome (0: splits only)")
     ap.add_argument("--ndisc", type=int, default=0, help="disconnection set size (default: a hundredth of the branches)")

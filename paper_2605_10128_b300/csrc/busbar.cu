@@ -262,11 +262,14 @@ int ensure_busbar(tto_grid* g, int B, int TT, cudaStream_t s) {
     TTO_CUDA_TRY(cudaStreamSynchronize(s));
     if (g->d_bbrec) cudaFree(g->d_bbrec);
     if (g->d_bbpart) cudaFree(g->d_bbpart);
+    if (g->d_bbstate) cudaFree(g->d_bbstate);
     g->d_bbrec = nullptr;
     g->d_bbpart = nullptr;
+    g->d_bbstate = nullptr;
     g->bb_cap_B = g->bb_cap_T = 0;
     TTO_CUDA_TRY(cudaMalloc(&g->d_bbrec, (size_t)nB * NB * bb_record_floats(nT) * sizeof(float)));
     TTO_CUDA_TRY(cudaMalloc(&g->d_bbpart, (size_t)nB * g->n_rowtiles * sizeof(float)));
+    TTO_CUDA_TRY(cudaMalloc(&g->d_bbstate, (size_t)nB * sizeof(SplitState)));
     g->bb_cap_B = nB;
     g->bb_cap_T = nT;
     forget_grid_graphs(g);
@@ -284,6 +287,7 @@ void fill_busbar_args(tto_grid* g, EvalArgs& a) {
   a.Pm = g->d_Pm;
   a.Nswm = g->d_Nswm;
   a.bbrec = g->d_bbrec;
+  a.bbstate = static_cast<SplitState*>(g->d_bbstate);
   a.bbpart = g->d_bbpart;
   a.lbpre = g->d_lbpre;
 }

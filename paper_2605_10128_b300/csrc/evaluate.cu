@@ -67,12 +67,19 @@ __device__ __forceinline__ void store_col_factors(const EvalArgs& a, int b, int 
 // z and y.  The small system is solved in FP64 as D^-1 N'_{R'R'} (symmetric:
 // D^-1 N and D^-1 U V^T = D^-1 W K^-1 W^T D^-1 are) by LDL^T, with the
 // islanding test pivot x b_r <= 1e-6 as for single outages.
-__device__ void busbar_setup(const EvalArgs& a, int b, int k, int ns, const int* s_st, const uint32_t* s_mask,
-                             const int* s_dis, int nd, const int* s_slot, const int* s_e, const double* s_sign,
-                             const double* s_coef, const double* const* s_col, const double (*s_Ki)[TTO_MAX_K],
-                             const double (*s_psi)[TTO_MAX_K], int* n_island) {
+__device__ void busbar_record(const EvalArgs& a, int b, int v, const SplitState& ss, int* n_island) {
   const int TT = a.TT, nt = a.n_t;
-  for (int v = threadIdx.x; v < a.NB; v += blockDim.x) {
+  const int k = ss.k, ns = ss.ns, nd = ss.nd;
+  const int* s_st = ss.st;
+  const uint32_t* s_mask = ss.mask;
+  const int* s_dis = ss.dis;
+  const int* s_slot = ss.slot;
+  const int* s_e = ss.e;
+  const double* s_sign = ss.sign;
+  const double* s_coef = ss.coef;
+  const double(*s_Ki)[TTO_MAX_K] = ss.Ki;
+  const double(*s_psi)[TTO_MAX_K] = ss.psi;
+  {
     float* rec = a.bbrec + ((size_t)b * a.NB + v) * a.kRec;
     int* irec = reinterpret_cast<int*>(rec);
     int s, side, js = -1;
@@ -84,7 +91,7 @@ __device__ void busbar_setup(const EvalArgs& a, int b, int k, int ns, const int*
       if (j >= ns) {
         irec[0] = 0;
         irec[1] = -1;  // no such busbar in this topology
-        continue;
+        return;
       }
       s = s_st[j];
       side = 1;
@@ -111,7 +118,7 @@ __device__ void busbar_setup(const EvalArgs& a, int b, int k, int ns, const int*
     if (nrv == 0) {  // a node without live branches: the topology itself islands (not reached)
       irec[1] = -2;
       atomicAdd(n_island, 1);
-      continue;
+      return;
     }
     float* prec = rec + kBBHead;
     float* zrec = prec + TT;
@@ -132,7 +139,7 @@ __device__ void busbar_setup(const EvalArgs& a, int b, int k, int ns, const int*
       ib[ii] = a.invb[r];
       for (int i = 0; i < k; ++i) {
         double w = 0.0;
-        for (int q = s_slot[i]; q < s_slot[i + 1]; ++q) w += s_coef[q] * s_col[q][r];
+        for (int q = s_slot[i]; q < s_slot[i + 1]; ++q) w += s_coef[q] * a.Nsw[(size_t)ss.col[q] * a.E + r];
         W[ii][i] = w;
       }
       double U[TTO_MAX_K], rh = a.Pst[(size_t)s * a.E + r];
@@ -169,7 +176,7 @@ __device__ void busbar_setup(const EvalArgs& a, int b, int k, int ns, const int*
     if (isl) {
       irec[1] = -2;
       atomicAdd(n_island, 1);
-      continue;
+      return;
     }
     // per timestep: rhs_j = (f'_{r_j} - p_v rho_j) / b_j, z from L D L^T, then y
     for (int t = 0; t < TT; ++t) {
@@ -209,6 +216,23 @@ __device__ void busbar_setup(const EvalArgs& a, int b, int k, int ns, const int*
   }
 }
 
+// One thread per (topology, busbar node): the busbar outage record from the
+// topology's split state, which its split update saved (records of a topology
+// whose split islands the grid, or whose genome is invalid, are marked unused).
+__global__ void __launch_bounds__(128) busbar_setup_kernel(EvalArgs a) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)a.B * a.NB) return;
+  const int b = (int)(i / a.NB), v = (int)(i % a.NB);
+  const SplitState& ss = a.bbstate[b];
+  if (ss.k < 0) {
+    int* irec = reinterpret_cast<int*>(a.bbrec + ((size_t)b * a.NB + v) * a.kRec);
+    irec[0] = 0;
+    irec[1] = -1;
+    return;
+  }
+  busbar_record(a, b, v, ss, &a.info[b].nbisl);
+}
+
 // ---------------------------------------------------------------- split update
 template <bool BB>
 __device__ __forceinline__ void split_update_body(const EvalArgs& a, const int b) {
@@ -235,7 +259,6 @@ __device__ __forceinline__ void split_update_body(const EvalArgs& a, const int b
   __shared__ int s_dis[TTO_MAX_K], s_nd;  // branches the genome opens
   __shared__ int s_st[TTO_MAX_K];          // station of each split slot
   __shared__ uint32_t s_mk[TTO_MAX_K];     // its busbar-B mask
-  __shared__ int s_bbisl;
 
   if (tid == 0) {
     int k = 0, ne = 0, bad = 0, ns = 0, nm = 0, nd = 0;
@@ -318,7 +341,6 @@ __device__ __forceinline__ void split_update_body(const EvalArgs& a, const int b
     s_ns = ns;
     s_nm = nm;
     s_nd = bad ? 0 : nd;
-    s_bbisl = 0;
     s_island = bad;
     s_cnt_c0 = 0;
     s_cnt_isl = 0;
@@ -545,15 +567,32 @@ __device__ __forceinline__ void split_update_body(const EvalArgs& a, const int b
   if (umax > 0.f) atomicMax(reinterpret_cast<int*>(&s_umax), __float_as_int(umax));
   if (vmax > 0.f) atomicMax(reinterpret_cast<int*>(&s_vmax), __float_as_int(vmax));
   if constexpr (BB) {
+    // the split state the busbar setup needs (busbar_setup_kernel, one thread
+    // per busbar node, runs after this kernel)
+    SplitState& ss = a.bbstate[b];
     if (dead) {
-      for (int v = tid; v < a.NB; v += blockDim.x) {
-        int* irec = reinterpret_cast<int*>(a.bbrec + ((size_t)b * a.NB + v) * a.kRec);
-        irec[0] = 0;
-        irec[1] = -1;
-      }
+      if (tid == 0) ss.k = -1;
     } else {
-      busbar_setup(a, b, k, s_ns, s_st, s_mk, s_dis, s_nd, s_slot, s_e, s_sign, s_coef, s_col, s_Ki, s_psi,
-                   &s_bbisl);
+      const int ne = s_slot[k];
+      if (tid == 0) {
+        ss.k = k;
+        ss.ns = s_ns;
+        ss.nd = s_nd;
+      }
+      for (int i = tid; i <= k; i += blockDim.x) ss.slot[i] = s_slot[i];
+      for (int i = tid; i < TTO_MAX_K; i += blockDim.x) {
+        ss.st[i] = s_st[i];
+        ss.mask[i] = s_mk[i];
+        ss.dis[i] = s_dis[i];
+      }
+      for (int i = tid; i < ne; i += blockDim.x) {
+        ss.e[i] = s_e[i];
+        ss.col[i] = a.swcol[s_e[i]];
+        ss.sign[i] = s_sign[i];
+        ss.coef[i] = s_coef[i];
+      }
+      for (int i = tid; i < TTO_MAX_K * TTO_MAX_K; i += blockDim.x) (&ss.Ki[0][0])[i] = (&s_Ki[0][0])[i];
+      for (int i = tid; i < a.TT * TTO_MAX_K; i += blockDim.x) (&ss.psi[0][0])[i] = (&s_psi[0][0])[i];
     }
   }
   __syncthreads();
@@ -567,7 +606,7 @@ __device__ __forceinline__ void split_update_body(const EvalArgs& a, const int b
     inf.umax = s_umax;
     inf.vmax = s_vmax;
     inf.nd = s_nd;
-    inf.nbisl = dead ? 0 : s_bbisl;
+    inf.nbisl = 0;  // busbar_setup_kernel counts the islanding busbar outages
     a.info[b] = inf;
   }
 }
@@ -819,8 +858,14 @@ int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, 
   if (g->prof_on && !split_only && g->prof_n < kProfileCalls && cap == cudaStreamCaptureStatusNone)
     ev = &g->prof_ev[4 * g->prof_n++];
   if (ev) TTO_CUDA_TRY(cudaEventRecord(ev[0], s));
-  if (bb) split_update_bb_kernel<<<B, 256, 0, s>>>(a);
-  else split_update_kernel<<<B, 256, 0, s>>>(a);
+  if (bb) {
+    split_update_bb_kernel<<<B, 256, 0, s>>>(a);
+    TTO_CUDA_TRY(cudaGetLastError());
+    const size_t n = (size_t)B * a.NB;
+    busbar_setup_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(a);
+  } else {
+    split_update_kernel<<<B, 256, 0, s>>>(a);
+  }
   TTO_CUDA_TRY(cudaGetLastError());
   if (split_only) {
     *split_only = a;

@@ -451,7 +451,7 @@ static void release(tto_grid* g) {
   forget_grid_graphs(g);
   free_workspace(g);
   void* ptrs[] = {g->d_from, g->d_Nf, g->d_Nmo, g->d_Nsw, g->d_Nsw32, g->d_swcol, g->d_Pst, g->d_Pm, g->d_Nswm,
-                  g->d_lbpre, g->d_empty, g->d_bbrec, g->d_bbpart, g->d_f0, g->d_p, g->d_b, g->d_invb, g->d_lim,
+                  g->d_lbpre, g->d_empty, g->d_bbrec, g->d_bbpart, g->d_bbstate, g->d_f0, g->d_p, g->d_b, g->d_invb, g->d_lim,
                   g->d_mon, g->d_out, g->d_Ncc, g->d_station_bus, g->d_asset_off,
                   g->d_asset_br, g->d_act_st, g->d_act_off, g->d_act_mask, g->d_disc, g->d_status};
   for (void* p : ptrs)

@@ -14,6 +14,23 @@ constexpr int kMaxBB = TTO_MAX_ASSETS - 1;
 constexpr int kBBHead = (2 + kMaxBB + 3) / 4 * 4;
 constexpr int bb_record_floats(int TT) { return kBBHead + TT * (1 + kMaxBB + 8); }
 
+// What the busbar setup needs from a topology's split update: the split
+// slots, the moved branch ends (with the switchable column of each), K^-1 and
+// psi per timestep.  k = -1 marks a topology without busbar records.
+struct SplitState {
+  int k, ns, nd, pad;
+  int slot[TTO_MAX_K + 1];
+  int st[TTO_MAX_K];
+  uint32_t mask[TTO_MAX_K];
+  int dis[TTO_MAX_K];
+  int e[kMaxMoved];
+  int col[kMaxMoved];
+  double sign[kMaxMoved];
+  double coef[kMaxMoved];
+  double Ki[TTO_MAX_K][TTO_MAX_K];
+  double psi[TTO_MAX_T][TTO_MAX_K];
+};
+
 struct EvalArgs {
   // grid (device)
   const float* Nmo;
@@ -50,6 +67,7 @@ struct EvalArgs {
   const float* Pm;       // [S][E_mon_pad] the same at the monitored rows
   const float* Nswm;     // [n_sw][E_mon_pad] switchable N columns at the monitored rows
   float* bbrec;          // [B][NB][kRec]
+  SplitState* bbstate;   // [B] split state for the busbar setup
   float* bbpart;         // [B][n_rowtiles] partial lambda_b
   float* bmax;           // [B][n_t][E_mon] max over busbar outages of |flow|, or NULL
   const float* lbpre;    // lambda_b of the unsplit topology

@@ -86,6 +86,7 @@ struct tto_grid {
   int32_t* d_empty = nullptr;  // one all-empty genome (the unsplit topology)
   float* d_bbrec = nullptr;    // busbar outage records [B][S + k_max][record]
   float* d_bbpart = nullptr;   // partial lambda_b [B][row tiles]
+  void* d_bbstate = nullptr;   // split state per topology for the busbar setup [B]
   int bb_cap_B = 0, bb_cap_T = 0;
   double* d_f0 = nullptr;      // [T][E] base flows
   double* d_p = nullptr;       // [T][n_bus]
