@@ -15,8 +15,8 @@
 // would leave below the training noise.  Scores are returned unscaled.
 //
 // Numerics: parameters and Adam moments are FP32; every product rounds both
-// operands to BF16 and accumulates in FP32 (mma.sync m16n8k16 for the dense
-// products).  The station block of the input holds at most k_max non-zero
+// operands to BF16 and accumulates in FP32 (tcgen05.mma kind::f16 with the
+// accumulator in tensor memory for the dense products).  The station block of the input holds at most k_max non-zero
 // 8-value slices per genome, so the first layer adds those slices of W1
 // directly instead of multiplying a mostly-zero matrix, and its gradient is a
 // per-station segmented sum.  Every reduction runs in a fixed order (no
@@ -79,7 +79,6 @@ struct tto_surrogate {
 namespace tto {
 namespace {
 
-constexpr int kBM = 64, kBN = 64, kBK = 32, kPadK = kBK + 8;
 constexpr int kMaxHidden = 1024;
 constexpr int kSortChunk = 2048;  // keys sorted per CTA in shared memory
 
@@ -87,106 +86,317 @@ __device__ __forceinline__ float bf(float x) { return __bfloat162float(__float2b
 
 // ------------------------------------------------------------------ GEMM
 // C[M][N] (ldc) = opA(A) opB(B) + bias[n], then zeroed where mask[m][n] <= 0
-// (mask has C's layout) and/or clamped at 0 (relu).
+// (mask has C's layout) and/or clamped at 0 (relu);
 // opA(m, k) = TA ? A[k lda + m] : A[m lda + k];
 // opB(k, n) = TB ? B[n ldb + k] : B[k ldb + n].
-// 64x64 output tile per 128-thread CTA (2x2 warps of 32x32), K in steps of 32;
-// operands are rounded to BF16 when staged in shared memory.  Split K:
-// blockIdx.z covers k in [z kc, z kc + kc) and writes its partial product to
-// C + z c_split (bias, mask and relu only without a split).
-template <bool TA, bool TB>
-__global__ void __launch_bounds__(128) gemm_bf16_kernel(int M, int N, int K, const float* __restrict__ A,
-                                                        int lda, const float* __restrict__ B, int ldb,
-                                                        float* C, int ldc, const float* __restrict__ bias,
-                                                        const float* __restrict__ mask, int relu, int kc,
-                                                        size_t c_split) {
-  __shared__ __align__(16) __nv_bfloat16 As[kBM][kPadK];
-  __shared__ __align__(16) __nv_bfloat16 Bs[kBN][kPadK];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, q = lane & 3;
-  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  float d[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) d[i][j][r] = 0.f;
-  const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
-  C += blockIdx.z * c_split;
-  for (int k0 = kb; k0 < ke; k0 += kBK) {
-    // consecutive threads read consecutive global addresses in both layouts
-    for (int e = tid; e < kBM * kBK; e += 128) {
-      const int r = TA ? e % kBM : e / kBK, c = TA ? e / kBM : e % kBK;
-      const int m = m0 + r, kk = k0 + c;
-      float v = 0.f;
-      if (m < M && kk < ke) v = TA ? A[(size_t)kk * lda + m] : A[(size_t)m * lda + kk];
-      As[r][c] = __float2bfloat16_rn(v);
-    }
-    for (int e = tid; e < kBN * kBK; e += 128) {
-      const int r = TB ? e / kBK : e % kBN, c = TB ? e % kBK : e / kBN;
-      const int n = n0 + r, kk = k0 + c;
-      float v = 0.f;
-      if (n < N && kk < ke) v = TB ? B[(size_t)n * ldb + kk] : B[(size_t)kk * ldb + n];
-      Bs[r][c] = __float2bfloat16_rn(v);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int ks = 0; ks < kBK; ks += 16) {
-      uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int r = wm + 16 * i + g;
-        af[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][ks + 2 * q]);
-        af[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + 2 * q]);
-        af[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][ks + 2 * q + 8]);
-        af[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + 2 * q + 8]);
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int n = wn + 8 * j + g;
-        bfr[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[n][ks + 2 * q]);
-        bfr[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[n][ks + 2 * q + 8]);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          asm volatile(
-              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-              "{%8,%9}, {%0,%1,%2,%3};"
-              : "+f"(d[i][j][0]), "+f"(d[i][j][1]), "+f"(d[i][j][2]), "+f"(d[i][j][3])
-              : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bfr[j][0]),
-                "r"(bfr[j][1]));
-    }
-    __syncthreads();
+// On the fifth-generation tensor cores: a CTA of 128 threads owns a 128 x 128
+// output tile whose FP32 accumulator lives in 128 columns of tensor memory.
+// K advances 64 at a time through two shared-memory stages: all threads load
+// the FP32 operands, round them to BF16 and store them in the canonical
+// K-major layout without swizzle (core matrices of 8 rows x 16 bytes: 128
+// bytes apart along K, 1024 bytes apart along M / N), then one thread issues
+// four tcgen05.mma kind::f16 (M = 128, N = 128, K = 16, BF16 x BF16 -> FP32)
+// and commits them to the stage's mbarrier, so the loads of the next stage
+// overlap these products.  The epilogue reads the accumulator with
+// tcgen05.ld (thread = row).  Split K: blockIdx.z covers k in [z kc, z kc +
+// kc) and writes its partial product to C + z c_split (bias, mask and relu
+// only without a split).  Every mbarrier wait is bounded (about a second):
+// one that gives up sets TTO_E_TIMEOUT, and the CTA still waits (bounded) for
+// the products it issued before it frees the tensor memory.
+constexpr int kGM = 128, kGN = 128, kGK = 64, kGStages = 2;
+constexpr uint32_t kGTile = kGM * kGK * 2;                  // one BF16 operand tile, 16 KB
+constexpr uint32_t kGSmem = kGStages * 2 * kGTile + 1024;   // + alignment slack
+constexpr long long kGWait = 1ll << 31;
+// instruction descriptor, kind::f16: F32 accumulator (bit 4), A and B BF16
+// (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t kIdescBF16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kGN >> 3) << 17) |
+                                ((uint32_t)(kGM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t g_su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ bool g_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(g_su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; false when it gave up or another thread of the CTA already did.
+__device__ __forceinline__ bool g_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+  if (g_try(b, parity)) return true;
+  const long long t0 = clock64();
+  for (;;) {
+    if (g_try(b, parity)) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kGWait) return false;
   }
+}
+// canonical K-major no-swizzle position of element (r, k) of a 128 x 64 tile
+__device__ __forceinline__ uint32_t g_off(int r, int k) {
+  return (uint32_t)((r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+// shared-memory descriptor of such a tile: start, LBO 128 B (along K), SBO
+// 1024 B (along M / N), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t g_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         (1ull << 46);
+}
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// Stage rows r0 .. r0 + 127 and k k0 .. k0 + 63 of op(X) into a tile:
+// op(r, k) = KMAJ ? X[r ld + k] : X[k ld + r], zero outside [0, R) x [k0, ke).
+// KMAJ: eight threads per row read 32 contiguous floats (16 float4 per
+// thread); otherwise a thread reads four rows at four consecutive k and
+// transposes them in registers (4 blocks of 4 float4 per thread).  The loads
+// of eight float4 are issued before any of them is converted, so that many
+// are in flight at once.  vec: float4 reads allowed (ld and X 16-byte aligned).
+__device__ __forceinline__ float4 g_ld4(const float* __restrict__ X, size_t o, int valid, bool vec) {
+  if (vec && valid >= 4) return __ldg(reinterpret_cast<const float4*>(X + o));
+  float4 x;
+  x.x = valid > 0 ? __ldg(X + o) : 0.f;
+  x.y = valid > 1 ? __ldg(X + o + 1) : 0.f;
+  x.z = valid > 2 ? __ldg(X + o + 2) : 0.f;
+  x.w = valid > 3 ? __ldg(X + o + 3) : 0.f;
+  return x;
+}
+
+template <bool KMAJ>
+__device__ __forceinline__ void g_stage(unsigned char* tile, const float* __restrict__ X, int ld, int r0, int R,
+                                        int k0, int ke, bool vec) {
+  const int tid = threadIdx.x;
+  if (KMAJ) {
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+    for (int h = 0; h < 2; ++h) {
+      float4 x[8];
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int m = m0 + wm + 16 * i + g + (r >= 2 ? 8 : 0);
-        const int n = n0 + wn + 8 * j + 2 * q + (r & 1);
-        if (m >= M || n >= N) continue;
-        float v = d[i][j][r];
-        if (bias) v += bias[n];
-        if (mask && !(mask[(size_t)m * ldc + n] > 0.f)) v = 0.f;
-        if (relu) v = fmaxf(v, 0.f);
-        C[(size_t)m * ldc + n] = v;
+      for (int i = 0; i < 8; ++i) {
+        const int idx = (h * 8 + i) * 128 + tid;
+        const int r = (idx >> 3) & 127, k = ((idx >> 10) << 5) + ((idx & 7) << 2);
+        const int gr = r0 + r, gk = k0 + k;
+        x[i] = gr < R ? g_ld4(X, (size_t)gr * ld + gk, ke - gk, vec) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int idx = (h * 8 + i) * 128 + tid;
+        const int r = (idx >> 3) & 127, k = ((idx >> 10) << 5) + ((idx & 7) << 2);
+        uint2 w;
+        w.x = pack_bf16x2(x[i].x, x[i].y);
+        w.y = pack_bf16x2(x[i].z, x[i].w);
+        *reinterpret_cast<uint2*>(tile + g_off(r, k)) = w;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float4 x[2][4];  // two 4 x 4 blocks: x[b][j] = rows r .. r + 3 at k + j
+#pragma unroll
+      for (int bI = 0; bI < 2; ++bI) {
+        const int idx = (h * 2 + bI) * 128 + tid;
+        const int r = (idx & 31) << 2, k = (idx >> 5) << 2;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int gk = k0 + k + j, gr = r0 + r;
+          x[bI][j] = gk < ke ? g_ld4(X, (size_t)gk * ld + gr, R - gr, vec) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+#pragma unroll
+      for (int bI = 0; bI < 2; ++bI) {
+        const int idx = (h * 2 + bI) * 128 + tid;
+        const int r = (idx & 31) << 2, k = (idx >> 5) << 2;
+        const float4* v = x[bI];
+        uint2 w;
+        w.x = pack_bf16x2(v[0].x, v[1].x), w.y = pack_bf16x2(v[2].x, v[3].x);
+        *reinterpret_cast<uint2*>(tile + g_off(r, k)) = w;
+        w.x = pack_bf16x2(v[0].y, v[1].y), w.y = pack_bf16x2(v[2].y, v[3].y);
+        *reinterpret_cast<uint2*>(tile + g_off(r + 1, k)) = w;
+        w.x = pack_bf16x2(v[0].z, v[1].z), w.y = pack_bf16x2(v[2].z, v[3].z);
+        *reinterpret_cast<uint2*>(tile + g_off(r + 2, k)) = w;
+        w.x = pack_bf16x2(v[0].w, v[1].w), w.y = pack_bf16x2(v[2].w, v[3].w);
+        *reinterpret_cast<uint2*>(tile + g_off(r + 3, k)) = w;
+      }
+    }
+  }
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(128) gemm_umma_kernel(int M, int N, int K, const float* __restrict__ A, int lda,
+                                                        const float* __restrict__ B, int ldb, float* C, int ldc,
+                                                        const float* __restrict__ bias,
+                                                        const float* __restrict__ mask, int relu, int kc,
+                                                        size_t c_split, int* status) {
+  extern __shared__ unsigned char g_smem_raw[];
+  unsigned char* smem = g_smem_raw + ((1024u - (g_su32(g_smem_raw) & 1023u)) & 1023u);
+  __shared__ __align__(8) uint64_t mbar[kGStages], done;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  volatile int* abort_flag = &s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * kGM, n0 = blockIdx.x * kGN;
+  const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
+  const int nk = ke > kb ? (ke - kb + kGK - 1) / kGK : 0;
+  C += blockIdx.z * c_split;
+  const bool vecA = ((lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+  const bool vecB = ((ldb & 3) == 0) && ((reinterpret_cast<uintptr_t>(B) & 15) == 0);
+  if (tid == 0) {
+    for (int i = 0; i < kGStages; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(g_su32(&mbar[i])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(g_su32(&done)) : "memory");
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(g_su32(&s_tmem)),
+                 "r"(kGN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+  bool ok = true;
+  for (int kt = 0; kt < nk; ++kt) {
+    const int st = kt & 1;
+    unsigned char* sa = smem + st * 2 * kGTile;
+    unsigned char* sb = sa + kGTile;
+    // the products that read this stage two steps ago must be complete
+    if (kt >= kGStages) ok = g_wait(&mbar[st], (uint32_t)((kt >> 1) - 1) & 1u, abort_flag);
+    if (!__syncthreads_and(ok)) {
+      ok = false;
+      break;
+    }
+    const int k0 = kb + kt * kGK;
+    g_stage<!TA>(sa, A, lda, m0, M, k0, ke, vecA);
+    g_stage<TB>(sb, B, ldb, n0, N, k0, ke, vecB);
+    // the generic-proxy stores must be visible to the tensor core (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint64_t da = g_desc(g_su32(sa)), db = g_desc(g_su32(sb));
+#pragma unroll
+      for (int kk = 0; kk < kGK / 16; ++kk) {
+        // K = 16 per product: two core matrices, 256 bytes (16 units) along K
+        const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+            "l"(da + (uint64_t)(16 * kk)), "l"(db + (uint64_t)(16 * kk)), "r"(kIdescBF16), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       g_su32(&mbar[st]))
+                   : "memory");
+    }
+  }
+  // every product issued by this CTA, complete (also on the error path)
+  if (tid == 0 && nk > 0)
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(g_su32(&done))
+                 : "memory");
+  if (nk > 0) {
+    int dummy = 0;
+    const bool fin = g_wait(&done, 0, &dummy);
+    ok = ok && fin;
+  }
+  if (!__syncthreads_and(ok)) {
+    if (tid == 0) atomicExch(status, TTO_E_TIMEOUT);
+  } else {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int row = m0 + warp * 32 + lane;
+    const bool vecC = ((ldc & 3) == 0) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0) &&
+                      (!mask || (reinterpret_cast<uintptr_t>(mask) & 15) == 0);
+#pragma unroll 1
+    for (int c0 = 0; c0 < kGN; c0 += 32) {
+      uint32_t r[32];
+      if (nk > 0) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+            "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+              "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+              "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+              "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) r[j] = 0u;
+      }
+      if (row >= M) continue;
+      float* crow = C + (size_t)row * ldc;
+      const float* mrow = mask ? mask + (size_t)row * ldc : nullptr;
+#pragma unroll
+      for (int j4 = 0; j4 < 32; j4 += 4) {
+        const int n = n0 + c0 + j4;
+        float v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          v[j] = __uint_as_float(r[j4 + j]);
+          if (bias && n + j < N) v[j] += bias[n + j];
+        }
+        if (vecC && n + 3 < N) {
+          if (mrow) {
+            const float4 mk = *reinterpret_cast<const float4*>(mrow + n);
+            v[0] = mk.x > 0.f ? v[0] : 0.f, v[1] = mk.y > 0.f ? v[1] : 0.f;
+            v[2] = mk.z > 0.f ? v[2] : 0.f, v[3] = mk.w > 0.f ? v[3] : 0.f;
+          }
+          if (relu)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] = fmaxf(v[j], 0.f);
+          *reinterpret_cast<float4*>(crow + n) = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (n + j >= N) continue;
+            float x = v[j];
+            if (mrow && !(mrow[n + j] > 0.f)) x = 0.f;
+            if (relu) x = fmaxf(x, 0.f);
+            crow[n + j] = x;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kGN) : "memory");
+  }
+}
+
+template <bool TA, bool TB>
+int launch_gemm(dim3 grid, int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
+                const float* bias, const float* mask, bool relu, int kc, size_t c_split, int* status,
+                cudaStream_t s) {
+  static bool attr[64] = {};
+  int dev = 0;
+  TTO_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return set_error(TTO_E_ARG, "device %d out of range", dev);
+  if (!attr[dev]) {
+    TTO_CUDA_TRY(cudaFuncSetAttribute(gemm_umma_kernel<TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kGSmem));
+    attr[dev] = true;
+  }
+  gemm_umma_kernel<TA, TB><<<grid, 128, kGSmem, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, mask, relu ? 1 : 0, kc,
+                                                     c_split, status);
+  TTO_CUDA_TRY(cudaGetLastError());
+  return TTO_OK;
 }
 
 template <bool TA, bool TB>
 int gemm(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
-         const float* bias, const float* mask, bool relu, cudaStream_t s) {
+         const float* bias, const float* mask, bool relu, int* status, cudaStream_t s) {
   if (M <= 0 || N <= 0) return TTO_OK;
-  const dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM);
+  const dim3 grid((N + kGN - 1) / kGN, (M + kGM - 1) / kGM);
   if (grid.y > 65535) return set_error(TTO_E_ARG, "surrogate batch too large for one product");
-  gemm_bf16_kernel<TA, TB><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, mask, relu ? 1 : 0, K, 0);
-  TTO_CUDA_TRY(cudaGetLastError());
-  return TTO_OK;
+  return launch_gemm<TA, TB>(grid, M, N, K, A, lda, B, ldb, C, ldc, bias, mask, relu, K, 0, status, s);
 }
 
 // out[m][n] (ldo) = sum over z in order of part[z][m][n]
@@ -204,17 +414,18 @@ constexpr int kMaxSplitK = 16;
 // few output tiles and a long K, so K is split over up to 16 CTAs per tile
 // whose partials (in ws, kMaxSplitK * M * N floats) are summed in a fixed order.
 int gemm_wgrad(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc, float* ws,
-               cudaStream_t s) {
+               int* status, cudaStream_t s) {
   if (M <= 0 || N <= 0) return TTO_OK;
-  const int tiles = ((N + kBN - 1) / kBN) * ((M + kBM - 1) / kBM);
-  int splits = std::max(1, std::min(kMaxSplitK, (4 * 148 + tiles - 1) / tiles));
+  const int tiles = ((N + kGN - 1) / kGN) * ((M + kGM - 1) / kGM);
+  int splits = std::max(1, std::min(kMaxSplitK, (3 * 148 + tiles - 1) / tiles));
   splits = std::max(1, std::min(splits, (K + 255) / 256));
-  const int kc = ((K + splits - 1) / splits + kBK - 1) / kBK * kBK;
+  const int kc = ((K + splits - 1) / splits + kGK - 1) / kGK * kGK;
   splits = (K + kc - 1) / kc;
-  if (splits <= 1) return gemm<true, false>(M, N, K, A, lda, B, ldb, C, ldc, nullptr, nullptr, false, s);
-  const dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM, splits);
-  gemm_bf16_kernel<true, false><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, ws, N, nullptr, nullptr, 0, kc,
-                                                     (size_t)M * N);
+  if (splits <= 1) return gemm<true, false>(M, N, K, A, lda, B, ldb, C, ldc, nullptr, nullptr, false, status, s);
+  const dim3 grid((N + kGN - 1) / kGN, (M + kGM - 1) / kGM, splits);
+  int rc = launch_gemm<true, false>(grid, M, N, K, A, lda, B, ldb, ws, N, nullptr, nullptr, false, kc, (size_t)M * N,
+                                    status, s);
+  if (rc) return rc;
   const size_t n = (size_t)M * N;
   splitk_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(M, N, splits, ws, C, ldc);
   TTO_CUDA_TRY(cudaGetLastError());
@@ -957,13 +1168,13 @@ int forward(tto_surrogate* s, int B, const int* valid, cudaStream_t st) {
   const float* P = s->P;
   const int H = s->H, D = s->D, R = s->R;
   int rc = gemm<false, true>(B, H, R, s->XD, R, P + s->oW1 + 8 * (size_t)s->S, D, s->H1, H, P + s->ob1, nullptr,
-                             false, st);
+                             false, s->g->d_status, st);
   if (rc) return rc;
   const size_t n = (size_t)B * H;
   station_terms_relu_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(B, H, s->k, s->SI, s->SF, s->W1sT, s->H1);
   TTO_CUDA_TRY(cudaGetLastError());
-  if ((rc = gemm<false, true>(B, H, H, s->H1, H, P + s->oW2, H, s->H2, H, P + s->ob2, nullptr, true, st))) return rc;
-  if ((rc = gemm<false, true>(B, H, H, s->H2, H, P + s->oW3, H, s->H3, H, P + s->ob3, nullptr, true, st))) return rc;
+  if ((rc = gemm<false, true>(B, H, H, s->H1, H, P + s->oW2, H, s->H2, H, P + s->ob2, nullptr, true, s->g->d_status, st))) return rc;
+  if ((rc = gemm<false, true>(B, H, H, s->H2, H, P + s->oW3, H, s->H3, H, P + s->ob3, nullptr, true, s->g->d_status, st))) return rc;
   output_kernel<<<(unsigned)(((size_t)B * 32 + 255) / 256), 256, 0, st>>>(B, H, s->H3, P + s->ow4, P + s->ob4, valid,
                                                                          valid ? s->stats : nullptr, s->Y);
   TTO_CUDA_TRY(cudaGetLastError());
@@ -985,13 +1196,13 @@ int backward(tto_surrogate* s, int M, cudaStream_t st) {
   out_back_kernel<<<nb, 256, 0, st>>>(M, H, s->dY, P + s->ow4, s->H3, s->dH3);
   TTO_CUDA_TRY(cudaGetLastError());
   int rc;
-  if ((rc = gemm_wgrad(H, H, M, s->dH3, H, s->H2, H, G + s->oW3, H, s->wsk, st))) return rc;
+  if ((rc = gemm_wgrad(H, H, M, s->dH3, H, s->H2, H, G + s->oW3, H, s->wsk, s->g->d_status, st))) return rc;
   colsum_kernel<<<ncs, cs, 0, st>>>(M, H, s->dH3, nullptr, G + s->ob3);
-  if ((rc = gemm<false, false>(M, H, H, s->dH3, H, P + s->oW3, H, s->dH2, H, nullptr, s->H2, false, st))) return rc;
-  if ((rc = gemm_wgrad(H, H, M, s->dH2, H, s->H1, H, G + s->oW2, H, s->wsk, st))) return rc;
+  if ((rc = gemm<false, false>(M, H, H, s->dH3, H, P + s->oW3, H, s->dH2, H, nullptr, s->H2, false, s->g->d_status, st))) return rc;
+  if ((rc = gemm_wgrad(H, H, M, s->dH2, H, s->H1, H, G + s->oW2, H, s->wsk, s->g->d_status, st))) return rc;
   colsum_kernel<<<ncs, cs, 0, st>>>(M, H, s->dH2, nullptr, G + s->ob2);
-  if ((rc = gemm<false, false>(M, H, H, s->dH2, H, P + s->oW2, H, s->dH1, H, nullptr, s->H1, false, st))) return rc;
-  if ((rc = gemm_wgrad(H, R, M, s->dH1, H, s->XD, R, G + s->oW1 + 8 * (size_t)s->S, D, s->wsk, st))) return rc;
+  if ((rc = gemm<false, false>(M, H, H, s->dH2, H, P + s->oW2, H, s->dH1, H, nullptr, s->H1, false, s->g->d_status, st))) return rc;
+  if ((rc = gemm_wgrad(H, R, M, s->dH1, H, s->XD, R, G + s->oW1 + 8 * (size_t)s->S, D, s->wsk, s->g->d_status, st))) return rc;
   colsum_kernel<<<ncs, cs, 0, st>>>(M, H, s->dH1, nullptr, G + s->ob1);
   station_grad_kernel<<<s->S, 256, 0, st>>>(M, H, D, s->k, s->SI, s->SF, s->dH1, G + s->oW1);
   TTO_CUDA_TRY(cudaGetLastError());
