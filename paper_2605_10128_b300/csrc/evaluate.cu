@@ -32,7 +32,23 @@ namespace tto {
 // ------------------------------------------------------- factor layouts
 // U [B][E_mon_pad][8], V [B][O_pad][8], g [B][O_pad][TT] in FP32; the
 // tensor-core sweep repacks them into mma fragment order (sweep_tc.cu).
+// With a.umma_packed (the tcgen05 sweep follows) the factors go straight into
+// that sweep's operand layouts: U rows -> [B][band][hi, lo][128 x 8] and V
+// columns -> [B][64-column chunk][hi, lo][64 x 8] as TF32 hi/lo splits in the
+// canonical K-major layout, g -> [B][t-pass][O_pad / 2][TC][2] with the two
+// columns of a pair interleaved per timestep.
 __device__ __forceinline__ void store_row_factors(const EvalArgs& a, int b, int l, const float* u) {
+  if (a.umma_packed) {
+    uint32_t* base = a.Ua + ((size_t)b * (a.E_mon_pad >> 7) + (l >> 7)) * 2048;
+    const int r = l & 127;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t hi = tf32_bits(u[k]);
+      base[canon(r, k)] = hi;
+      base[1024 + canon(r, k)] = tf32_bits(u[k] - __uint_as_float(hi));
+    }
+    return;
+  }
   float4* Urow = reinterpret_cast<float4*>(a.U + ((size_t)b * a.E_mon_pad + l) * 8);
   Urow[0] = make_float4(u[0], u[1], u[2], u[3]);
   Urow[1] = make_float4(u[4], u[5], u[6], u[7]);
@@ -40,6 +56,20 @@ __device__ __forceinline__ void store_row_factors(const EvalArgs& a, int b, int 
 
 __device__ __forceinline__ void store_col_factors(const EvalArgs& a, int b, int c, const float* v,
                                                   const float* gv) {
+  if (a.umma_packed) {
+    uint32_t* base = a.Vb + ((size_t)b * (a.O_pad >> 6) + (c >> 6)) * 1024;
+    const int n = c & 63;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t hi = tf32_bits(v[k]);
+      base[canon(n, k)] = hi;
+      base[512 + canon(n, k)] = tf32_bits(v[k] - __uint_as_float(hi));
+    }
+    for (int ci = 0; ci < a.n_tch; ++ci)
+      for (int t = 0; t < a.TC; ++t)
+        a.gq[((((size_t)b * a.n_tch + ci) * (a.O_pad / 2) + c / 2) * a.TC + t) * 2 + (c & 1)] = gv[ci * a.TC + t];
+    return;
+  }
   float4* Vrow = reinterpret_cast<float4*>(a.V + ((size_t)b * a.O_pad + c) * 8);
   Vrow[0] = make_float4(v[0], v[1], v[2], v[3]);
   Vrow[1] = make_float4(v[4], v[5], v[6], v[7]);
@@ -846,6 +876,13 @@ int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, 
   a.n_parts = g->n_rowtiles;
   a.precision = o->precision;
   a.shape = g->tuned_shape[o->precision] >= 0 ? g->tuned_shape[o->precision] : 0;
+  // the tcgen05 sweep follows: the split update writes its operand layouts
+  // directly (no plain U, V, g), with its timestep passes of at most 4
+  a.umma_packed = (!split_only && !bb && a.precision == TTO_PREC_TF32X3 && a.shape == kUmmaShape) ? 1 : 0;
+  if (a.umma_packed) {
+    a.TC = TT < 4 ? TT : 4;
+    a.n_tch = TT / a.TC;
+  }
   a.from = g->d_from;
   if (bb) fill_busbar_args(g, a);
   if (prepare_only) {  // arguments only: the caller launches (mixed-grid batches)

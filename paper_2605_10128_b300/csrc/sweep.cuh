@@ -76,6 +76,7 @@ struct EvalArgs {
   int n_rowtiles;
   int n_parts;  // partial-metric records per topology (set by the sweep launcher)
   int shape;    // sweep tile variant chosen by the autotuner (0 = default)
+  int umma_packed;  // the split update writes the tcgen05 operand layouts (Ua, Vb, gq) instead of U, V, g
   // batch
   const int32_t* topo;
   int B;
@@ -118,6 +119,17 @@ struct MultiArgs {
   unsigned int* counter;                        // next sweep item (zeroed before the launch)
   EvalArgs job[kMaxMultiJobs];
 };
+
+// TF32 operand layouts of the tcgen05 sweep: the round-to-nearest TF32 bits of
+// x, and the canonical K-major no-swizzle position of element (row, k) in a
+// tile of 8-column rows: core matrix (row / 8, k / 4) at 256 (row / 8) +
+// 128 (k / 4) bytes, 16 bytes per core-matrix row (in 32-bit words).
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ int canon(int row, int k) { return (row >> 3) * 64 + (k >> 2) * 32 + (row & 7) * 4 + (k & 3); }
 
 // Launch the fused N-1 sweep for the precision in a.precision; sets a.n_parts.
 int launch_sweep(EvalArgs& a, cudaStream_t s);

@@ -511,17 +511,6 @@ __global__ void __launch_bounds__(kUThreads, 1)
   }
 }
 
-__device__ __forceinline__ uint32_t tf32_bits(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-
-// Canonical K-major no-swizzle position of element (row, k) in a tile of
-// 8-column rows: core matrix (row / 8, k / 4) at 256 (row / 8) + 128 (k / 4)
-// bytes, 16 bytes per core-matrix row.
-__device__ __forceinline__ int canon(int row, int k) { return (row >> 3) * 64 + (k >> 2) * 32 + (row & 7) * 4 + (k & 3); }
-
 // U rows -> [B][band][hi, lo][128 x 8]; V columns -> [B][chunk][hi, lo][64 x 8];
 // g -> [B][t-chunk][O_pad / 2][TC][2], column pairs interleaved (zero beyond
 // the padded timesteps).
@@ -620,9 +609,11 @@ int launch_sweep_umma(EvalArgs& a, cudaStream_t s) {
   // stay in registers); more timesteps take more passes
   a.TC = a.TT < 4 ? a.TT : 4;
   a.n_tch = a.TT / a.TC;
-  const size_t threads = ((size_t)a.E_mon_pad + a.O_pad) * a.B;
-  pack_umma_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
-  TTO_CUDA_TRY(cudaGetLastError());
+  if (!a.umma_packed) {  // the split update did not write the operand layouts itself
+    const size_t threads = ((size_t)a.E_mon_pad + a.O_pad) * a.B;
+    pack_umma_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
+    TTO_CUDA_TRY(cudaGetLastError());
+  }
   a.n_parts = (a.E_mon_pad / 32) * a.n_tch;
   for (int ci = 0; ci < a.n_tch; ++ci) {
     int rc;
