@@ -32,7 +32,9 @@ from synth import CONFIGS, config_grid, limits_from_flows, random_topologies  # 
 
 METRIC = "N-1 topology evals/s (10k-bus)"
 UNIT = "evals/s"
-LAUNCHES_PER_STEP = 8  # propose, split update, sweep, metrics, 4 insert kernels (+1 pack for the mma.sync sweeps)
+# propose, split update, sweep, metrics, 4 insert kernels (+1 pack for the mma.sync sweeps; +2 with lambda_f2:
+# the busbar setup and the busbar sweep)
+LAUNCHES_PER_STEP = 8
 
 
 def rank_seed(rank):
@@ -640,7 +642,8 @@ def main():
                     "d2h_bytes_per_step": int(B * 4)},
             # the mma.sync sweeps repack U, V and g in a launch of their own; for the
             # tcgen05 sweep (variant 4) the split update writes its operand layouts
-            "gpu_launches": (LAUNCHES_PER_STEP + (0 if prec == PREC_FP32 or tuned_shape == 4 else 1)) * args.steps,
+            "gpu_launches": (LAUNCHES_PER_STEP + (0 if prec == PREC_FP32 or tuned_shape == 4 else 1)
+                             + (2 if args.fitness == "f2" else 0)) * args.steps,
             "clocks": clk,
             "cpu_baseline": cpu,
         }

@@ -36,7 +36,8 @@ namespace tto {
 // that sweep's operand layouts: U rows -> [B][band][hi, lo][128 x 8] and V
 // columns -> [B][64-column chunk][hi, lo][64 x 8] as TF32 hi/lo splits in the
 // canonical K-major layout, g -> [B][t-pass][O_pad / 2][TC][2] with the two
-// columns of a pair interleaved per timestep.
+// columns of a pair interleaved per timestep (and U rows in plain order too
+// when the busbar sweep follows).
 __device__ __forceinline__ void store_row_factors(const EvalArgs& a, int b, int l, const float* u) {
   if (a.umma_packed) {
     uint32_t* base = a.Ua + ((size_t)b * (a.E_mon_pad >> 7) + (l >> 7)) * 2048;
@@ -47,7 +48,7 @@ __device__ __forceinline__ void store_row_factors(const EvalArgs& a, int b, int 
       base[canon(r, k)] = hi;
       base[1024 + canon(r, k)] = tf32_bits(u[k] - __uint_as_float(hi));
     }
-    return;
+    if (!a.busbar) return;  // the busbar sweep reads the plain U rows as well
   }
   float4* Urow = reinterpret_cast<float4*>(a.U + ((size_t)b * a.E_mon_pad + l) * 8);
   Urow[0] = make_float4(u[0], u[1], u[2], u[3]);
@@ -877,8 +878,9 @@ int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, 
   a.precision = o->precision;
   a.shape = g->tuned_shape[o->precision] >= 0 ? g->tuned_shape[o->precision] : 0;
   // the tcgen05 sweep follows: the split update writes its operand layouts
-  // directly (no plain U, V, g), with its timestep passes of at most 4
-  a.umma_packed = (!split_only && !bb && a.precision == TTO_PREC_TF32X3 && a.shape == kUmmaShape) ? 1 : 0;
+  // directly (no plain V, g; plain U only for the busbar sweep), with its
+  // timestep passes of at most 4
+  a.umma_packed = (!split_only && a.precision == TTO_PREC_TF32X3 && a.shape == kUmmaShape) ? 1 : 0;
   if (a.umma_packed) {
     a.TC = TT < 4 ? TT : 4;
     a.n_tch = TT / a.TC;

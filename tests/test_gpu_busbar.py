@@ -79,16 +79,23 @@ def test_busbar_outages_tto2k_sampled():
     assert _check(sg, _run(g, topo), idx, _oracle(sg, topo, idx)) >= 1
 
 
-def test_lambda_f2_fitness():
-    from paper_2605_10128_b300 import Grid, TTOError, FIT_F2
+@pytest.mark.parametrize("mode", ["fp32", "tcgen05", "mma"])
+def test_lambda_f2_fitness(mode):
+    """lambda_f2 with the N-1 sweep in FP32, on the tcgen05 kernel (whose
+    operand layouts the split update writes, plain U rows kept for the busbar
+    sweep) and on an mma.sync variant."""
+    from paper_2605_10128_b300 import Grid, TTOError, FIT_F2, PREC_FP32, PREC_TF32X3
     sg = _grid("tto30", 5)
     g = Grid(sg)
+    prec = PREC_FP32 if mode == "fp32" else PREC_TF32X3
+    if mode != "fp32":
+        g.set_sweep_shape(PREC_TF32X3, 4 if mode == "tcgen05" else 0)
     topo = random_topologies(sg, 48, seed=11)
     t = torch.tensor(topo, dtype=torch.int32, device="cuda")
     with pytest.raises(TTOError):
-        g.evaluate(t, fitness_kind=FIT_F2)
+        g.evaluate(t, fitness_kind=FIT_F2, precision=prec)
     g.busbar_reference()
-    out = g.evaluate(t, fitness_kind=FIT_F2, metrics=True, fmax=True)
+    out = g.evaluate(t, fitness_kind=FIT_F2, metrics=True, fmax=True, precision=prec)
     g.sync_status()
     out = {k: v.cpu().numpy() for k, v in out.items() if not k.startswith("_")}
     idx = list(range(len(topo)))
@@ -110,7 +117,7 @@ def test_lambda_f2_fitness():
     # changing the limits drops the reference
     g.set_limits(sg.limit * 1.01)
     with pytest.raises(TTOError):
-        g.evaluate(t, fitness_kind=FIT_F2)
+        g.evaluate(t, fitness_kind=FIT_F2, precision=prec)
 
 
 @pytest.mark.parametrize("T", [2, 5, 24, 32])
