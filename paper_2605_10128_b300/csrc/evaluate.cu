@@ -42,12 +42,17 @@ __device__ __forceinline__ void store_row_factors(const EvalArgs& a, int b, int 
   if (a.umma_packed) {
     uint32_t* base = a.Ua + ((size_t)b * (a.E_mon_pad >> 7) + (l >> 7)) * 2048;
     const int r = l & 127;
+    uint32_t hi[8], lo[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const uint32_t hi = tf32_bits(u[k]);
-      base[canon(r, k)] = hi;
-      base[1024 + canon(r, k)] = tf32_bits(u[k] - __uint_as_float(hi));
+      hi[k] = tf32_bits(u[k]);
+      lo[k] = tf32_bits(u[k] - __uint_as_float(hi[k]));
     }
+    // k = 0-3 and 4-7 of a row are 16 contiguous bytes each in the canonical layout
+    *reinterpret_cast<uint4*>(base + canon(r, 0)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    *reinterpret_cast<uint4*>(base + canon(r, 4)) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+    *reinterpret_cast<uint4*>(base + 1024 + canon(r, 0)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    *reinterpret_cast<uint4*>(base + 1024 + canon(r, 4)) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
     if (!a.busbar) return;  // the busbar sweep reads the plain U rows as well
   }
   float4* Urow = reinterpret_cast<float4*>(a.U + ((size_t)b * a.E_mon_pad + l) * 8);
@@ -60,12 +65,16 @@ __device__ __forceinline__ void store_col_factors(const EvalArgs& a, int b, int 
   if (a.umma_packed) {
     uint32_t* base = a.Vb + ((size_t)b * (a.O_pad >> 6) + (c >> 6)) * 1024;
     const int n = c & 63;
+    uint32_t hi[8], lo[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const uint32_t hi = tf32_bits(v[k]);
-      base[canon(n, k)] = hi;
-      base[512 + canon(n, k)] = tf32_bits(v[k] - __uint_as_float(hi));
+      hi[k] = tf32_bits(v[k]);
+      lo[k] = tf32_bits(v[k] - __uint_as_float(hi[k]));
     }
+    *reinterpret_cast<uint4*>(base + canon(n, 0)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    *reinterpret_cast<uint4*>(base + canon(n, 4)) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+    *reinterpret_cast<uint4*>(base + 512 + canon(n, 0)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    *reinterpret_cast<uint4*>(base + 512 + canon(n, 4)) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
     for (int ci = 0; ci < a.n_tch; ++ci)
       for (int t = 0; t < a.TC; ++t)
         a.gq[((((size_t)b * a.n_tch + ci) * (a.O_pad / 2) + c / 2) * a.TC + t) * 2 + (c & 1)] = gv[ci * a.TC + t];
