@@ -60,8 +60,7 @@ __device__ __forceinline__ void store_row_factors(const EvalArgs& a, int b, int 
   Urow[1] = make_float4(u[4], u[5], u[6], u[7]);
 }
 
-__device__ __forceinline__ void store_col_factors(const EvalArgs& a, int b, int c, const float* v,
-                                                  const float* gv) {
+__device__ __forceinline__ void store_col_v(const EvalArgs& a, int b, int c, const float* v) {
   if (a.umma_packed) {
     uint32_t* base = a.Vb + ((size_t)b * (a.O_pad >> 6) + (c >> 6)) * 1024;
     const int n = c & 63;
@@ -75,16 +74,20 @@ __device__ __forceinline__ void store_col_factors(const EvalArgs& a, int b, int 
     *reinterpret_cast<uint4*>(base + canon(n, 4)) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
     *reinterpret_cast<uint4*>(base + 512 + canon(n, 0)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     *reinterpret_cast<uint4*>(base + 512 + canon(n, 4)) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
-    for (int ci = 0; ci < a.n_tch; ++ci)
-      for (int t = 0; t < a.TC; ++t)
-        a.gq[((((size_t)b * a.n_tch + ci) * (a.O_pad / 2) + c / 2) * a.TC + t) * 2 + (c & 1)] = gv[ci * a.TC + t];
     return;
   }
   float4* Vrow = reinterpret_cast<float4*>(a.V + ((size_t)b * a.O_pad + c) * 8);
   Vrow[0] = make_float4(v[0], v[1], v[2], v[3]);
   Vrow[1] = make_float4(v[4], v[5], v[6], v[7]);
-  float* grow = a.gg + ((size_t)b * a.O_pad + c) * a.TT;
-  for (int t = 0; t < a.TT; ++t) grow[t] = gv[t];
+}
+
+// g of column c at padded timestep t = ci TC + tt (timestep pass ci, position
+// tt within it; the packed layout's passes, the plain layout ignores them).
+__device__ __forceinline__ void store_col_g(const EvalArgs& a, int b, int c, int t, int ci, int tt, float g) {
+  if (a.umma_packed)
+    a.gq[((((size_t)b * a.n_tch + ci) * (a.O_pad / 2) + c / 2) * a.TC + tt) * 2 + (c & 1)] = g;
+  else
+    a.gg[((size_t)b * a.O_pad + c) * a.TT + t] = g;
 }
 
 // ------------------------------------------------------ busbar outage setup
@@ -475,14 +478,19 @@ __device__ __forceinline__ void split_update_body(const EvalArgs& a, const int b
   int c0cnt = 0;
   float umax = 0.f, vmax = 0.f;
   // monitored rows: f', U
+  // The FP32 loops over the k split slots are unrolled to TTO_MAX_K
+  // (predicated on k, which is uniform over the CTA) so that the per-slot
+  // arrays stay in registers; timesteps are stored as they are computed.
   for (int l = tid; l < a.E_mon_pad; l += blockDim.x) {
     const int lr = min(l, a.E_mon - 1);
     const int e = a.mon[lr];
+    float* fpr = a.fp + (size_t)b * TT * a.E_mon_pad + l;  // f' of row l, timestep t at t E_mon_pad
     float u[TTO_MAX_K];
     if (dead) {
+#pragma unroll
       for (int j = 0; j < TTO_MAX_K; ++j) u[j] = 0.f;
       store_row_factors(a, b, l, u);
-      for (int t = 0; t < TT; ++t) a.fp[((size_t)b * TT + t) * a.E_mon_pad + l] = 0.f;
+      for (int t = 0; t < TT; ++t) fpr[(size_t)t * a.E_mon_pad] = 0.f;
       continue;
     }
     // FP32 first (B300's FP64 pipe is narrow): W from the FP32 copy of the N
@@ -493,72 +501,86 @@ __device__ __forceinline__ void split_update_body(const EvalArgs& a, const int b
     // |W|_j |psi_j|) with |W|_j the sum of the absolute W terms.  A row whose
     // bound exceeds 1e-5 of its limit is recomputed in FP64.
     float Wf[TTO_MAX_K], Wa[TTO_MAX_K];
-    for (int j = 0; j < k; ++j) {
+#pragma unroll
+    for (int j = 0; j < TTO_MAX_K; ++j) {
       float w = 0.f, wa = 0.f;
-      for (int q = s_slot[j]; q < s_slot[j + 1]; ++q) {
-        const float n = s_col32[q][e];
-        w = fmaf(s_coef32[q], n, w);
-        wa = fmaf(fabsf(s_coef32[q]), fabsf(n), wa);
-      }
+      if (j < k)
+        for (int q = s_slot[j]; q < s_slot[j + 1]; ++q) {
+          const float n = s_col32[q][e];
+          w = fmaf(s_coef32[q], n, w);
+          wa = fmaf(fabsf(s_coef32[q]), fabsf(n), wa);
+        }
       Wf[j] = w;
       Wa[j] = wa;
     }
     // U of a monitored row only enters the TF32-split contraction: FP32 is
     // exact enough
+#pragma unroll
     for (int jj = 0; jj < TTO_MAX_K; ++jj) {
       float uu = 0.f;
-      if (jj < k)
-        for (int j = 0; j < k; ++j) uu = fmaf(Wf[j], s_Kif[j][jj], uu);
+#pragma unroll
+      for (int j = 0; j < TTO_MAX_K; ++j)
+        if (jj < k && j < k) uu = fmaf(Wf[j], s_Kif[j][jj], uu);
       u[jj] = uu;
-      umax = fmaxf(umax, fabsf(u[jj]));
+      umax = fmaxf(umax, fabsf(uu));
     }
     store_row_factors(a, b, l, u);
     const float lim = a.lim[lr];
-    float fv[TTO_MAX_T];
     bool fp32_ok = true;
+    int c0row = 0;
     for (int t = 0; t < TT; ++t) {
-      fv[t] = 0.f;
+      float fv = 0.f;
       if (t < nt) {
         const float f0 = (float)a.f0[(size_t)a.tsel[t] * a.E + e];
         float f = f0, bound = fabsf(f0);
-        for (int j = 0; j < k; ++j) {
-          f = fmaf(Wf[j], s_psi32[t][j], f);
-          bound = fmaf(Wa[j], fabsf(s_psi32[t][j]), bound);
-        }
-        fv[t] = f;
+#pragma unroll
+        for (int j = 0; j < TTO_MAX_K; ++j)
+          if (j < k) {
+            f = fmaf(Wf[j], s_psi32[t][j], f);
+            bound = fmaf(Wa[j], fabsf(s_psi32[t][j]), bound);
+          }
+        fv = f;
         fp32_ok = fp32_ok && bound * (32.f / 16777216.f) <= 1e-5f * lim;
+        if (l < a.E_mon && fabsf(f) > lim) ++c0row;
       }
+      fpr[(size_t)t * a.E_mon_pad] = fv;
     }
-    if (!fp32_ok) {
+    if (!fp32_ok) {  // the FP64 values replace the FP32 ones just written
       double W[TTO_MAX_K];
       for (int j = 0; j < k; ++j) {
         double w = 0.0;
         for (int q = s_slot[j]; q < s_slot[j + 1]; ++q) w += s_coef[q] * s_col[q][e];
         W[j] = w;
       }
+      c0row = 0;
       for (int t = 0; t < nt; ++t) {
         double f = a.f0[(size_t)a.tsel[t] * a.E + e];
         for (int j = 0; j < k; ++j) f += W[j] * s_psi[t][j];
-        fv[t] = (float)f;
+        const float fv = (float)f;
+        fpr[(size_t)t * a.E_mon_pad] = fv;
+        if (l < a.E_mon && fabsf(fv) > lim) ++c0row;
       }
     }
-    for (int t = 0; t < TT; ++t) {
-      if (t < nt && l < a.E_mon && fabsf(fv[t]) > lim) ++c0cnt;
-      a.fp[((size_t)b * TT + t) * a.E_mon_pad + l] = fv[t];
-    }
+    c0cnt += c0row;
   }
   // outage rows: V, g, islanding of each outage
   int islcnt = 0;
   for (int c = tid; c < a.O_pad; c += blockDim.x) {
     const int cr = min(c, a.O - 1);
     const int e = a.out[cr];
-    float v[TTO_MAX_K], gv[TTO_MAX_T];
+    float v[TTO_MAX_K];
     if (dead) {
+#pragma unroll
       for (int j = 0; j < TTO_MAX_K; ++j) v[j] = 0.f;
-      for (int t = 0; t < TT; ++t) gv[t] = t < nt ? qnan : 0.f;
-      store_col_factors(a, b, c, v, gv);
+      store_col_v(a, b, c, v);
+      for (int t = 0, ci = 0, tt = 0; t < TT; ++t) {
+        store_col_g(a, b, c, t, ci, tt, t < nt ? qnan : 0.f);
+        if (++tt == a.TC) tt = 0, ++ci;
+      }
       continue;
     }
+    // (the FP64 loops run to k: unrolled to TTO_MAX_K with predicates they
+    // measured slower, the FP64 pipe being narrow)
     double W[TTO_MAX_K];
     for (int j = 0; j < k; ++j) {
       double w = 0.0;
@@ -586,7 +608,8 @@ __device__ __forceinline__ void split_update_body(const EvalArgs& a, const int b
     const bool isl = opened || !(npcc > kIslandTol);
     if (isl && !opened && c < a.O) ++islcnt;
     const double inv_np = isl ? 0.0 : 1.0 / npcc;
-    for (int t = 0; t < TT; ++t) {
+    store_col_v(a, b, c, v);
+    for (int t = 0, ci = 0, tt = 0; t < TT; ++t) {
       float g = 0.f;
       if (t < nt) {
         if (isl) {
@@ -597,9 +620,9 @@ __device__ __forceinline__ void split_update_body(const EvalArgs& a, const int b
           g = (float)(f * inv_np);
         }
       }
-      gv[t] = g;
+      store_col_g(a, b, c, t, ci, tt, g);
+      if (++tt == a.TC) tt = 0, ++ci;
     }
-    store_col_factors(a, b, c, v, gv);
   }
   if (c0cnt) atomicAdd(&s_cnt_c0, c0cnt);
   if (islcnt) atomicAdd(&s_cnt_isl, islcnt);
