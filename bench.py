@@ -541,7 +541,8 @@ def main():
     out = None
     for _ in range(2):
         topo_d.copy_(topo_h, non_blocking=True)
-        out = g.evaluate(topo_d, precision=prec, d_split=ds, d_moved=dm, d_disc=dd, out=out)
+        out = g.evaluate(topo_d, precision=prec, fitness_kind=fit_kind, d_split=ds, d_moved=dm, d_disc=dd,
+                         out=out)
         fit_h.copy_(out["fitness"], non_blocking=True)
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -549,7 +550,8 @@ def main():
     e0.record(stream)
     for _ in range(args.steps):
         topo_d.copy_(topo_h, non_blocking=True)
-        out = g.evaluate(topo_d, precision=prec, d_split=ds, d_moved=dm, d_disc=dd, out=out)
+        out = g.evaluate(topo_d, precision=prec, fitness_kind=fit_kind, d_split=ds, d_moved=dm, d_disc=dd,
+                         out=out)
         fit_h.copy_(out["fitness"], non_blocking=True)
     e1.record(stream)
     barrier()
@@ -633,7 +635,8 @@ def main():
             "pair_rate": {"value": B * world * T * E_mon * O * args.steps / (elapsed_ms / 1000.0),
                           "unit": "(topology, t, monitored branch, outage) pairs/s"},
             "stage_ms_per_step": {"split_update": stage_ms[0] / max(ncalls, 1), "sweep": sweep_ms,
-                                  "metrics": stage_ms[2] / max(ncalls, 1)},
+                                  "metrics": stage_ms[2] / max(ncalls, 1),
+                                  "busbar_sweep": stage_ms[3] / max(ncalls, 1)},
             "worst_k_export": wk,
             "time_to_target": ttt,
             "epoch_export": ({"every_steps": args.epoch, "exports_in_timed_region": n_export, "k": 20,

@@ -250,8 +250,9 @@ int tto_evaluate_multi(const tto_eval_job* jobs, int32_t n, const tto_eval_opts*
  * tto_grid_profile(g, 1) clears the record and times the next calls (at most
  * 256); tto_grid_profile(g, 0) stops.  tto_grid_profile_read synchronises on
  * the recorded events and returns, summed over the recorded calls, the
- * milliseconds of the split update, the N-1 sweep and the metric reduction in
- * ms_stage[0..2], and the number of calls in *n_calls. */
+ * milliseconds of the split update, the N-1 sweep, the metric reduction and
+ * the busbar sweep (lambda_f2; 0 without it) in ms_stage[0..3] (host float
+ * [4]), and the number of calls in *n_calls. */
 int tto_grid_profile(tto_grid* g, int32_t enable);
 int tto_grid_profile_read(tto_grid* g, float* ms_stage, int32_t* n_calls);
 

@@ -166,7 +166,8 @@ class Grid:
         _lib.tto_grid_profile(self._h, enable)
 
     def profile_read(self):
-        """([split update ms, sweep ms, reduction ms] summed, number of calls)."""
+        """([split update ms, N-1 sweep ms, reduction ms, busbar sweep ms]
+        summed, number of calls)."""
         return _lib.tto_grid_profile_read(self._h)
 
 

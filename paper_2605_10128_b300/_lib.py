@@ -368,10 +368,10 @@ def tto_grid_profile(h, enable):
 
 
 def tto_grid_profile_read(h):
-    ms = (C.c_float * 3)()
+    ms = (C.c_float * 4)()
     n = C.c_int32()
     check(lib().tto_grid_profile_read(h, ms, C.byref(n)))
-    return [ms[0], ms[1], ms[2]], n.value
+    return [ms[0], ms[1], ms[2], ms[3]], n.value
 
 
 def tto_archive_create(grid_h, d_split, d_moved, d_disc=1):

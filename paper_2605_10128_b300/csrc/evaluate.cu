@@ -927,7 +927,7 @@ int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, 
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   TTO_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
   if (g->prof_on && !split_only && g->prof_n < kProfileCalls && cap == cudaStreamCaptureStatusNone)
-    ev = &g->prof_ev[4 * g->prof_n++];
+    ev = &g->prof_ev[kProfileEvents * g->prof_n++];
   if (ev) TTO_CUDA_TRY(cudaEventRecord(ev[0], s));
   if (bb) {
     split_update_bb_kernel<<<B, 256, 0, s>>>(a);
@@ -950,14 +950,15 @@ int evaluate_impl(tto_grid* g, const int32_t* topo, int B, const int32_t* tsel, 
   }
   rc = launch_sweep(a, s);
   if (rc) return rc;
+  if (ev) TTO_CUDA_TRY(cudaEventRecord(ev[2], s));
   if (bb) {
     rc = launch_busbar_sweep(a, s);
     if (rc) return rc;
   }
-  if (ev) TTO_CUDA_TRY(cudaEventRecord(ev[2], s));
+  if (ev) TTO_CUDA_TRY(cudaEventRecord(ev[3], s));
   fitness_kernel<<<(B + 127) / 128, 128, 0, s>>>(a);
   TTO_CUDA_TRY(cudaGetLastError());
-  if (ev) TTO_CUDA_TRY(cudaEventRecord(ev[3], s));
+  if (ev) TTO_CUDA_TRY(cudaEventRecord(ev[4], s));
   return TTO_OK;
 }
 
@@ -982,7 +983,7 @@ int tto_grid_profile(tto_grid* g, int32_t enable) {
   if (!g) return tto::set_error(TTO_E_ARG, "null grid");
   TTO_CUDA_TRY(cudaSetDevice(g->device));
   if (enable && g->prof_ev.empty()) {
-    g->prof_ev.resize(4 * tto::kProfileCalls);
+    g->prof_ev.resize(tto::kProfileEvents * tto::kProfileCalls);
     for (auto& e : g->prof_ev) TTO_CUDA_TRY(cudaEventCreate(&e));
   }
   g->prof_on = enable ? 1 : 0;
@@ -993,12 +994,16 @@ int tto_grid_profile(tto_grid* g, int32_t enable) {
 int tto_grid_profile_read(tto_grid* g, float* ms_stage, int32_t* n_calls) {
   if (!g || !ms_stage) return tto::set_error(TTO_E_ARG, "null argument");
   TTO_CUDA_TRY(cudaSetDevice(g->device));
-  for (int q = 0; q < 3; ++q) ms_stage[q] = 0.f;
+  // events per call: start, split update done, N-1 sweep done, busbar sweep
+  // done (no busbar sweep: right after the previous one), reduction done
+  static const int kFrom[4] = {0, 1, 3, 2}, kTo[4] = {1, 2, 4, 3};
+  for (int q = 0; q < 4; ++q) ms_stage[q] = 0.f;
   for (int c = 0; c < g->prof_n; ++c) {
-    TTO_CUDA_TRY(cudaEventSynchronize(g->prof_ev[4 * c + 3]));
-    for (int q = 0; q < 3; ++q) {
+    const cudaEvent_t* ev = &g->prof_ev[tto::kProfileEvents * c];
+    TTO_CUDA_TRY(cudaEventSynchronize(ev[tto::kProfileEvents - 1]));
+    for (int q = 0; q < 4; ++q) {
       float ms = 0.f;
-      TTO_CUDA_TRY(cudaEventElapsedTime(&ms, g->prof_ev[4 * c + q], g->prof_ev[4 * c + q + 1]));
+      TTO_CUDA_TRY(cudaEventElapsedTime(&ms, ev[kFrom[q]], ev[kTo[q]]));
       ms_stage[q] += ms;
     }
   }

@@ -15,6 +15,7 @@ constexpr int kRowTile = 128;   // monitored-branch rows per sweep CTA
 constexpr int kColPad = 64;     // outage columns are padded to this multiple
 constexpr int kMaxMoved = TTO_MAX_K * TTO_MAX_ASSETS;
 constexpr int kProfileCalls = 256;  // evaluation calls timed per profiling window
+constexpr int kProfileEvents = 5;   // CUDA events per timed call
 constexpr double kIslandTol = 1e-6;  // N'_cc (and normalised split pivot) at or below: islanded
 
 int set_error(int code, const char* fmt, ...);
@@ -110,7 +111,7 @@ struct tto_grid {
   int tuned_shape[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
   // optional per-stage timing (tto_grid_profile)
   int prof_on = 0, prof_n = 0;
-  std::vector<cudaEvent_t> prof_ev;  // 4 per recorded call
+  std::vector<cudaEvent_t> prof_ev;  // kProfileEvents per recorded call
 };
 
 namespace tto {
