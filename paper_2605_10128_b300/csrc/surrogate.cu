@@ -92,7 +92,8 @@ __device__ __forceinline__ float bf(float x) { return __bfloat162float(__float2b
 // On the fifth-generation tensor cores: a CTA of 128 threads owns a 128 x 128
 // output tile whose FP32 accumulator lives in 128 columns of tensor memory.
 // K advances 64 at a time through two shared-memory stages: all threads load
-// the FP32 operands, round them to BF16 and store them in the canonical
+// the FP32 operands (all of a stage's loads issued at once, 32 float4 per
+// thread), round them to BF16 and store them in the canonical
 // K-major layout without swizzle (core matrices of 8 rows x 16 bytes: 128
 // bytes apart along K, 1024 bytes apart along M / N), then one thread issues
 // four tcgen05.mma kind::f16 (M = 128, N = 128, K = 16, BF16 x BF16 -> FP32)
@@ -151,9 +152,8 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 // op(r, k) = KMAJ ? X[r ld + k] : X[k ld + r], zero outside [0, R) x [k0, ke).
 // KMAJ: eight threads per row read 32 contiguous floats (16 float4 per
 // thread); otherwise a thread reads four rows at four consecutive k and
-// transposes them in registers (4 blocks of 4 float4 per thread).  The loads
-// of eight float4 are issued before any of them is converted, so that many
-// are in flight at once.  vec: float4 reads allowed (ld and X 16-byte aligned).
+// transposes them in registers (4 blocks of 4 float4 per thread).  vec:
+// float4 reads allowed (ld and X 16-byte aligned).
 __device__ __forceinline__ float4 g_ld4(const float* __restrict__ X, size_t o, int valid, bool vec) {
   if (vec && valid >= 4) return __ldg(reinterpret_cast<const float4*>(X + o));
   float4 x;
@@ -164,60 +164,64 @@ __device__ __forceinline__ float4 g_ld4(const float* __restrict__ X, size_t o, i
   return x;
 }
 
+// Loads (g_load, into registers) and stores (g_store, rounded to BF16 into
+// the tile) are split so that a stage's loads of both operands are all in
+// flight before any of them is used, and before the thread waits for the
+// products that last read the stage.
 template <bool KMAJ>
-__device__ __forceinline__ void g_stage(unsigned char* tile, const float* __restrict__ X, int ld, int r0, int R,
-                                        int k0, int ke, bool vec) {
+__device__ __forceinline__ void g_load(float4 (&x)[16], const float* __restrict__ X, int ld, int r0, int R, int k0,
+                                       int ke, bool vec) {
   const int tid = threadIdx.x;
   if (KMAJ) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      float4 x[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int idx = (h * 8 + i) * 128 + tid;
-        const int r = (idx >> 3) & 127, k = ((idx >> 10) << 5) + ((idx & 7) << 2);
-        const int gr = r0 + r, gk = k0 + k;
-        x[i] = gr < R ? g_ld4(X, (size_t)gr * ld + gk, ke - gk, vec) : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int idx = (h * 8 + i) * 128 + tid;
-        const int r = (idx >> 3) & 127, k = ((idx >> 10) << 5) + ((idx & 7) << 2);
-        uint2 w;
-        w.x = pack_bf16x2(x[i].x, x[i].y);
-        w.y = pack_bf16x2(x[i].z, x[i].w);
-        *reinterpret_cast<uint2*>(tile + g_off(r, k)) = w;
-      }
+    for (int i = 0; i < 16; ++i) {
+      const int idx = i * 128 + tid;
+      const int r = (idx >> 3) & 127, k = ((idx >> 10) << 5) + ((idx & 7) << 2);
+      const int gr = r0 + r, gk = k0 + k;
+      x[i] = gr < R ? g_ld4(X, (size_t)gr * ld + gk, ke - gk, vec) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   } else {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      float4 x[2][4];  // two 4 x 4 blocks: x[b][j] = rows r .. r + 3 at k + j
+    for (int b = 0; b < 4; ++b) {  // four 4 x 4 blocks: x[4 b + j] = rows r .. r + 3 at k + j
+      const int idx = b * 128 + tid;
+      const int r = (idx & 31) << 2, k = (idx >> 5) << 2;
 #pragma unroll
-      for (int bI = 0; bI < 2; ++bI) {
-        const int idx = (h * 2 + bI) * 128 + tid;
-        const int r = (idx & 31) << 2, k = (idx >> 5) << 2;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int gk = k0 + k + j, gr = r0 + r;
-          x[bI][j] = gk < ke ? g_ld4(X, (size_t)gk * ld + gr, R - gr, vec) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
+      for (int j = 0; j < 4; ++j) {
+        const int gk = k0 + k + j, gr = r0 + r;
+        x[4 * b + j] = gk < ke ? g_ld4(X, (size_t)gk * ld + gr, R - gr, vec) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
+    }
+  }
+}
+
+template <bool KMAJ>
+__device__ __forceinline__ void g_store(unsigned char* tile, const float4 (&x)[16]) {
+  const int tid = threadIdx.x;
+  if (KMAJ) {
 #pragma unroll
-      for (int bI = 0; bI < 2; ++bI) {
-        const int idx = (h * 2 + bI) * 128 + tid;
-        const int r = (idx & 31) << 2, k = (idx >> 5) << 2;
-        const float4* v = x[bI];
-        uint2 w;
-        w.x = pack_bf16x2(v[0].x, v[1].x), w.y = pack_bf16x2(v[2].x, v[3].x);
-        *reinterpret_cast<uint2*>(tile + g_off(r, k)) = w;
-        w.x = pack_bf16x2(v[0].y, v[1].y), w.y = pack_bf16x2(v[2].y, v[3].y);
-        *reinterpret_cast<uint2*>(tile + g_off(r + 1, k)) = w;
-        w.x = pack_bf16x2(v[0].z, v[1].z), w.y = pack_bf16x2(v[2].z, v[3].z);
-        *reinterpret_cast<uint2*>(tile + g_off(r + 2, k)) = w;
-        w.x = pack_bf16x2(v[0].w, v[1].w), w.y = pack_bf16x2(v[2].w, v[3].w);
-        *reinterpret_cast<uint2*>(tile + g_off(r + 3, k)) = w;
-      }
+    for (int i = 0; i < 16; ++i) {
+      const int idx = i * 128 + tid;
+      const int r = (idx >> 3) & 127, k = ((idx >> 10) << 5) + ((idx & 7) << 2);
+      uint2 w;
+      w.x = pack_bf16x2(x[i].x, x[i].y);
+      w.y = pack_bf16x2(x[i].z, x[i].w);
+      *reinterpret_cast<uint2*>(tile + g_off(r, k)) = w;
+    }
+  } else {
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int idx = b * 128 + tid;
+      const int r = (idx & 31) << 2, k = (idx >> 5) << 2;
+      const float4* v = x + 4 * b;
+      uint2 w;
+      w.x = pack_bf16x2(v[0].x, v[1].x), w.y = pack_bf16x2(v[2].x, v[3].x);
+      *reinterpret_cast<uint2*>(tile + g_off(r, k)) = w;
+      w.x = pack_bf16x2(v[0].y, v[1].y), w.y = pack_bf16x2(v[2].y, v[3].y);
+      *reinterpret_cast<uint2*>(tile + g_off(r + 1, k)) = w;
+      w.x = pack_bf16x2(v[0].z, v[1].z), w.y = pack_bf16x2(v[2].z, v[3].z);
+      *reinterpret_cast<uint2*>(tile + g_off(r + 2, k)) = w;
+      w.x = pack_bf16x2(v[0].w, v[1].w), w.y = pack_bf16x2(v[2].w, v[3].w);
+      *reinterpret_cast<uint2*>(tile + g_off(r + 3, k)) = w;
     }
   }
 }
@@ -263,15 +267,18 @@ __global__ void __launch_bounds__(128) gemm_umma_kernel(int M, int N, int K, con
     const int st = kt & 1;
     unsigned char* sa = smem + st * 2 * kGTile;
     unsigned char* sb = sa + kGTile;
+    const int k0 = kb + kt * kGK;
+    float4 xa[16], xb[16];
+    g_load<!TA>(xa, A, lda, m0, M, k0, ke, vecA);
+    g_load<TB>(xb, B, ldb, n0, N, k0, ke, vecB);
     // the products that read this stage two steps ago must be complete
     if (kt >= kGStages) ok = g_wait(&mbar[st], (uint32_t)((kt >> 1) - 1) & 1u, abort_flag);
     if (!__syncthreads_and(ok)) {
       ok = false;
       break;
     }
-    const int k0 = kb + kt * kGK;
-    g_stage<!TA>(sa, A, lda, m0, M, k0, ke, vecA);
-    g_stage<TB>(sb, B, ldb, n0, N, k0, ke, vecB);
+    g_store<!TA>(sa, xa);
+    g_store<TB>(sb, xb);
     // the generic-proxy stores must be visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
