@@ -54,6 +54,7 @@ struct tto_surrogate {
   // per-batch buffers (capacity bcap rows)
   int bcap = 0;
   int* SI = nullptr;      // [bcap][k] station of each genome slot, -1 = empty
+  uint32_t* SM = nullptr; // [S][ceil(bcap / 32)] bit r of word w: row 32 w + r splits the station
   float* SF = nullptr;    // [bcap][k][8] that station's eight values
   float* XD = nullptr;    // [bcap][R] loadings
   int* valid = nullptr;   // [bcap] 0 = the split islands the grid (or the genome is invalid)
@@ -758,24 +759,43 @@ __global__ void __launch_bounds__(1024) colsum_kernel(int M, int N, const float*
 }
 
 // Gradient of the station block of W1: one CTA per station s,
-// G1[h][8 s + c] = sum over genome slots holding s (in slot order) of
-// dH1[row][h] f_c.  Each thread counts the hits in its contiguous share of
-// the slots; an exclusive scan of the counts gives every hit its position in
-// slot order; the hits are then staged in shared memory 1024 at a time and
-// accumulated by all threads, two hidden units each (H <= 1024: four).
+// G1[h][8 s + c] = sum over genome slots holding s (in slot order, i.e. row
+// order) of dH1[row][h] f_c.  The hits are staged in shared memory 1024 at a
+// time and accumulated by all threads, two hidden units each (H <= 1024:
+// four).
 constexpr int kGradList = 1024;
-__global__ void __launch_bounds__(256) station_grad_kernel(int M, int H, int D, int k, const int* SI,
-                                                           const float* SF, const float* dH1, float* G1) {
+// Row masks of the batch per station (SM zeroed before): one thread per
+// genome slot sets its row's bit in the word of its station.  A genome names
+// a station at most once (a repeat marks the whole genome invalid, every slot
+// -1), so a station's set rows are exactly its (row, slot) entries.
+__global__ void station_mask_kernel(int n_ent, int k, int words, const int* SI, uint32_t* SM) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_ent) return;
+  const int st = SI[e];
+  if (st < 0) return;
+  const int row = e / k;
+  atomicOr(SM + (size_t)st * words + (row >> 5), 1u << (row & 31));
+}
+
+// Gradient of the station block of W1 (columns 8 s .. 8 s + 7): for every
+// hidden unit h, the sum over the batch rows that split station s, in row
+// order, of dH1[row][h] times the station's eight values (rounded to BF16 as
+// in the forward product).  One CTA per station: its rows come from the
+// station's mask words (each thread a run of words, a prefix sum over the
+// threads gives every row its place), kGradList rows at a time.
+__global__ void __launch_bounds__(256) station_grad_kernel(int M, int H, int D, int k, int words, const int* SI,
+                                                           const float* SF, const uint32_t* SM, const float* dH1,
+                                                           float* G1) {
   const int s = blockIdx.x, tid = threadIdx.x;
   __shared__ int s_row[kGradList];
   __shared__ float s_f[kGradList][8];
   __shared__ int s_cnt[256];
   __shared__ int s_total;
-  const int n_ent = M * k;
-  const int per = (n_ent + 255) / 256;
-  const int e0 = min(n_ent, tid * per), e1 = min(n_ent, e0 + per);
+  const uint32_t* sm = SM + (size_t)s * words;
+  const int per = (words + 255) / 256;
+  const int w0 = min(words, tid * per), w1 = min(words, w0 + per);
   int cnt = 0;
-  for (int e = e0; e < e1; ++e) cnt += SI[e] == s ? 1 : 0;
+  for (int w = w0; w < w1; ++w) cnt += __popc(sm[w]);
   s_cnt[tid] = cnt;
   __syncthreads();
   if (tid == 0) {
@@ -797,14 +817,21 @@ __global__ void __launch_bounds__(256) station_grad_kernel(int M, int H, int D, 
   for (int base = 0; base < total; base += kGradList) {
     if (cnt > 0 && off < base + kGradList && off + cnt > base) {
       int pos = off;
-      for (int e = e0; e < e1 && pos < base + kGradList; ++e) {
-        if (SI[e] != s) continue;
-        if (pos >= base) {
-          s_row[pos - base] = e / k;
+      for (int w = w0; w < w1 && pos < base + kGradList; ++w) {
+        uint32_t bits = sm[w];
+        while (bits && pos < base + kGradList) {
+          const int row = 32 * w + __ffs(bits) - 1;
+          bits &= bits - 1;
+          if (pos >= base) {
+            int j = 0;
+            while (j < k - 1 && SI[(size_t)row * k + j] != s) ++j;
+            const float* f = SF + ((size_t)row * k + j) * 8;
+            s_row[pos - base] = row;
 #pragma unroll
-          for (int c = 0; c < 8; ++c) s_f[pos - base][c] = bf(SF[(size_t)e * 8 + c]);
+            for (int c = 0; c < 8; ++c) s_f[pos - base][c] = bf(f[c]);
+          }
+          ++pos;
         }
-        ++pos;
       }
     }
     __syncthreads();
@@ -830,6 +857,7 @@ __global__ void __launch_bounds__(256) station_grad_kernel(int M, int H, int D, 
 #pragma unroll
       for (int c = 0; c < 8; ++c) G1[(size_t)h * D + 8 * s + c] = acc[u][c];
   }
+  (void)M;
 }
 
 // Adam with bias correction: c1 = 1 - beta1^t, c2 = 1 - beta2^t.
@@ -1093,11 +1121,12 @@ __global__ void sample_kernel(int M, int n_rep, int k, int R, uint2 key, uint32_
 // ------------------------------------------------------------------ host side
 int alloc_batch(tto_surrogate* s, int B) {
   if (B <= s->bcap) return TTO_OK;
-  void* old[] = {s->SI, s->SF, s->XD, s->valid, s->nsm, s->H1, s->H2, s->H3, s->Y, s->dH1, s->dH2, s->dH3, s->dY,
+  void* old[] = {s->SI, s->SM, s->SF, s->XD, s->valid, s->nsm, s->H1, s->H2, s->H3, s->Y, s->dH1, s->dH2, s->dH3, s->dY,
                  s->T, s->mb_topo};
   for (void* p : old)
     if (p) cudaFree(p);
   s->SI = nullptr;
+  s->SM = nullptr;
   s->SF = s->XD = s->H1 = s->H2 = s->H3 = s->Y = s->dH1 = s->dH2 = s->dH3 = s->dY = s->T = nullptr;
   s->valid = nullptr;
   s->nsm = nullptr;
@@ -1105,6 +1134,7 @@ int alloc_batch(tto_surrogate* s, int B) {
   s->bcap = 0;
   const size_t b = B, H = s->H;
   TTO_CUDA_TRY(cudaMalloc(&s->SI, b * s->k * sizeof(int)));
+  TTO_CUDA_TRY(cudaMalloc(&s->SM, (size_t)s->S * ((b + 31) / 32) * sizeof(uint32_t)));
   TTO_CUDA_TRY(cudaMalloc(&s->SF, b * s->k * 8 * sizeof(float)));
   TTO_CUDA_TRY(cudaMalloc(&s->XD, b * s->R * sizeof(float)));
   TTO_CUDA_TRY(cudaMalloc(&s->valid, b * sizeof(int)));
@@ -1211,7 +1241,10 @@ int backward(tto_surrogate* s, int M, cudaStream_t st) {
   if ((rc = gemm<false, false>(M, H, H, s->dH2, H, P + s->oW2, H, s->dH1, H, nullptr, s->H1, false, s->g->d_status, st))) return rc;
   if ((rc = gemm_wgrad(H, R, M, s->dH1, H, s->XD, R, G + s->oW1 + 8 * (size_t)s->S, D, s->wsk, s->g->d_status, st))) return rc;
   colsum_kernel<<<ncs, cs, 0, st>>>(M, H, s->dH1, nullptr, G + s->ob1);
-  station_grad_kernel<<<s->S, 256, 0, st>>>(M, H, D, s->k, s->SI, s->SF, s->dH1, G + s->oW1);
+  const int words = (M + 31) / 32;
+  TTO_CUDA_TRY(cudaMemsetAsync(s->SM, 0, (size_t)s->S * words * sizeof(uint32_t), st));
+  station_mask_kernel<<<(unsigned)(((size_t)M * s->k + 255) / 256), 256, 0, st>>>(M * s->k, s->k, words, s->SI, s->SM);
+  station_grad_kernel<<<s->S, 256, 0, st>>>(M, H, D, s->k, words, s->SI, s->SF, s->SM, s->dH1, G + s->oW1);
   TTO_CUDA_TRY(cudaGetLastError());
   return TTO_OK;
 }
@@ -1307,7 +1340,7 @@ int append(tto_surrogate* s, const int32_t* topo, int n, const int32_t* idx, con
 }
 
 void release(tto_surrogate* s) {
-  void* ptrs[] = {s->P,  s->G,     s->Am, s->Av, s->W1sT, s->wsk, s->rows, s->row_lim, s->Nsr, s->SI,  s->SF,
+  void* ptrs[] = {s->P,  s->G,     s->Am, s->Av, s->W1sT, s->wsk, s->rows, s->row_lim, s->Nsr, s->SI, s->SM, s->SF,
                   s->XD, s->valid, s->nsm, s->H1, s->H2, s->H3, s->Y,    s->dH1,     s->dH2, s->dH3, s->dY,
                   s->T,  s->mb_topo, s->loss, s->stats, s->rep_genome, s->rep_xd, s->rep_t, s->prop, s->keys, s->sel};
   for (void* p : ptrs)
