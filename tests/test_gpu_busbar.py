@@ -95,7 +95,12 @@ def test_lambda_f2_fitness(mode):
     with pytest.raises(TTOError):
         g.evaluate(t, fitness_kind=FIT_F2, precision=prec)
     g.busbar_reference()
+    g.profile(True)
     out = g.evaluate(t, fitness_kind=FIT_F2, metrics=True, fmax=True, precision=prec)
+    g.evaluate(t, precision=prec)  # a plain evaluation: no busbar stage
+    stage, n_calls = g.profile_read()
+    g.profile(False)
+    assert n_calls == 2 and min(stage[:3]) > 0 and stage[3] > 0  # split, N-1 sweep, metrics, busbar sweep
     g.sync_status()
     out = {k: v.cpu().numpy() for k, v in out.items() if not k.startswith("_")}
     idx = list(range(len(topo)))
