@@ -783,9 +783,9 @@ __global__ void station_mask_kernel(int n_ent, int k, int words, const int* SI, 
 // in the forward product).  One CTA per station: its rows come from the
 // station's mask words (each thread a run of words, a prefix sum over the
 // threads gives every row its place), kGradList rows at a time.
-__global__ void __launch_bounds__(256) station_grad_kernel(int M, int H, int D, int k, int words, const int* SI,
-                                                           const float* SF, const uint32_t* SM, const float* dH1,
-                                                           float* G1) {
+__global__ void __launch_bounds__(256) station_grad_kernel(int H, int D, int k, int words, const int* SI,
+                                                           const float* SF, const uint32_t* SM,
+                                                           const float* dH1, float* G1) {
   const int s = blockIdx.x, tid = threadIdx.x;
   __shared__ int s_row[kGradList];
   __shared__ float s_f[kGradList][8];
@@ -857,7 +857,6 @@ __global__ void __launch_bounds__(256) station_grad_kernel(int M, int H, int D, 
 #pragma unroll
       for (int c = 0; c < 8; ++c) G1[(size_t)h * D + 8 * s + c] = acc[u][c];
   }
-  (void)M;
 }
 
 // Adam with bias correction: c1 = 1 - beta1^t, c2 = 1 - beta2^t.
@@ -1244,7 +1243,7 @@ int backward(tto_surrogate* s, int M, cudaStream_t st) {
   const int words = (M + 31) / 32;
   TTO_CUDA_TRY(cudaMemsetAsync(s->SM, 0, (size_t)s->S * words * sizeof(uint32_t), st));
   station_mask_kernel<<<(unsigned)(((size_t)M * s->k + 255) / 256), 256, 0, st>>>(M * s->k, s->k, words, s->SI, s->SM);
-  station_grad_kernel<<<s->S, 256, 0, st>>>(M, H, D, s->k, words, s->SI, s->SF, s->SM, s->dH1, G + s->oW1);
+  station_grad_kernel<<<s->S, 256, 0, st>>>(H, D, s->k, words, s->SI, s->SF, s->SM, s->dH1, G + s->oW1);
   TTO_CUDA_TRY(cudaGetLastError());
   return TTO_OK;
 }
