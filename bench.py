@@ -275,7 +275,7 @@ def _best(archive):
     return float(fit[filled.astype(bool)].max()) if filled.any() else -np.inf
 
 
-def time_to_target(g, prec, variants_spec, seeds, iters, train_steps, stop_at_target=False):
+def time_to_target(g, prec, variants_spec, seeds, iters, train_steps, stop_at_target=False, seed_base=2000):
     """Time to target on the 10000-bus workload: surrogate-screened MapElites
     against plain MapElites (8192 proposals evaluated exactly per iteration),
     same seeds, same precision.  A screened variant "rank:n" proposes n
@@ -346,7 +346,7 @@ def time_to_target(g, prec, variants_spec, seeds, iters, train_steps, stop_at_ta
 
     runs = []
     for k in range(seeds):
-        seed = 2000 + k
+        seed = seed_base + k
         plain, _ = run_arm(seed, None)
         target = plain[-1][1]
         t_plain = next(t for t, b in plain if b >= target)
@@ -386,7 +386,7 @@ def run_surrogate(args, prec):
     g.reserve(B)
     g.autotune(512, precision=prec)
     summary, runs = time_to_target(g, prec, args.variants, args.seeds, args.iters, args.train_steps,
-                                   args.stop_at_target)
+                                   args.stop_at_target, seed_base=args.seed_base)
     head = summary[args.variants.split(",")[0]]["median_speedup"]
     line = {"metric": "time-to-target best fitness (10k-bus), surrogate-screened vs plain MapElites",
             "value": head, "unit": "x (plain s / screened s)",
@@ -395,7 +395,8 @@ def run_surrogate(args, prec):
             "config": {"workload": workload_desc(cfg, B), "precision": args.precision,
                        "variants": args.variants, "exact_per_iter": B,
                        "train_steps_per_iter": args.train_steps,
-                       "seeds": args.seeds, "iterations": args.iters, "stop_at_target": args.stop_at_target},
+                       "seeds": args.seeds, "seed_base": args.seed_base, "iterations": args.iters,
+                       "stop_at_target": args.stop_at_target},
             "summary": summary, "runs": runs, "gpu_launches": None}
     print(json.dumps(line), flush=True)
 
@@ -415,6 +416,7 @@ def main():
                     help="fix the sweep tile variant instead of autotuning (4 = tcgen05, TF32X3 only)")
     ap.add_argument("--iters", type=int, default=60, help="--config surrogate: iterations per arm")
     ap.add_argument("--seeds", type=int, default=6, help="--config surrogate: seeds")
+    ap.add_argument("--seed-base", type=int, default=2000, help="--config surrogate: first seed")
     ap.add_argument("--variants", default="score:65536@16,score:65536@8",
                     help="--config surrogate: screened variants rank:proposals[@first screened iteration] "
                          "(rank = score or gain)")
